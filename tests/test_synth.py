@@ -17,8 +17,9 @@ def test_descriptor_recipe_statistics():
     assert (a >= 0).sum() == 800 and (b >= 0).sum() == 800
     assert set(a[a >= 0]) == set(b[b >= 0])
     pos_a = {t: k for k, t in enumerate(a) if t >= 0}
-    diff = [np.abs(d[pos_a[t]].astype(int) - d[2000 + k].astype(int)).std() for k, t in enumerate(b) if t >= 0]
-    assert 6 < np.mean(diff) < 9
+    diff = np.array([d[2000 + k].astype(int) - d[pos_a[t]].astype(int) for k, t in enumerate(b) if t >= 0])
+    # sigma-8 noise, a little less after clipping at 0
+    assert 6.5 < diff.std() < 8.5 and abs(diff.mean()) < 1.5
 
 
 def test_generation_is_deterministic_and_sliceable():
