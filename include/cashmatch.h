@@ -1,0 +1,218 @@
+/*
+ * cashmatch — cascade-hashing feature matching over MBR-scheduled image blocks,
+ * for NVIDIA B300 (sm_103a).  C ABI.
+ *
+ * Method: "Efficient Feature Matching for UAV Images based on Compact GPU Data
+ * Scheduling" (arXiv 2505.22089).  Cascade hashing, Sec. 2.3.1 steps (1)-(4):
+ * hash lookup in L tables of 2^m buckets, remapping to n-bit codes, Hamming
+ * ranking to the top K, Euclidean rerank and ratio test.  Schedule blocks by
+ * matrix band reduction, Sec. 2.2 steps (1)-(5) with the GPS ordering of
+ * Algorithm 2.  Block-row load / match / free, Sec. 2.3.2 and Algorithm 1.
+ *
+ * Conventions for every call:
+ *  - Return value: CM_OK or an error code; nothing is thrown across the ABI.
+ *    cm_last_error() returns a message for the calling thread's last error.
+ *  - "device" pointers are CUDA global-memory addresses on the current device;
+ *    "host" pointers are CPU addresses (pinned memory gives overlapped copies).
+ *  - Streams are cudaStream_t values passed as cm_stream (NULL = legacy
+ *    default stream).  Calls documented "async" only enqueue work: inputs must
+ *    stay valid and outputs must not be read until the stream is synchronised.
+ *  - Ownership: the caller owns every buffer it passes.  The library owns the
+ *    handles it returns and frees them in the matching cm_*_destroy / cm_free_*.
+ *    The library never calls cudaMalloc: all device storage of an index comes
+ *    from the caller's arena.
+ *  - Descriptors are uint8 [rows][128], row-major, 128 bytes per row.  An
+ *    image holds at most 65,535 descriptors.
+ */
+#ifndef CASHMATCH_H
+#define CASHMATCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cm_stream;
+
+typedef enum {
+    CM_OK = 0,
+    CM_ERR_INVALID = 1,  /* bad argument: NULL, out-of-range id, i == j, N > 65535, bad params */
+    CM_ERR_BUDGET = 2,   /* arena / HBM budget too small for what was asked */
+    CM_ERR_CUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error) */
+    CM_ERR_TIMEOUT = 4,  /* a bounded device wait gave up; results of that launch are invalid */
+    CM_ERR_NOMEM = 5,    /* host allocation failed */
+    CM_ERR_STATE = 6     /* call not valid in the object's current state (e.g. image not resident) */
+} cm_status;
+
+/* How the top-K candidates are re-scored by Euclidean distance (step (4)). */
+typedef enum {
+    CM_RERANK_FP32 = 0,  /* CUDA cores, FP32 arithmetic (exact: all partial sums are integers < 2^24) */
+    CM_RERANK_BF16 = 1,  /* tensor cores (tcgen05, kind::f16), BF16 inputs, FP32 accumulate (exact for uint8) */
+    CM_RERANK_FP8 = 2,   /* tensor cores, FP8 e4m3 with a per-descriptor scale, FP32 accumulate; the top 2
+                            are re-scored exactly in FP32 */
+    CM_RERANK_INT = 3    /* CUDA cores, 4-way byte SIMD integer arithmetic (exact) */
+} cm_rerank;
+
+/* Where descriptor pointers given to the library live. */
+typedef enum {
+    CM_MEM_HOST = 0,          /* host memory: the library copies it into the arena (H2D) */
+    CM_MEM_DEVICE = 1,        /* device memory: the library copies it into the arena (D2D) */
+    CM_MEM_DEVICE_INPLACE = 2 /* device memory used in place; the caller keeps it alive and unchanged */
+} cm_mem;
+
+/* Cascade-hashing parameters.  Paper defaults (Sec. 2.3.1): L = 6, m = 8,
+ * n = 128, K = 8; ratio threshold t_r = ratio_num / ratio_den (0.8 = 4/5 in
+ * SiftGPU, 0.5 chosen in Sec. 3.2).  The ratio test dis(q1) < t_r dis(q2) is
+ * decided exactly. */
+typedef struct cm_params {
+    int32_t L;           /* hash tables, 1..8 */
+    int32_t m;           /* bits per bucket key, 0..8 (2^m buckets per table) */
+    int32_t n_bits;      /* fine code bits; must be 128 */
+    int32_t K;           /* Hamming top-K kept for the rerank: 2, 4, 8 or 16 */
+    int32_t ratio_num;   /* t_r numerator, >= 0 */
+    int32_t ratio_den;   /* t_r denominator, >= 1; num/den <= 4 */
+    uint64_t seed;       /* seed of the projection weights (splitmix64 + Box-Muller, see cm_make_weights) */
+    int32_t rerank;      /* cm_rerank */
+    int32_t query_tile;  /* queries per work item of the match kernel; 0 = library default */
+} cm_params;
+
+typedef struct { int32_t i, j; } cm_pair;  /* query image i, database image j (i != j) */
+
+typedef struct cm_index cm_index;
+typedef struct cm_schedule cm_schedule;
+typedef struct cm_match_plan cm_match_plan;
+
+/* Outputs of a match launch: per query row, device pointers, any may be NULL
+ * except best_j.  Rows of pair k start at row_off(k) = sum of N_i over the
+ * pairs before k in the plan's pair list. */
+typedef struct cm_match_out {
+    int32_t* best_j;     /* index in image j of the accepted nearest neighbour, or -1 */
+    uint32_t* d1sq;      /* squared distance to q1 (UINT32_MAX if fewer than 1 candidate) */
+    uint32_t* d2sq;      /* squared distance to q2 (UINT32_MAX if fewer than 2 candidates) */
+    int32_t* topk;       /* [rows][K] Hamming top-K in rank order, -1 padded (diagnostic) */
+    uint32_t* stats;     /* [4] accumulated counters: 0 FP64 re-checks, 1 matches, 2 FP8 top-2 swaps, 3 reserved */
+} cm_match_out;
+
+/* One row of a schedule (Sec. 2.3.2: load the row's new block, match, free the first block). */
+typedef struct cm_schedule_row {
+    int32_t iteration;      /* MBR iteration (Sec. 2.2 step (5)) */
+    int32_t n_load;         /* images to make resident before the row */
+    const int32_t* load;
+    int32_t n_free;         /* images released after the row */
+    const int32_t* free_ids;
+    int64_t n_pairs;        /* pairs matched in this row, as indices into the caller's pair list */
+    const int64_t* pairs;
+} cm_schedule_row;
+
+/* ---- library ------------------------------------------------------------ */
+const char* cm_version(void);
+/* Message of the calling thread's last failed call ("" if none).  Valid until the next call on the thread. */
+const char* cm_last_error(void);
+/* Fills paper defaults: L=6, m=8, n_bits=128, K=8, t_r=4/5, rerank=FP32. */
+cm_status cm_params_default(cm_params* p);
+/* Checks a parameter set; CM_ERR_INVALID with a message if unsupported. */
+cm_status cm_params_check(const cm_params* p);
+
+/* Projection weights W[128][P] (host, row-major, P = L*m + n_bits): random
+ * hyperplanes through the centred origin (Sec. 2.3.1 "LSH ... random hashing
+ * functions").  Columns t*m .. t*m+m-1 give the bucket key of table t (bit b =
+ * column t*m+b), columns L*m .. P-1 the fine code.  W is drawn from one
+ * splitmix64 stream seeded with p->seed: each pair of outputs (r1, r2) gives
+ * u1 = ((r1>>11)+1) 2^-53, u2 = (r2>>11) 2^-53 and the Box-Muller pair
+ * sqrt(-2 ln u1) (cos, sin)(2 pi u2), filled row-major and rounded to float. */
+cm_status cm_make_weights(const cm_params* p, float* W_host);
+
+/* Arena bytes one resident image of n descriptors occupies (layout of the
+ * index: descriptors, keys, codes, bucket-sorted codes and indices, offsets,
+ * norms, and the tensor-core copy for BF16/FP8 reranks). */
+cm_status cm_image_bytes(const cm_params* p, int32_t n_desc, uint64_t* bytes);
+/* Arena bytes for an index holding every image of n_desc resident (descriptors
+ * in place when inplace != 0), plus its fixed tables. */
+cm_status cm_index_bytes(const cm_params* p, int32_t n_images, const int32_t* n_desc, int32_t inplace,
+                         uint64_t* bytes);
+
+/* ---- schedule blocks (Sec. 2.2; Algorithm 1, CascadeHashingMatching; Algorithm 2) */
+/* Symmetrises the pair graph, orders it by GPS, cuts the order into chunks of
+ * at most max_images_per_block images (Size_blk), and forms block rows: the
+ * window of consecutive chunks whose resident bytes (cm_image_bytes) fit
+ * hbm_budget.  Each row takes the unprocessed pairs whose lower chunk is the
+ * row's first chunk and whose other image lies in the window; the rest wait
+ * for the next MBR iteration, which re-orders the remaining graph.  Repeats
+ * until every pair is placed.  Host only, synchronous.
+ * Errors: CM_ERR_INVALID (id out of range, i == j), CM_ERR_BUDGET (a pair's two
+ * images exceed the budget). */
+cm_status cm_schedule_blocks(const cm_pair* pairs, int64_t n_pairs, int32_t n_images, const int32_t* n_desc,
+                             const cm_params* p, uint64_t hbm_budget, int32_t max_images_per_block,
+                             cm_schedule** out);
+int32_t cm_schedule_num_rows(const cm_schedule* s);
+int32_t cm_schedule_num_iterations(const cm_schedule* s);
+/* View of row r; pointers stay valid until cm_free_schedule. */
+cm_status cm_schedule_get_row(const cm_schedule* s, int32_t r, cm_schedule_row* row);
+void cm_free_schedule(cm_schedule* s);
+/* GPS ordering (Algorithm 2) of the undirected graph on n nodes with the given
+ * edges (int32 pairs).  Writes the non-isolated nodes in their new order to
+ * order[] (capacity n) and their count to *n_order. */
+cm_status cm_gps_order(int32_t n, int64_t n_edges, const int32_t* edges, int32_t* order, int32_t* n_order);
+
+/* ---- index (Sec. 2.3.2 step (1): load, hash, build lookup tables) -------- */
+/* Creates an empty index over n_images images of the given sizes, using the
+ * caller's device arena for all its device storage.  Nothing resident yet. */
+cm_status cm_index_create(const cm_params* p, int32_t n_images, const int32_t* n_desc, void* d_arena,
+                          uint64_t arena_bytes, cm_index** out);
+/* Centring mean from exact column sums: mu = sums / n_total (host values;
+ * the upload is enqueued on stream). */
+cm_status cm_index_set_mean(cm_index* ix, const uint64_t* col_sums_host, uint64_t n_total, cm_stream stream);
+/* Centring mean from the exact column sums of n_rows device descriptor rows
+ * (async, on stream). */
+cm_status cm_index_mean_device(cm_index* ix, const uint8_t* d_desc, uint64_t n_rows, cm_stream stream);
+/* Exact column sums and row count behind the current centring mean, copied to
+ * host (waits for stream).  Valid after cm_build_index, cm_index_mean_device,
+ * cm_index_rehash or cm_index_set_mean. */
+cm_status cm_index_col_sums(cm_index* ix, uint64_t* sums_host, uint64_t* n_total, cm_stream stream);
+/* Makes images resident (async): copies their descriptors into the arena
+ * (unless CM_MEM_DEVICE_INPLACE), computes keys and codes and builds the per
+ * table buckets.  desc[k] points at image ids[k]'s rows.  The mean must be set.
+ * Errors: CM_ERR_STATE (already resident / mean unset), CM_ERR_BUDGET (arena full). */
+cm_status cm_index_load(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc,
+                        int32_t mem, cm_stream stream);
+/* Recomputes centring statistics from the resident descriptors, then keys,
+ * codes and buckets of every resident image (async; a whole hashing pass). */
+cm_status cm_index_rehash(cm_index* ix, cm_stream stream);
+/* Releases resident images (Sec. 2.3.2 step (3)) and refreshes the device
+ * tables on stream.  Every call on an index must use the same stream: work
+ * already enqueued that reads an evicted image then precedes any later load
+ * that reuses its arena space. */
+cm_status cm_index_evict(cm_index* ix, int32_t count, const int32_t* ids, cm_stream stream);
+/* Builds an index with every image resident: create + mean over all given
+ * descriptors + load.  desc = all images' rows concatenated in image order. */
+cm_status cm_build_index(const cm_params* p, int32_t n_images, const int32_t* n_desc, const uint8_t* desc,
+                         int32_t mem, void* d_arena, uint64_t arena_bytes, cm_stream stream, cm_index** out);
+/* Device pointers of a resident image's index data (diagnostics / tests):
+ * keys u64[n] (byte t = key of table t), codes 4 x u32 [n], sorted codes
+ * [L][n] (16 B), sorted local indices u16 [L][n], offsets u32 [L][2^m+1]. */
+cm_status cm_index_image_view(const cm_index* ix, int32_t image, const void** keys, const void** codes,
+                              const void** sorted_codes, const void** sorted_idx, const void** offsets);
+void cm_index_destroy(cm_index* ix);
+
+/* ---- matching (Sec. 2.3.1 steps (1)-(4), one launch per block) ------------ */
+/* Plans a batch of pairs (host list): validates ids and residency and uploads
+ * the work table into the index arena (async, on stream).  A plan can be run
+ * many times and captured in a CUDA graph; it must not outlive the residency
+ * of its images. */
+cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, cm_stream stream,
+                               cm_match_plan** out);
+/* Total query rows of the plan (sum of N_i) — the size of each output array. */
+int64_t cm_match_plan_rows(const cm_match_plan* pl);
+/* One persistent fused launch over every pair of the plan (async): bucket
+ * lookup, Hamming ranking, top-K, rerank and ratio test. */
+cm_status cm_match_plan_run(cm_match_plan* pl, const cm_match_out* out, cm_stream stream);
+void cm_match_plan_destroy(cm_match_plan* pl);
+/* Convenience: plan, run on stream, wait for the stream, destroy the plan. */
+cm_status cm_match_pairs(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, const cm_match_out* out,
+                         cm_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CASHMATCH_H */

@@ -1,0 +1,362 @@
+"""Python binding of the cashmatch C ABI (include/cashmatch.h).
+
+Argument marshalling only: every step of the matching path runs in the CUDA
+library ``libcashmatch.so`` built from ``csrc/`` for sm_103a.  PyTorch provides
+device memory (the index arena, outputs) and streams.  There is no fallback:
+if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import weakref
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcashmatch.so")
+
+CM_OK, CM_ERR_INVALID, CM_ERR_BUDGET, CM_ERR_CUDA, CM_ERR_TIMEOUT, CM_ERR_NOMEM, CM_ERR_STATE = range(7)
+RERANK = {"fp32": 0, "bf16": 1, "fp8": 2, "int": 3}
+MEM_HOST, MEM_DEVICE, MEM_DEVICE_INPLACE = 0, 1, 2
+
+# Every symbol include/cashmatch.h declares (checked by the CPU tests).
+EXPORTS = [
+    "cm_version", "cm_last_error", "cm_params_default", "cm_params_check", "cm_make_weights", "cm_image_bytes",
+    "cm_index_bytes", "cm_schedule_blocks", "cm_schedule_num_rows", "cm_schedule_num_iterations",
+    "cm_schedule_get_row", "cm_free_schedule", "cm_gps_order", "cm_index_create", "cm_index_set_mean",
+    "cm_index_mean_device", "cm_index_col_sums", "cm_index_load", "cm_index_rehash", "cm_index_evict", "cm_build_index",
+    "cm_index_image_view", "cm_index_destroy", "cm_match_plan_create", "cm_match_plan_rows", "cm_match_plan_run",
+    "cm_match_plan_destroy", "cm_match_pairs",
+]
+
+
+class CMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("cashmatch error %d: %s" % (status, msg))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("m", ctypes.c_int32), ("n_bits", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("ratio_num", ctypes.c_int32), ("ratio_den", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("rerank", ctypes.c_int32), ("query_tile", ctypes.c_int32)]
+
+    @classmethod
+    def make(cls, L=6, m=8, K=8, ratio=(4, 5), seed=0x5EED, rerank="fp32", query_tile=0, n_bits=128):
+        return cls(L, m, n_bits, K, ratio[0], ratio[1], seed, RERANK[rerank] if isinstance(rerank, str) else rerank,
+                   query_tile)
+
+    @property
+    def P(self):
+        return self.L * self.m + self.n_bits
+
+
+class MatchOut(ctypes.Structure):
+    _fields_ = [("best_j", ctypes.c_void_p), ("d1sq", ctypes.c_void_p), ("d2sq", ctypes.c_void_p),
+                ("topk", ctypes.c_void_p), ("stats", ctypes.c_void_p)]
+
+
+class ScheduleRow(ctypes.Structure):
+    _fields_ = [("iteration", ctypes.c_int32), ("n_load", ctypes.c_int32), ("load", ctypes.POINTER(ctypes.c_int32)),
+                ("n_free", ctypes.c_int32), ("free_ids", ctypes.POINTER(ctypes.c_int32)),
+                ("n_pairs", ctypes.c_int64), ("pairs", ctypes.POINTER(ctypes.c_int64))]
+
+
+_lib = None
+
+
+def lib():
+    """Load libcashmatch.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libcashmatch.so is not built: run python -m paper_2505_22089_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+        P = ctypes.POINTER(Params)
+        sig = {
+            "cm_version": (ctypes.c_char_p, []),
+            "cm_last_error": (ctypes.c_char_p, []),
+            "cm_params_default": (i32, [P]),
+            "cm_params_check": (i32, [P]),
+            "cm_make_weights": (i32, [P, vp]),
+            "cm_image_bytes": (i32, [P, i32, ctypes.POINTER(u64)]),
+            "cm_index_bytes": (i32, [P, i32, vp, i32, ctypes.POINTER(u64)]),
+            "cm_schedule_blocks": (i32, [vp, i64, i32, vp, P, u64, i32, ctypes.POINTER(vp)]),
+            "cm_schedule_num_rows": (i32, [vp]),
+            "cm_schedule_num_iterations": (i32, [vp]),
+            "cm_schedule_get_row": (i32, [vp, i32, ctypes.POINTER(ScheduleRow)]),
+            "cm_free_schedule": (None, [vp]),
+            "cm_gps_order": (i32, [i32, i64, vp, vp, ctypes.POINTER(i32)]),
+            "cm_index_create": (i32, [P, i32, vp, vp, u64, ctypes.POINTER(vp)]),
+            "cm_index_set_mean": (i32, [vp, vp, u64, vp]),
+            "cm_index_mean_device": (i32, [vp, vp, u64, vp]),
+            "cm_index_col_sums": (i32, [vp, vp, ctypes.POINTER(u64), vp]),
+            "cm_index_load": (i32, [vp, i32, vp, vp, i32, vp]),
+            "cm_index_rehash": (i32, [vp, vp]),
+            "cm_index_evict": (i32, [vp, i32, vp, vp]),
+            "cm_build_index": (i32, [P, i32, vp, vp, i32, vp, u64, vp, ctypes.POINTER(vp)]),
+            "cm_index_image_view": (i32, [vp, i32] + [ctypes.POINTER(vp)] * 5),
+            "cm_index_destroy": (None, [vp]),
+            "cm_match_plan_create": (i32, [vp, vp, i64, vp, ctypes.POINTER(vp)]),
+            "cm_match_plan_rows": (i64, [vp]),
+            "cm_match_plan_run": (i32, [vp, ctypes.POINTER(MatchOut), vp]),
+            "cm_match_plan_destroy": (None, [vp]),
+            "cm_match_pairs": (i32, [vp, vp, i64, ctypes.POINTER(MatchOut), vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != CM_OK:
+        raise CMError(status, lib().cm_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def version() -> str:
+    return lib().cm_version().decode()
+
+
+def make_weights(p: Params) -> np.ndarray:
+    W = np.empty((128, p.P), dtype=np.float32)
+    check(lib().cm_make_weights(ctypes.byref(p), W.ctypes.data))
+    return W
+
+
+def image_bytes(p: Params, n: int) -> int:
+    b = ctypes.c_uint64()
+    check(lib().cm_image_bytes(ctypes.byref(p), int(n), ctypes.byref(b)))
+    return b.value
+
+
+def index_bytes(p: Params, n_desc, inplace: bool = False) -> int:
+    nd = np.ascontiguousarray(n_desc, dtype=np.int32)
+    b = ctypes.c_uint64()
+    check(lib().cm_index_bytes(ctypes.byref(p), len(nd), nd.ctypes.data, int(inplace), ctypes.byref(b)))
+    return b.value
+
+
+def gps_order(n: int, edges) -> list:
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    order = np.empty(max(n, 1), dtype=np.int32)
+    cnt = ctypes.c_int32()
+    check(lib().cm_gps_order(n, e.shape[0], e.ctypes.data, order.ctypes.data, ctypes.byref(cnt)))
+    return [int(x) for x in order[:cnt.value]]
+
+
+@dataclass
+class Schedule:
+    rows: list
+    iterations: int
+
+
+def schedule_blocks(pairs, n_desc, p: Params, budget: int, max_images_per_block: int) -> Schedule:
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    nd = np.ascontiguousarray(n_desc, dtype=np.int32)
+    h = ctypes.c_void_p()
+    check(lib().cm_schedule_blocks(pr.ctypes.data, pr.shape[0], len(nd), nd.ctypes.data, ctypes.byref(p),
+                                   int(budget), int(max_images_per_block), ctypes.byref(h)))
+    try:
+        rows = []
+        r = ScheduleRow()
+        for k in range(lib().cm_schedule_num_rows(h)):
+            check(lib().cm_schedule_get_row(h, k, ctypes.byref(r)))
+            rows.append({"iteration": r.iteration,
+                         "load": [r.load[q] for q in range(r.n_load)],
+                         "free": [r.free_ids[q] for q in range(r.n_free)],
+                         "pairs": [r.pairs[q] for q in range(r.n_pairs)]})
+        return Schedule(rows, lib().cm_schedule_num_iterations(h))
+    finally:
+        lib().cm_free_schedule(h)
+
+
+def _cudart():
+    import torch  # noqa: F401  (loads the CUDA runtime)
+    for name in ("libcudart.so.13", "libcudart.so"):
+        try:
+            rt = ctypes.CDLL(name)
+            rt.cudaMemcpy.restype = ctypes.c_int
+            rt.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+            return rt
+        except OSError:
+            continue
+    raise RuntimeError("CUDA runtime library not found")
+
+
+def device_to_numpy(ptr: int, shape, dtype) -> np.ndarray:
+    """Copy `shape` elements of `dtype` from a device address into a new numpy array."""
+    import torch
+    torch.cuda.synchronize()
+    out = np.empty(shape, dtype=dtype)
+    if out.nbytes:
+        rc = _cudart().cudaMemcpy(out.ctypes.data, ctypes.c_void_p(ptr), out.nbytes, 2)  # DeviceToHost
+        if rc != 0:
+            raise RuntimeError("cudaMemcpy failed: %d" % rc)
+    return out
+
+
+class Index:
+    """An arena-backed index (cm_index).  The arena is a torch uint8 CUDA tensor."""
+
+    def __init__(self, p: Params, n_desc, arena_bytes: int | None = None, inplace: bool = False, device="cuda",
+                 arena=None):
+        """Empty index.  `arena` (optional) is a CUDA uint8 tensor to use as the
+        device arena; otherwise one of `arena_bytes` (default: room for every
+        image) is allocated."""
+        import torch
+        self.p = p
+        self.n_desc = np.ascontiguousarray(n_desc, dtype=np.int32)
+        if arena is None:
+            if arena_bytes is None:
+                arena_bytes = index_bytes(p, self.n_desc, inplace)
+            arena = torch.empty(int(arena_bytes) + 256, dtype=torch.uint8, device=device)
+        self.arena = arena
+        base = (self.arena.data_ptr() + 255) // 256 * 256
+        arena_bytes = self.arena.numel() - (base - self.arena.data_ptr())
+        self.h = ctypes.c_void_p()
+        check(lib().cm_index_create(ctypes.byref(p), len(self.n_desc), self.n_desc.ctypes.data,
+                                    ctypes.c_void_p(base), int(arena_bytes), ctypes.byref(self.h)))
+        self._keep = []
+        self._plans = []
+
+    @classmethod
+    def build(cls, p: Params, n_desc, desc, mem: int | None = None, stream=None, arena_bytes: int | None = None):
+        """Index with every image resident.  `desc` = all rows concatenated: a CUDA
+        uint8 tensor (used in place unless mem says otherwise) or a host array/tensor."""
+        import torch
+        self = cls.__new__(cls)
+        self.p = p
+        self.n_desc = np.ascontiguousarray(n_desc, dtype=np.int32)
+        on_dev = isinstance(desc, torch.Tensor) and desc.is_cuda
+        if mem is None:
+            mem = MEM_DEVICE_INPLACE if on_dev else MEM_HOST
+        if arena_bytes is None:
+            arena_bytes = index_bytes(p, self.n_desc, mem == MEM_DEVICE_INPLACE)
+        self.arena = torch.empty(int(arena_bytes) + 256, dtype=torch.uint8, device="cuda")
+        base = (self.arena.data_ptr() + 255) // 256 * 256
+        ptr = desc.data_ptr() if isinstance(desc, torch.Tensor) else np.ascontiguousarray(desc).ctypes.data
+        self._keep = [desc]
+        self._plans = []
+        self.h = ctypes.c_void_p()
+        check(lib().cm_build_index(ctypes.byref(p), len(self.n_desc), self.n_desc.ctypes.data, ctypes.c_void_p(ptr),
+                                   mem, ctypes.c_void_p(base), int(arena_bytes), _stream(stream),
+                                   ctypes.byref(self.h)))
+        return self
+
+    def set_mean(self, sums, n_total: int, stream=None):
+        s = np.ascontiguousarray(sums, dtype=np.uint64)
+        check(lib().cm_index_set_mean(self.h, s.ctypes.data, int(n_total), _stream(stream)))
+
+    def mean_device(self, desc, stream=None):
+        check(lib().cm_index_mean_device(self.h, _ptr(desc), desc.shape[0], _stream(stream)))
+
+    def col_sums(self, stream=None):
+        """(exact uint64 column sums, row count) behind the current centring mean."""
+        s = np.zeros(128, dtype=np.uint64)
+        n = ctypes.c_uint64()
+        check(lib().cm_index_col_sums(self.h, s.ctypes.data, ctypes.byref(n), _stream(stream)))
+        return s, n.value
+
+    def load(self, ids, descs, mem: int, stream=None):
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        ptrs = (ctypes.c_void_p * len(ids))(*[d.data_ptr() if hasattr(d, "data_ptr") else
+                                               np.ascontiguousarray(d).ctypes.data for d in descs])
+        self._keep += list(descs)
+        check(lib().cm_index_load(self.h, len(ids), ids.ctypes.data, ptrs, mem, _stream(stream)))
+
+    def evict(self, ids, stream=None):
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        check(lib().cm_index_evict(self.h, len(ids), ids.ctypes.data, _stream(stream)))
+
+    def rehash(self, stream=None):
+        check(lib().cm_index_rehash(self.h, _stream(stream)))
+
+    def image_view(self, image: int) -> dict:
+        """Copies of a resident image's keys, codes and bucket tables (host numpy)."""
+        ptrs = [ctypes.c_void_p() for _ in range(5)]
+        check(lib().cm_index_image_view(self.h, image, *[ctypes.byref(x) for x in ptrs]))
+        n, L, B = int(self.n_desc[image]), self.p.L, 1 << self.p.m
+        keyw = device_to_numpy(ptrs[0].value, (n,), np.uint64)
+        keys = np.stack([(keyw >> np.uint64(8 * t)) & np.uint64(0xFF) for t in range(L)], 1).astype(np.uint8) \
+            if n else np.zeros((0, L), np.uint8)
+        return {"keys": keys,
+                "code": device_to_numpy(ptrs[1].value, (n, 4), np.uint32),
+                "scode": device_to_numpy(ptrs[2].value, (L, n, 4), np.uint32),
+                "sidx": device_to_numpy(ptrs[3].value, (L, n), np.uint16),
+                "off": device_to_numpy(ptrs[4].value, (L, B + 1), np.uint32)}
+
+    def close(self):
+        for ref in getattr(self, "_plans", []):
+            pl = ref()
+            if pl is not None:
+                pl.close()
+        if getattr(self, "h", None):
+            lib().cm_index_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MatchPlan:
+    """cm_match_plan over a list of pairs of resident images."""
+
+    def __init__(self, index: Index, pairs, stream=None):
+        self.index = index
+        self.pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        self.h = ctypes.c_void_p()
+        check(lib().cm_match_plan_create(index.h, self.pairs.ctypes.data, self.pairs.shape[0], _stream(stream),
+                                         ctypes.byref(self.h)))
+        self.rows = int(lib().cm_match_plan_rows(self.h))
+        index._plans.append(weakref.ref(self))
+        nd = index.n_desc[self.pairs[:, 0]].astype(np.int64) if len(self.pairs) else np.zeros(0, np.int64)
+        self.row_off = np.concatenate([[0], np.cumsum(nd)]).astype(np.int64)
+
+    def alloc_out(self, d12: bool = True, topk: bool = False, stats: bool = True):
+        import torch
+        n = max(self.rows, 1)
+        out = {"best_j": torch.empty(n, dtype=torch.int32, device="cuda")}
+        if d12:
+            out["d1sq"] = torch.empty(n, dtype=torch.int32, device="cuda")
+            out["d2sq"] = torch.empty(n, dtype=torch.int32, device="cuda")
+        if topk:
+            out["topk"] = torch.empty(n * self.index.p.K, dtype=torch.int32, device="cuda")
+        if stats:
+            out["stats"] = torch.zeros(4, dtype=torch.int32, device="cuda")
+        return out
+
+    def run(self, out: dict, stream=None):
+        mo = MatchOut(*[ctypes.c_void_p(out[k].data_ptr()) if out.get(k) is not None else None
+                        for k in ("best_j", "d1sq", "d2sq", "topk", "stats")])
+        check(lib().cm_match_plan_run(self.h, ctypes.byref(mo), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cm_match_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,755 @@
+// C-ABI entry points: parameters, projection weights, the arena-backed index,
+// match plans.  Host C++; device work is enqueued through the launchers of
+// cm_kernels.cu.  See include/cashmatch.h for the contract of each call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "cm_internal.h"
+
+using namespace cm;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static cm_status fail(cm_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CM_CUDA(call)                                                                               \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return fail(CM_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                           __FILE__, __LINE__);                                     \
+    } while (0)
+
+extern "C" const char* cm_version(void) { return "cashmatch 0.1 (sm_103a)"; }
+extern "C" cm_status cm_internal_fail(cm_status st, const char* msg) { return fail(st, "%s", msg); }
+extern "C" const char* cm_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// parameters
+// ---------------------------------------------------------------------------
+extern "C" cm_status cm_params_default(cm_params* p) {
+    if (!p) return fail(CM_ERR_INVALID, "cm_params_default: NULL");
+    p->L = 6;
+    p->m = 8;
+    p->n_bits = 128;
+    p->K = 8;
+    p->ratio_num = 4;
+    p->ratio_den = 5;
+    p->seed = 0x5EED;
+    p->rerank = CM_RERANK_FP32;
+    p->query_tile = 0;
+    return CM_OK;
+}
+
+extern "C" cm_status cm_params_check(const cm_params* p) {
+    if (!p) return fail(CM_ERR_INVALID, "params: NULL");
+    if (p->L < 1 || p->L > kMaxL) return fail(CM_ERR_INVALID, "params: L=%d not in 1..8", p->L);
+    if (p->m < 0 || p->m > kMaxM) return fail(CM_ERR_INVALID, "params: m=%d not in 0..8", p->m);
+    if (p->n_bits != 128) return fail(CM_ERR_INVALID, "params: n_bits=%d, only 128 is supported", p->n_bits);
+    if (p->K != 2 && p->K != 4 && p->K != 8 && p->K != 16)
+        return fail(CM_ERR_INVALID, "params: K=%d not in {2,4,8,16}", p->K);
+    if (p->ratio_den < 1 || p->ratio_num < 0 || p->ratio_num > 4 * p->ratio_den)
+        return fail(CM_ERR_INVALID, "params: ratio %d/%d out of range", p->ratio_num, p->ratio_den);
+    if (p->rerank != CM_RERANK_FP32 && p->rerank != CM_RERANK_INT)
+        return fail(CM_ERR_INVALID, "params: rerank mode %d not available", p->rerank);
+    if (p->query_tile != 0 && (p->query_tile < 64 || p->query_tile > 8192 || p->query_tile % 64))
+        return fail(CM_ERR_INVALID, "params: query_tile=%d must be 0 or a multiple of 64 in 64..8192",
+                    p->query_tile);
+    const int S = p->query_tile ? p->query_tile : kDefaultQueryTile;
+    if (match_smem_bytes(S, p->K) > 227 * 1024)
+        return fail(CM_ERR_INVALID, "params: query_tile=%d with K=%d needs %zu bytes of shared memory (> 227 KB)", S,
+                    p->K, match_smem_bytes(S, p->K));
+    return CM_OK;
+}
+
+static int proj_count(const cm_params* p) { return p->L * p->m + p->n_bits; }
+static int proj_pad(const cm_params* p) { return (proj_count(p) + 15) / 16 * 16; }
+static int query_tile(const cm_params* p) { return p->query_tile ? p->query_tile : kDefaultQueryTile; }
+
+// ---------------------------------------------------------------------------
+// projection weights: splitmix64 stream -> Box-Muller pairs -> float
+// ---------------------------------------------------------------------------
+namespace {
+struct SplitMix64 {
+    uint64_t x;
+    uint64_t operator()() {
+        x += 0x9E3779B97F4A7C15ull;
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+};
+}  // namespace
+
+extern "C" cm_status cm_make_weights(const cm_params* p, float* W) {
+    cm_status st = cm_params_check(p);
+    if (st != CM_OK) return st;
+    if (!W) return fail(CM_ERR_INVALID, "cm_make_weights: NULL output");
+    const int64_t n = (int64_t)kDim * proj_count(p);
+    SplitMix64 g{p->seed};
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    const double inv53 = 1.0 / 9007199254740992.0;
+    for (int64_t e = 0; e < n; e += 2) {
+        const uint64_t a = g(), b = g();
+        const double u1 = (double)((a >> 11) + 1) * inv53;
+        const double u2 = (double)(b >> 11) * inv53;
+        const double radius = std::sqrt(-2.0 * std::log(u1));
+        const double angle = two_pi * u2;
+        W[e] = (float)(radius * std::cos(angle));
+        if (e + 1 < n) W[e + 1] = (float)(radius * std::sin(angle));
+    }
+    return CM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// arena layout
+// ---------------------------------------------------------------------------
+namespace {
+constexpr uint64_t kAlign = 256;
+inline uint64_t align_up(uint64_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct SlotLayout {
+    uint64_t desc, key, code, scode, sidx, off, hist, norm, xq, xscale, total;
+};
+
+SlotLayout slot_layout(const cm_params* p, int64_t n, bool inplace) {
+    const int64_t B = 1ll << p->m;
+    SlotLayout s{};
+    uint64_t o = 0;
+    auto take = [&](uint64_t bytes) { uint64_t at = o; o = align_up(o + bytes); return at; };
+    s.desc = inplace ? 0 : take((uint64_t)n * kDim);
+    s.key = take((uint64_t)n * 8);
+    s.code = take((uint64_t)n * 16);
+    s.scode = take((uint64_t)p->L * n * 16);
+    s.sidx = take((uint64_t)p->L * n * 2);
+    s.off = take((uint64_t)p->L * (B + 1) * 4);
+    s.hist = take((uint64_t)p->L * B * 4);
+    s.norm = take((uint64_t)n * 4);
+    const uint64_t xq_bytes = p->rerank == CM_RERANK_BF16 ? 256 : (p->rerank == CM_RERANK_FP8 ? 128 : 0);
+    s.xq = xq_bytes ? take((uint64_t)n * xq_bytes) : 0;
+    s.xscale = p->rerank == CM_RERANK_FP8 ? take((uint64_t)n * 4) : 0;
+    s.total = o;
+    return s;
+}
+
+// Fixed tables at the start of the arena.
+struct FixedLayout {
+    uint64_t imgs, W, mu, sums, ntot, batch, tiles, rbatch, rtiles, total;
+};
+
+FixedLayout fixed_layout(const cm_params* p, int n_images) {
+    FixedLayout f{};
+    uint64_t o = 0;
+    auto take = [&](uint64_t bytes) { uint64_t at = o; o = align_up(o + bytes); return at; };
+    f.imgs = take((uint64_t)n_images * sizeof(DevImage));
+    f.W = take((uint64_t)kDim * proj_pad(p) * 4);
+    f.mu = take(kDim * 4);
+    f.sums = take(kDim * 8);
+    f.ntot = take(8);
+    f.batch = take((uint64_t)n_images * 4);
+    f.tiles = take((uint64_t)(n_images + 1) * 4);
+    f.rbatch = take((uint64_t)n_images * 4);
+    f.rtiles = take((uint64_t)(n_images + 1) * 4);
+    f.total = o;
+    return f;
+}
+
+// First-fit allocator over [begin, end) of the arena (host bookkeeping only).
+class ArenaAlloc {
+   public:
+    void init(uint64_t begin, uint64_t end) {
+        free_.clear();
+        if (end > begin) free_[begin] = end - begin;
+    }
+    bool alloc(uint64_t bytes, uint64_t* at) {
+        bytes = align_up(bytes ? bytes : kAlign);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *at = it->first;
+                const uint64_t rest = it->second - bytes, base = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[base] = rest;
+                used_[*at] = bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(uint64_t at) {
+        auto u = used_.find(at);
+        if (u == used_.end()) return;
+        uint64_t base = at, size = u->second;
+        used_.erase(u);
+        auto next = free_.lower_bound(base);
+        if (next != free_.end() && base + size == next->first) {
+            size += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == base) {
+                prev->second += size;
+                return;
+            }
+        }
+        free_[base] = size;
+    }
+
+   private:
+    std::map<uint64_t, uint64_t> free_, used_;
+};
+
+// Pinned host buffers for table uploads; a buffer is reused once the copy that
+// read it has completed on its stream.
+class Staging {
+   public:
+    ~Staging() {
+        for (auto& b : bufs_) {
+            cudaEventDestroy(b.ev);
+            cudaFreeHost(b.p);
+        }
+    }
+    cudaError_t upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+        if (!bytes) return cudaSuccess;
+        Buf* use = nullptr;
+        for (auto& b : bufs_) {
+            if (b.cap >= bytes && (!b.pending || cudaEventQuery(b.ev) == cudaSuccess)) {
+                use = &b;
+                break;
+            }
+        }
+        if (!use) {
+            Buf b{};
+            b.cap = std::max<size_t>(bytes, 1 << 16);
+            cudaError_t e = cudaHostAlloc(&b.p, b.cap, cudaHostAllocDefault);
+            if (e != cudaSuccess) return e;
+            e = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+            bufs_.push_back(b);
+            use = &bufs_.back();
+        }
+        memcpy(use->p, src, bytes);
+        cudaError_t e = cudaMemcpyAsync(dst, use->p, bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+        e = cudaEventRecord(use->ev, s);
+        use->pending = true;
+        return e;
+    }
+
+   private:
+    struct Buf {
+        void* p;
+        size_t cap;
+        cudaEvent_t ev;
+        bool pending;
+    };
+    std::vector<Buf> bufs_;
+};
+}  // namespace
+
+extern "C" cm_status cm_image_bytes(const cm_params* p, int32_t n_desc, uint64_t* bytes) {
+    cm_status st = cm_params_check(p);
+    if (st != CM_OK) return st;
+    if (!bytes || n_desc < 0 || n_desc > 65535) return fail(CM_ERR_INVALID, "cm_image_bytes: bad argument");
+    *bytes = slot_layout(p, n_desc, false).total;
+    return CM_OK;
+}
+
+extern "C" cm_status cm_index_bytes(const cm_params* p, int32_t n_images, const int32_t* n_desc, int32_t inplace,
+                                    uint64_t* bytes) {
+    cm_status st = cm_params_check(p);
+    if (st != CM_OK) return st;
+    if (!bytes || n_images < 0 || (n_images && !n_desc)) return fail(CM_ERR_INVALID, "cm_index_bytes: bad argument");
+    uint64_t t = fixed_layout(p, n_images).total;
+    for (int i = 0; i < n_images; ++i) {
+        if (n_desc[i] < 0 || n_desc[i] > 65535) return fail(CM_ERR_INVALID, "image %d: %d descriptors", i, n_desc[i]);
+        t += slot_layout(p, n_desc[i], inplace != 0).total;
+    }
+    *bytes = t + 64 * kAlign;
+    return CM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// index
+// ---------------------------------------------------------------------------
+struct cm_match_plan;
+
+struct cm_index {
+    cm_params p{};
+    std::set<cm_match_plan*> plans;    // live plans (detached when the index is destroyed)
+    int P = 0, P_pad = 0, B = 0, sms = 148;
+    int n_images = 0;
+    std::vector<int32_t> n_desc;
+    uint8_t* arena = nullptr;
+    uint64_t arena_bytes = 0;
+    FixedLayout fx{};
+    ArenaAlloc alloc;
+    std::vector<DevImage> h_imgs;
+    std::vector<uint64_t> slot_at;     // arena offset of each image's slot (valid if resident)
+    std::vector<char> resident;
+    bool mean_set = false;
+    bool sums_on_host = false;         // the mean came from cm_index_set_mean
+    uint64_t host_sums[kDim] = {};
+    uint64_t n_total = 0;              // rows behind the current mean
+    Staging staging;
+
+    template <class T>
+    T* at(uint64_t off) const { return reinterpret_cast<T*>(arena + off); }
+
+    HashLaunch hash_launch(bool resident_set, int n_batch, int n_tiles) const {
+        HashLaunch h{};
+        h.imgs = at<DevImage>(fx.imgs);
+        h.batch = at<int32_t>(resident_set ? fx.rbatch : fx.batch);
+        h.tile_pref = at<int32_t>(resident_set ? fx.rtiles : fx.tiles);
+        h.n_batch = n_batch;
+        h.n_tiles = n_tiles;
+        h.W = at<float>(fx.W);
+        h.mu = at<float>(fx.mu);
+        h.L = p.L;
+        h.m = p.m;
+        h.P_pad = P_pad;
+        h.rerank = p.rerank;
+        return h;
+    }
+};
+
+struct cm_match_plan {
+    cm_index* ix = nullptr;
+    uint64_t table_at = 0;   // arena offset: [n_pairs] DevPair, then the work counter
+    int64_t n_pairs = 0;
+    int64_t rows = 0;
+    int32_t n_items = 0;
+};
+
+static cm_status upload_table(cm_index* ix, uint64_t off, const void* src, size_t bytes, cudaStream_t s) {
+    CM_CUDA(ix->staging.upload(ix->arena + off, src, bytes, s));
+    return CM_OK;
+}
+
+extern "C" cm_status cm_index_create(const cm_params* p, int32_t n_images, const int32_t* n_desc, void* d_arena,
+                                     uint64_t arena_bytes, cm_index** out) {
+    cm_status st = cm_params_check(p);
+    if (st != CM_OK) return st;
+    if (!out || !d_arena || n_images < 1 || !n_desc) return fail(CM_ERR_INVALID, "cm_index_create: bad argument");
+    if (reinterpret_cast<uintptr_t>(d_arena) % kAlign) return fail(CM_ERR_INVALID, "arena must be 256-byte aligned");
+    for (int i = 0; i < n_images; ++i)
+        if (n_desc[i] < 0 || n_desc[i] > 65535)
+            return fail(CM_ERR_INVALID, "image %d has %d descriptors (0..65535 supported)", i, n_desc[i]);
+    cm_index* ix = new (std::nothrow) cm_index();
+    if (!ix) return fail(CM_ERR_NOMEM, "cm_index_create: host allocation");
+    ix->p = *p;
+    ix->P = proj_count(p);
+    ix->P_pad = proj_pad(p);
+    ix->B = 1 << p->m;
+    ix->n_images = n_images;
+    ix->n_desc.assign(n_desc, n_desc + n_images);
+    ix->arena = static_cast<uint8_t*>(d_arena);
+    ix->arena_bytes = arena_bytes;
+    ix->fx = fixed_layout(p, n_images);
+    if (ix->fx.total > arena_bytes) {
+        const unsigned long long need = ix->fx.total;
+        delete ix;
+        return fail(CM_ERR_BUDGET, "arena of %llu bytes is smaller than the index tables (%llu)",
+                    (unsigned long long)arena_bytes, need);
+    }
+    ix->alloc.init(ix->fx.total, arena_bytes);
+    ix->h_imgs.assign(n_images, DevImage{});
+    for (int i = 0; i < n_images; ++i) ix->h_imgs[i].n = n_desc[i];
+    ix->slot_at.assign(n_images, 0);
+    ix->resident.assign(n_images, 0);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&ix->sms, cudaDevAttrMultiProcessorCount, dev);
+    // weights, zero-padded to P_pad columns
+    std::vector<float> W((size_t)kDim * ix->P), Wp((size_t)kDim * ix->P_pad, 0.f);
+    cm_make_weights(p, W.data());
+    for (int k = 0; k < kDim; ++k)
+        for (int h = 0; h < ix->P; ++h) Wp[(size_t)k * ix->P_pad + h] = W[(size_t)k * ix->P + h];
+    cudaError_t e = cudaMemcpy(ix->arena + ix->fx.W, Wp.data(), Wp.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ix->arena + ix->fx.imgs, ix->h_imgs.data(), ix->h_imgs.size() * sizeof(DevImage),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        delete ix;
+        return fail(CM_ERR_CUDA, "cm_index_create: %s", cudaGetErrorString(e));
+    }
+    *out = ix;
+    return CM_OK;
+}
+
+extern "C" void cm_index_destroy(cm_index* ix);
+
+extern "C" cm_status cm_index_set_mean(cm_index* ix, const uint64_t* sums, uint64_t n_total, cm_stream stream) {
+    if (!ix || !sums || !n_total) return fail(CM_ERR_INVALID, "cm_index_set_mean: bad argument");
+    float mu[kDim];
+    for (int k = 0; k < kDim; ++k) mu[k] = (float)((double)sums[k] / (double)n_total);
+    cm_status st = upload_table(ix, ix->fx.mu, mu, sizeof mu, reinterpret_cast<cudaStream_t>(stream));
+    if (st == CM_OK) {
+        ix->mean_set = true;
+        ix->sums_on_host = true;
+        std::copy(sums, sums + kDim, ix->host_sums);
+        ix->n_total = n_total;
+    }
+    return st;
+}
+
+extern "C" cm_status cm_index_col_sums(cm_index* ix, uint64_t* sums, uint64_t* n_total, cm_stream stream) {
+    if (!ix || !sums) return fail(CM_ERR_INVALID, "cm_index_col_sums: bad argument");
+    if (!ix->mean_set) return fail(CM_ERR_STATE, "cm_index_col_sums: no centring mean yet");
+    if (ix->sums_on_host) {
+        std::copy(ix->host_sums, ix->host_sums + kDim, sums);
+    } else {
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        CM_CUDA(cudaMemcpyAsync(sums, ix->arena + ix->fx.sums, kDim * 8, cudaMemcpyDeviceToHost, s));
+        CM_CUDA(cudaStreamSynchronize(s));
+    }
+    if (n_total) *n_total = ix->n_total;
+    return CM_OK;
+}
+
+extern "C" cm_status cm_index_mean_device(cm_index* ix, const uint8_t* d_desc, uint64_t n_rows, cm_stream stream) {
+    if (!ix || (!d_desc && n_rows) || !n_rows) return fail(CM_ERR_INVALID, "cm_index_mean_device: bad argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long* sums = ix->at<unsigned long long>(ix->fx.sums);
+    CM_CUDA(cudaMemsetAsync(sums, 0, kDim * 8, s));
+    CM_CUDA(launch_colsum_rows(d_desc, n_rows, sums, s));
+    CM_CUDA(launch_mean(sums, nullptr, n_rows, ix->at<float>(ix->fx.mu), s));
+    ix->mean_set = true;
+    ix->sums_on_host = false;
+    ix->n_total = n_rows;
+    return CM_OK;
+}
+
+// Allocate slots, copy descriptors, refresh the device image table and the
+// load-batch table.  Returns the batch's hash-tile count.
+static cm_status stage_images(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc,
+                              int32_t mem, cudaStream_t s, int* n_tiles_out) {
+    if (count < 0 || (count && (!ids || !desc))) return fail(CM_ERR_INVALID, "load: bad argument");
+    if (mem != CM_MEM_HOST && mem != CM_MEM_DEVICE && mem != CM_MEM_DEVICE_INPLACE)
+        return fail(CM_ERR_INVALID, "load: bad memory kind %d", mem);
+    std::vector<char> seen(ix->n_images, 0);
+    for (int k = 0; k < count; ++k) {
+        const int i = ids[k];
+        if (i < 0 || i >= ix->n_images) return fail(CM_ERR_INVALID, "load: image id %d out of range", i);
+        if (ix->resident[i] || seen[i]) return fail(CM_ERR_STATE, "load: image %d is already resident", i);
+        if (!desc[k] && ix->n_desc[i]) return fail(CM_ERR_INVALID, "load: NULL descriptors for image %d", i);
+        seen[i] = 1;
+    }
+    const bool inplace = mem == CM_MEM_DEVICE_INPLACE;
+    std::vector<int32_t> batch(count), tiles(count + 1, 0);
+    int k_done = 0;
+    for (int k = 0; k < count; ++k, ++k_done) {
+        const int i = ids[k];
+        const int64_t n = ix->n_desc[i];
+        const SlotLayout L = slot_layout(&ix->p, n, inplace);
+        uint64_t at = 0;
+        if (!ix->alloc.alloc(L.total, &at)) {
+            for (int r = 0; r < k_done; ++r) {  // roll back this call's slots
+                ix->alloc.release(ix->slot_at[ids[r]]);
+                ix->resident[ids[r]] = 0;
+            }
+            return fail(CM_ERR_BUDGET, "load: arena full while placing image %d (%llu bytes)", i,
+                        (unsigned long long)L.total);
+        }
+        uint8_t* base = ix->arena + at;
+        DevImage& e = ix->h_imgs[i];
+        e.n = (int32_t)n;
+        e.desc = inplace ? desc[k] : base + L.desc;
+        e.key = reinterpret_cast<uint64_t*>(base + L.key);
+        e.code = reinterpret_cast<uint4*>(base + L.code);
+        e.scode = reinterpret_cast<uint4*>(base + L.scode);
+        e.sidx = reinterpret_cast<uint16_t*>(base + L.sidx);
+        e.off = reinterpret_cast<uint32_t*>(base + L.off);
+        e.hist = reinterpret_cast<uint32_t*>(base + L.hist);
+        e.norm = reinterpret_cast<uint32_t*>(base + L.norm);
+        e.xq = L.xq ? base + L.xq : nullptr;
+        e.xscale = L.xscale ? reinterpret_cast<float*>(base + L.xscale) : nullptr;
+        ix->slot_at[i] = at;
+        ix->resident[i] = 1;
+        batch[k] = i;
+        tiles[k + 1] = tiles[k] + (int)((n + kHashTile - 1) / kHashTile);
+        if (!inplace && n) {
+            const cudaMemcpyKind kind = mem == CM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+            CM_CUDA(cudaMemcpyAsync(base + L.desc, desc[k], (size_t)n * kDim, kind, s));
+        }
+        CM_CUDA(cudaMemsetAsync(e.hist, 0, (size_t)ix->p.L * ix->B * 4, s));
+    }
+    cm_status st = upload_table(ix, ix->fx.imgs, ix->h_imgs.data(), ix->h_imgs.size() * sizeof(DevImage), s);
+    if (st == CM_OK) st = upload_table(ix, ix->fx.batch, batch.data(), batch.size() * 4, s);
+    if (st == CM_OK) st = upload_table(ix, ix->fx.tiles, tiles.data(), tiles.size() * 4, s);
+    if (st != CM_OK) return st;
+    *n_tiles_out = tiles[count];
+    return CM_OK;
+}
+
+// The resident-set table used by cm_index_rehash.
+static cm_status refresh_resident(cm_index* ix, cudaStream_t s, int* n_batch, int* n_tiles, uint64_t* rows) {
+    std::vector<int32_t> batch, tiles(1, 0);
+    uint64_t r = 0;
+    for (int i = 0; i < ix->n_images; ++i) {
+        if (!ix->resident[i]) continue;
+        batch.push_back(i);
+        tiles.push_back(tiles.back() + (ix->n_desc[i] + kHashTile - 1) / kHashTile);
+        r += (uint64_t)ix->n_desc[i];
+    }
+    cm_status st = upload_table(ix, ix->fx.rbatch, batch.data(), batch.size() * 4, s);
+    if (st == CM_OK) st = upload_table(ix, ix->fx.rtiles, tiles.data(), tiles.size() * 4, s);
+    *n_batch = (int)batch.size();
+    *n_tiles = tiles.back();
+    *rows = r;
+    return st;
+}
+
+static cm_status hash_batch(cm_index* ix, const HashLaunch& h, cudaStream_t s) {
+    if (h.n_batch == 0) return CM_OK;
+    CM_CUDA(launch_hash(h, ix->sms, s));
+    CM_CUDA(launch_bucket(h, s));
+    return CM_OK;
+}
+
+extern "C" cm_status cm_index_load(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc,
+                                   int32_t mem, cm_stream stream) {
+    if (!ix) return fail(CM_ERR_INVALID, "cm_index_load: NULL index");
+    if (!ix->mean_set) return fail(CM_ERR_STATE, "cm_index_load: centring mean not set");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int n_tiles = 0;
+    cm_status st = stage_images(ix, count, ids, desc, mem, s, &n_tiles);
+    if (st != CM_OK) return st;
+    int rb = 0, rt = 0;
+    uint64_t rows = 0;
+    st = refresh_resident(ix, s, &rb, &rt, &rows);
+    if (st != CM_OK) return st;
+    return hash_batch(ix, ix->hash_launch(false, count, n_tiles), s);
+}
+
+extern "C" cm_status cm_index_rehash(cm_index* ix, cm_stream stream) {
+    if (!ix) return fail(CM_ERR_INVALID, "cm_index_rehash: NULL index");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int nb = 0, nt = 0;
+    uint64_t rows = 0;
+    // the resident table is current after every load/evict; recount on the host only
+    for (int i = 0; i < ix->n_images; ++i)
+        if (ix->resident[i]) {
+            ++nb;
+            nt += (ix->n_desc[i] + kHashTile - 1) / kHashTile;
+            rows += (uint64_t)ix->n_desc[i];
+        }
+    if (!nb) return fail(CM_ERR_STATE, "cm_index_rehash: no resident image");
+    const HashLaunch h = ix->hash_launch(true, nb, nt);
+    unsigned long long* sums = ix->at<unsigned long long>(ix->fx.sums);
+    CM_CUDA(cudaMemsetAsync(sums, 0, kDim * 8, s));
+    CM_CUDA(launch_colsum_images(h, sums, s));
+    CM_CUDA(launch_mean(sums, nullptr, rows, ix->at<float>(ix->fx.mu), s));
+    ix->mean_set = true;
+    ix->sums_on_host = false;
+    ix->n_total = rows;
+    return hash_batch(ix, h, s);
+}
+
+extern "C" cm_status cm_index_evict(cm_index* ix, int32_t count, const int32_t* ids, cm_stream stream) {
+    if (!ix || count < 0 || (count && !ids)) return fail(CM_ERR_INVALID, "cm_index_evict: bad argument");
+    for (int k = 0; k < count; ++k) {
+        const int i = ids[k];
+        if (i < 0 || i >= ix->n_images) return fail(CM_ERR_INVALID, "evict: image id %d out of range", i);
+        if (!ix->resident[i]) return fail(CM_ERR_STATE, "evict: image %d is not resident", i);
+    }
+    for (int k = 0; k < count; ++k) {
+        const int i = ids[k];
+        ix->alloc.release(ix->slot_at[i]);
+        ix->resident[i] = 0;
+        DevImage& e = ix->h_imgs[i];
+        const int n = e.n;
+        e = DevImage{};
+        e.n = n;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cm_status st = upload_table(ix, ix->fx.imgs, ix->h_imgs.data(), ix->h_imgs.size() * sizeof(DevImage), s);
+    int rb = 0, rt = 0;
+    uint64_t rows = 0;
+    if (st == CM_OK) st = refresh_resident(ix, s, &rb, &rt, &rows);
+    return st;
+}
+
+extern "C" cm_status cm_build_index(const cm_params* p, int32_t n_images, const int32_t* n_desc,
+                                    const uint8_t* desc, int32_t mem, void* d_arena, uint64_t arena_bytes,
+                                    cm_stream stream, cm_index** out) {
+    if (!out || !desc) return fail(CM_ERR_INVALID, "cm_build_index: bad argument");
+    cm_index* ix = nullptr;
+    cm_status st = cm_index_create(p, n_images, n_desc, d_arena, arena_bytes, &ix);
+    if (st != CM_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<int32_t> ids(n_images);
+    std::vector<const uint8_t*> ptrs(n_images);
+    uint64_t row = 0;
+    for (int i = 0; i < n_images; ++i) {
+        ids[i] = i;
+        ptrs[i] = desc + row * kDim;
+        row += (uint64_t)n_desc[i];
+    }
+    int n_tiles = 0;
+    st = stage_images(ix, n_images, ids.data(), ptrs.data(), mem, s, &n_tiles);
+    int rb = 0, rt = 0;
+    uint64_t rows = 0;
+    if (st == CM_OK) st = refresh_resident(ix, s, &rb, &rt, &rows);
+    if (st == CM_OK) {
+        // centring mean over every descriptor of the index, then hash all images
+        const HashLaunch h = ix->hash_launch(false, n_images, n_tiles);
+        unsigned long long* sums = ix->at<unsigned long long>(ix->fx.sums);
+        cudaError_t e = cudaMemsetAsync(sums, 0, kDim * 8, s);
+        if (e == cudaSuccess) e = launch_colsum_images(h, sums, s);
+        if (e == cudaSuccess) e = launch_mean(sums, nullptr, rows, ix->at<float>(ix->fx.mu), s);
+        if (e != cudaSuccess) st = fail(CM_ERR_CUDA, "cm_build_index: %s", cudaGetErrorString(e));
+        ix->mean_set = true;
+        ix->n_total = rows;
+        if (st == CM_OK) st = hash_batch(ix, h, s);
+    }
+    if (st != CM_OK) {
+        cm_index_destroy(ix);
+        return st;
+    }
+    *out = ix;
+    return CM_OK;
+}
+
+extern "C" cm_status cm_index_image_view(const cm_index* ix, int32_t image, const void** keys, const void** codes,
+                                         const void** sorted_codes, const void** sorted_idx, const void** offsets) {
+    if (!ix || image < 0 || image >= ix->n_images) return fail(CM_ERR_INVALID, "image_view: bad image");
+    if (!ix->resident[image]) return fail(CM_ERR_STATE, "image_view: image %d not resident", image);
+    const DevImage& e = ix->h_imgs[image];
+    if (keys) *keys = e.key;
+    if (codes) *codes = e.code;
+    if (sorted_codes) *sorted_codes = e.scode;
+    if (sorted_idx) *sorted_idx = e.sidx;
+    if (offsets) *offsets = e.off;
+    return CM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// match plans
+// ---------------------------------------------------------------------------
+extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, cm_stream stream,
+                                          cm_match_plan** out) {
+    if (!ix || !out || n_pairs < 0 || (n_pairs && !pairs)) return fail(CM_ERR_INVALID, "plan: bad argument");
+    const int S = query_tile(&ix->p);
+    std::vector<DevPair> tab((size_t)n_pairs);
+    int64_t rows = 0, items = 0;
+    for (int64_t k = 0; k < n_pairs; ++k) {
+        const int i = pairs[k].i, j = pairs[k].j;
+        if (i < 0 || j < 0 || i >= ix->n_images || j >= ix->n_images)
+            return fail(CM_ERR_INVALID, "plan: pair %lld (%d,%d) has an image id out of range", (long long)k, i, j);
+        if (i == j) return fail(CM_ERR_INVALID, "plan: pair %lld matches image %d with itself", (long long)k, i);
+        if (!ix->resident[i] || !ix->resident[j])
+            return fail(CM_ERR_STATE, "plan: pair %lld (%d,%d) needs an image that is not resident", (long long)k, i,
+                        j);
+        DevPair& d = tab[k];
+        d.i = i;
+        d.j = j;
+        d.row_off = rows;
+        d.item0 = (int32_t)items;
+        d.nitems = (ix->n_desc[i] + S - 1) / S;
+        rows += ix->n_desc[i];
+        items += d.nitems;
+    }
+    if (items > INT32_MAX / 2) return fail(CM_ERR_INVALID, "plan: too many work items");
+    cm_match_plan* pl = new (std::nothrow) cm_match_plan();
+    if (!pl) return fail(CM_ERR_NOMEM, "plan: host allocation");
+    const uint64_t bytes = align_up((uint64_t)n_pairs * sizeof(DevPair)) + kAlign;  // table, then the counter
+    if (!ix->alloc.alloc(bytes, &pl->table_at)) {
+        delete pl;
+        return fail(CM_ERR_BUDGET, "plan: arena full (%llu bytes for the pair table)", (unsigned long long)bytes);
+    }
+    pl->ix = ix;
+    ix->plans.insert(pl);
+    pl->n_pairs = n_pairs;
+    pl->rows = rows;
+    pl->n_items = (int32_t)items;
+    if (n_pairs) {
+        cm_status st = upload_table(ix, pl->table_at, tab.data(), tab.size() * sizeof(DevPair),
+                                    reinterpret_cast<cudaStream_t>(stream));
+        if (st != CM_OK) {
+            ix->alloc.release(pl->table_at);
+            delete pl;
+            return st;
+        }
+    }
+    *out = pl;
+    return CM_OK;
+}
+
+extern "C" int64_t cm_match_plan_rows(const cm_match_plan* pl) { return pl ? pl->rows : -1; }
+
+extern "C" cm_status cm_match_plan_run(cm_match_plan* pl, const cm_match_out* out, cm_stream stream) {
+    if (!pl || !out || (!out->best_j && pl->rows)) return fail(CM_ERR_INVALID, "plan_run: bad argument");
+    cm_index* ix = pl->ix;
+    if (!ix) return fail(CM_ERR_STATE, "plan_run: the plan's index was destroyed");
+    if (!pl->n_items) return CM_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t counter_at = pl->table_at + align_up((uint64_t)pl->n_pairs * sizeof(DevPair));
+    unsigned* counter = reinterpret_cast<unsigned*>(ix->arena + counter_at);
+    CM_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
+    MatchLaunch m{};
+    m.imgs = ix->at<DevImage>(ix->fx.imgs);
+    m.pairs = reinterpret_cast<const DevPair*>(ix->arena + pl->table_at);
+    m.n_pairs = (int32_t)pl->n_pairs;
+    m.n_items = pl->n_items;
+    m.S = query_tile(&ix->p);
+    m.L = ix->p.L;
+    m.m = ix->p.m;
+    m.K = ix->p.K;
+    m.ratio_num = ix->p.ratio_num;
+    m.ratio_den = ix->p.ratio_den;
+    m.rerank = ix->p.rerank;
+    m.counter = counter;
+    m.out = *out;
+    CM_CUDA(launch_match(m, ix->sms, s));
+    return CM_OK;
+}
+
+extern "C" void cm_match_plan_destroy(cm_match_plan* pl) {
+    if (!pl) return;
+    if (pl->ix) {
+        pl->ix->alloc.release(pl->table_at);
+        pl->ix->plans.erase(pl);
+    }
+    delete pl;
+}
+
+extern "C" void cm_index_destroy(cm_index* ix) {
+    if (!ix) return;
+    for (cm_match_plan* pl : ix->plans) pl->ix = nullptr;  // a plan outliving its index becomes inert
+    delete ix;
+}
+
+extern "C" cm_status cm_match_pairs(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, const cm_match_out* out,
+                                    cm_stream stream) {
+    cm_match_plan* pl = nullptr;
+    cm_status st = cm_match_plan_create(ix, pairs, n_pairs, stream, &pl);
+    if (st != CM_OK) return st;
+    st = cm_match_plan_run(pl, out, stream);
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    cm_match_plan_destroy(pl);
+    if (st != CM_OK) return st;
+    if (e != cudaSuccess) return fail(CM_ERR_CUDA, "cm_match_pairs: %s", cudaGetErrorString(e));
+    return CM_OK;
+}

@@ -1,0 +1,82 @@
+// Internal types shared by the host library and the kernels (not part of the ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/cashmatch.h"
+
+namespace cm {
+
+constexpr int kDim = 128;          // descriptor length (SIFT)
+constexpr int kMaxL = 8;
+constexpr int kMaxM = 8;
+constexpr int kMaxP = 192;         // L*m + 128 <= 192
+constexpr int kHashTile = 64;      // descriptors per hash tile
+constexpr int kHashThreads = 256;
+constexpr int kMatchThreads = 1024;
+constexpr int kDefaultQueryTile = 2048;
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+
+// One resident image, as the kernels see it.  All pointers are into the arena
+// (desc may point at caller memory when loaded in place).
+struct DevImage {
+    const uint8_t* desc;   // [n][128]
+    uint64_t* key;         // [n]   byte t = bucket key of table t
+    uint4* code;           // [n]   128-bit fine code
+    uint4* scode;          // [L][n] codes sorted by bucket, per table
+    uint16_t* sidx;        // [L][n] local indices sorted by bucket (ascending inside a bucket)
+    uint32_t* off;         // [L][B+1] bucket offsets
+    uint32_t* hist;        // [L][B] bucket counts (zero between hashing passes)
+    uint32_t* norm;        // [n]   squared norm of the raw descriptor (tensor-core forms)
+    void* xq;              // [n][128] BF16 or FP8 copy (tensor-core forms)
+    float* xscale;         // [n]   FP8 scale (FP8 form)
+    int32_t n;
+    int32_t pad;
+};
+
+// One pair of a match plan.
+struct DevPair {
+    int32_t i, j;          // query image, database image
+    int64_t row_off;       // first output row of this pair
+    int32_t item0;         // first work item of this pair
+    int32_t nitems;        // work items (query tiles) of this pair
+};
+
+struct HashLaunch {
+    const DevImage* imgs;
+    const int32_t* batch;      // image ids of the batch
+    const int32_t* tile_pref;  // [n_batch+1] prefix of hash tiles per image
+    int32_t n_batch;
+    int32_t n_tiles;
+    const float* W;            // [128][P_pad]
+    const float* mu;           // [128]
+    int32_t L, m, P_pad;
+    int32_t rerank;
+};
+
+struct MatchLaunch {
+    const DevImage* imgs;
+    const DevPair* pairs;
+    int32_t n_pairs;
+    int32_t n_items;
+    int32_t S;                 // queries per item
+    int32_t L, m, K;
+    int32_t ratio_num, ratio_den;
+    int32_t rerank;
+    unsigned* counter;         // work counter (zeroed before each launch)
+    cm_match_out out;
+};
+
+// Kernel launchers (cm_kernels.cu).  Return cudaGetLastError().
+cudaError_t launch_colsum_rows(const uint8_t* desc, uint64_t n_rows, unsigned long long* sums, cudaStream_t s);
+cudaError_t launch_colsum_images(const HashLaunch& h, unsigned long long* sums, cudaStream_t s);
+cudaError_t launch_mean(const unsigned long long* sums, const unsigned long long* n_total_dev, uint64_t n_total,
+                        float* mu, cudaStream_t s);
+cudaError_t launch_count_rows(const HashLaunch& h, unsigned long long* n_total, cudaStream_t s);
+cudaError_t launch_hash(const HashLaunch& h, int sm_count, cudaStream_t s);
+cudaError_t launch_bucket(const HashLaunch& h, cudaStream_t s);
+cudaError_t launch_match(const MatchLaunch& m, int sm_count, cudaStream_t s);
+size_t match_smem_bytes(int S, int K);
+int hash_npg(int P_pad);
+
+}  // namespace cm
