@@ -47,12 +47,14 @@ def parse():
     ap.add_argument("--workload", default="grid5000", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--rerank", default="fp32", choices=["fp32", "int", "bf16", "fp8"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="auto", choices=["auto", "tile", "warp"], help="match kernel thread mapping")
     ap.add_argument("--block-images", type=int, default=400, help="Size_blk: images per schedule chunk")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="HBM budget of the MBR schedule")
     ap.add_argument("--plain-pairs", type=int, default=200, help="pairs timed in the plain per-pair form")
     ap.add_argument("--oracle-pairs", type=int, default=12, help="pairs in the CPU-oracle sample")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", default=None, help="GXxGY: a smaller grid of the same per-image shape (profiling)")
     return ap.parse_args()
 
 
@@ -81,6 +83,9 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.05)
         except OSError:
             self.proc = None
         return self
@@ -135,13 +140,20 @@ def bucket_evaluations(index, wl, pairs):
     return int(sum((cnt[int(i)] * cnt[int(j)]).sum() for i, j in pairs))
 
 
+def make_workload(args):
+    if args.grid:
+        gx, gy = (int(v) for v in args.grid.lower().split("x"))
+        return synth.WORKLOADS[args.workload](gx=gx, gy=gy)
+    return synth.workload(args.workload)
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2505_22089_b300 as cm
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = synth.workload(args.workload)
+    wl = make_workload(args)
     if world > 1:
         wl.seed += 1000 * rank          # weak scaling: an independent job of the same shape per rank
     n_desc = wl.n_desc
@@ -151,7 +163,7 @@ def run_ours(args, rank, world, local):
     host = torch.empty((total, 128), dtype=torch.uint8, pin_memory=True)
     wl.generate(desc=host.numpy())
     gen_s = time.time() - t0
-    p = cm.Params.make(rerank=args.rerank)
+    p = cm.Params.make(rerank=args.rerank, algo=args.algo)
     stream = torch.cuda.Stream(device=dev)
 
     # schedule blocks (MBR) under the HBM budget
@@ -221,12 +233,14 @@ def run_ours(args, rank, world, local):
                 "kernel": "k_match", "evals_per_step": evals, "match_ms_per_step": float(np.mean(match_ms))}
 
     # ---- end to end through the C ABI: host descriptors in, host results out
-    e2e_ms = []
+    e2e_ms = [float("nan")]
     h2d = total * 128
     best_host = torch.empty(n_rows, dtype=torch.int32, pin_memory=True)
     del plans, outs, index
     torch.cuda.empty_cache()
-    for s in range(args.e2e_steps + 1):
+    if args.e2e_steps > 0:
+        e2e_ms = []
+    for s in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
@@ -247,11 +261,11 @@ def run_ours(args, rank, world, local):
     e2e_value = n_pairs * world / (np.mean(e2e_ms) / 1e3)
 
     # ---- plain per-pair form (no schedule): upload both images, hash, match, download, free
-    plain = plain_per_pair(args, wl, host, sums, stream, dev)
+    plain = plain_per_pair(args, wl, host, sums, stream, dev) if args.plain_pairs > 0 else None
 
     # ---- CPU oracle on a bounded sample (rank 0 at N=1): baseline and match agreement
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.oracle_pairs > 0:
         cpu = cpu_baseline_and_agreement(args, wl, host.numpy(), sums, pairs, rows, gpu_rows)
 
     res = {
@@ -260,7 +274,7 @@ def run_ours(args, rank, world, local):
         "vs_baseline": None, "dtype": "u8/fp32" if args.rerank == "fp32" else "u8/" + args.rerank,
         "data": "synthetic (seeded track model, %s)" % args.workload,
         "config": {"workload": args.workload, "images": wl.n_images, "pairs": n_pairs,
-                   "descriptors": total, "rerank": args.rerank, "L": p.L, "m": p.m, "K": p.K,
+                   "descriptors": total, "rerank": args.rerank, "algo": args.algo, "L": p.L, "m": p.m, "K": p.K,
                    "ratio": "%d/%d" % (p.ratio_num, p.ratio_den), "block_rows": len(rows),
                    "size_blk": args.block_images, "budget_gb": args.budget_gb,
                    "l2": "inputs (%.1f GB descriptors) larger than L2" % (total * 128 / 1e9),
@@ -268,6 +282,7 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": n_rows * 4, "ms_per_step": float(np.mean(e2e_ms))},
         "plain_fp32_per_pair": plain,
+        # per step: colsum, mean, hash, bucket, then one match launch per block row
         "gpu_launches": args.steps * (4 + len(rows)),
         "roofline": roofline,
         "clocks": clocks,

@@ -54,6 +54,14 @@ typedef enum {
     CM_RERANK_INT = 3    /* CUDA cores, 4-way byte SIMD integer arithmetic (exact) */
 } cm_rerank;
 
+/* Thread mapping of the match kernel (both compute the same result). */
+typedef enum {
+    CM_ALGO_AUTO = 0,    /* library choice */
+    CM_ALGO_TILE = 1,    /* one lane per query; a CTA keeps a tile of queries' top-K in shared memory and
+                            sweeps the tables with the queries sorted by bucket */
+    CM_ALGO_WARP = 2     /* one warp per query; top-K kept across the warp with ballots and shuffles */
+} cm_algo;
+
 /* Where descriptor pointers given to the library live. */
 typedef enum {
     CM_MEM_HOST = 0,          /* host memory: the library copies it into the arena (H2D) */
@@ -74,7 +82,9 @@ typedef struct cm_params {
     int32_t ratio_den;   /* t_r denominator, >= 1; num/den <= 4 */
     uint64_t seed;       /* seed of the projection weights (splitmix64 + Box-Muller, see cm_make_weights) */
     int32_t rerank;      /* cm_rerank */
-    int32_t query_tile;  /* queries per work item of the match kernel; 0 = library default */
+    int32_t query_tile;  /* queries per work item of the match kernel, multiple of 64; 0 = default (2048, less
+                            for K = 16 so the tile kernel's shared memory fits) */
+    int32_t algo;        /* cm_algo */
 } cm_params;
 
 typedef struct { int32_t i, j; } cm_pair;  /* query image i, database image j (i != j) */

@@ -19,7 +19,11 @@ LIB_PATH = os.path.join(HERE, "libcashmatch.so")
 
 CM_OK, CM_ERR_INVALID, CM_ERR_BUDGET, CM_ERR_CUDA, CM_ERR_TIMEOUT, CM_ERR_NOMEM, CM_ERR_STATE = range(7)
 RERANK = {"fp32": 0, "bf16": 1, "fp8": 2, "int": 3}
+ALGO = {"auto": 0, "tile": 1, "warp": 2}
 MEM_HOST, MEM_DEVICE, MEM_DEVICE_INPLACE = 0, 1, 2
+# Arena headroom the binding adds to cm_index_bytes for match-plan tables
+# (24 bytes per planned pair): room for about 600,000 pairs of plans.
+PLAN_HEADROOM = 16 << 20
 
 # Every symbol include/cashmatch.h declares (checked by the CPU tests).
 EXPORTS = [
@@ -41,12 +45,12 @@ class CMError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("m", ctypes.c_int32), ("n_bits", ctypes.c_int32), ("K", ctypes.c_int32),
                 ("ratio_num", ctypes.c_int32), ("ratio_den", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("rerank", ctypes.c_int32), ("query_tile", ctypes.c_int32)]
+                ("rerank", ctypes.c_int32), ("query_tile", ctypes.c_int32), ("algo", ctypes.c_int32)]
 
     @classmethod
-    def make(cls, L=6, m=8, K=8, ratio=(4, 5), seed=0x5EED, rerank="fp32", query_tile=0, n_bits=128):
+    def make(cls, L=6, m=8, K=8, ratio=(4, 5), seed=0x5EED, rerank="fp32", query_tile=0, n_bits=128, algo="auto"):
         return cls(L, m, n_bits, K, ratio[0], ratio[1], seed, RERANK[rerank] if isinstance(rerank, str) else rerank,
-                   query_tile)
+                   query_tile, ALGO[algo] if isinstance(algo, str) else algo)
 
     @property
     def P(self):
@@ -225,7 +229,7 @@ class Index:
         self.n_desc = np.ascontiguousarray(n_desc, dtype=np.int32)
         if arena is None:
             if arena_bytes is None:
-                arena_bytes = index_bytes(p, self.n_desc, inplace)
+                arena_bytes = index_bytes(p, self.n_desc, inplace) + PLAN_HEADROOM
             arena = torch.empty(int(arena_bytes) + 256, dtype=torch.uint8, device=device)
         self.arena = arena
         base = (self.arena.data_ptr() + 255) // 256 * 256
@@ -248,7 +252,7 @@ class Index:
         if mem is None:
             mem = MEM_DEVICE_INPLACE if on_dev else MEM_HOST
         if arena_bytes is None:
-            arena_bytes = index_bytes(p, self.n_desc, mem == MEM_DEVICE_INPLACE)
+            arena_bytes = index_bytes(p, self.n_desc, mem == MEM_DEVICE_INPLACE) + PLAN_HEADROOM
         self.arena = torch.empty(int(arena_bytes) + 256, dtype=torch.uint8, device="cuda")
         base = (self.arena.data_ptr() + 255) // 256 * 256
         ptr = desc.data_ptr() if isinstance(desc, torch.Tensor) else np.ascontiguousarray(desc).ctypes.data

@@ -58,7 +58,17 @@ extern "C" cm_status cm_params_default(cm_params* p) {
     p->seed = 0x5EED;
     p->rerank = CM_RERANK_FP32;
     p->query_tile = 0;
+    p->algo = CM_ALGO_AUTO;
     return CM_OK;
+}
+
+// Default work-item size: kDefaultQueryTile, shrunk until the tile kernel's
+// shared memory (top-K lists and hit buffers of the tile) fits.
+static int query_tile(const cm_params* p) {
+    if (p->query_tile) return p->query_tile;
+    int S = kDefaultQueryTile;
+    while (S > 64 && match_smem_bytes(S, p->K) > 226 * 1024) S -= 64;
+    return S;
 }
 
 extern "C" cm_status cm_params_check(const cm_params* p) {
@@ -75,8 +85,9 @@ extern "C" cm_status cm_params_check(const cm_params* p) {
     if (p->query_tile != 0 && (p->query_tile < 64 || p->query_tile > 8192 || p->query_tile % 64))
         return fail(CM_ERR_INVALID, "params: query_tile=%d must be 0 or a multiple of 64 in 64..8192",
                     p->query_tile);
-    const int S = p->query_tile ? p->query_tile : kDefaultQueryTile;
-    if (match_smem_bytes(S, p->K) > 227 * 1024)
+    if (p->algo < CM_ALGO_AUTO || p->algo > CM_ALGO_WARP) return fail(CM_ERR_INVALID, "params: algo %d", p->algo);
+    const int S = query_tile(p);
+    if (p->algo == CM_ALGO_TILE && match_smem_bytes(S, p->K) > 226 * 1024)
         return fail(CM_ERR_INVALID, "params: query_tile=%d with K=%d needs %zu bytes of shared memory (> 227 KB)", S,
                     p->K, match_smem_bytes(S, p->K));
     return CM_OK;
@@ -84,8 +95,6 @@ extern "C" cm_status cm_params_check(const cm_params* p) {
 
 static int proj_count(const cm_params* p) { return p->L * p->m + p->n_bits; }
 static int proj_pad(const cm_params* p) { return (proj_count(p) + 15) / 16 * 16; }
-static int query_tile(const cm_params* p) { return p->query_tile ? p->query_tile : kDefaultQueryTile; }
-
 // ---------------------------------------------------------------------------
 // projection weights: splitmix64 stream -> Box-Muller pairs -> float
 // ---------------------------------------------------------------------------
@@ -130,7 +139,7 @@ constexpr uint64_t kAlign = 256;
 inline uint64_t align_up(uint64_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct SlotLayout {
-    uint64_t desc, key, code, scode, sidx, off, hist, norm, xq, xscale, total;
+    uint64_t desc, key, code, scode, sidx, off, hist, brank, norm, xq, xscale, total;
 };
 
 SlotLayout slot_layout(const cm_params* p, int64_t n, bool inplace) {
@@ -145,6 +154,7 @@ SlotLayout slot_layout(const cm_params* p, int64_t n, bool inplace) {
     s.sidx = take((uint64_t)p->L * n * 2);
     s.off = take((uint64_t)p->L * (B + 1) * 4);
     s.hist = take((uint64_t)p->L * B * 4);
+    s.brank = take((uint64_t)p->L * 256);
     s.norm = take((uint64_t)n * 4);
     const uint64_t xq_bytes = p->rerank == CM_RERANK_BF16 ? 256 : (p->rerank == CM_RERANK_FP8 ? 128 : 0);
     s.xq = xq_bytes ? take((uint64_t)n * xq_bytes) : 0;
@@ -482,6 +492,7 @@ static cm_status stage_images(cm_index* ix, int32_t count, const int32_t* ids, c
         e.sidx = reinterpret_cast<uint16_t*>(base + L.sidx);
         e.off = reinterpret_cast<uint32_t*>(base + L.off);
         e.hist = reinterpret_cast<uint32_t*>(base + L.hist);
+        e.brank = base + L.brank;
         e.norm = reinterpret_cast<uint32_t*>(base + L.norm);
         e.xq = L.xq ? base + L.xq : nullptr;
         e.xscale = L.xscale ? reinterpret_cast<float*>(base + L.xscale) : nullptr;
@@ -722,7 +733,9 @@ extern "C" cm_status cm_match_plan_run(cm_match_plan* pl, const cm_match_out* ou
     m.rerank = ix->p.rerank;
     m.counter = counter;
     m.out = *out;
-    CM_CUDA(launch_match(m, ix->sms, s));
+    m.algo = ix->p.algo == CM_ALGO_WARP ? CM_ALGO_WARP : CM_ALGO_TILE;   // auto: tile, if its tile fits
+    if (m.algo == CM_ALGO_TILE && match_smem_bytes(m.S, m.K) > 226 * 1024) m.algo = CM_ALGO_WARP;
+    CM_CUDA(m.algo == CM_ALGO_TILE ? launch_match(m, ix->sms, s) : launch_match_wq(m, ix->sms, s));
     return CM_OK;
 }
 

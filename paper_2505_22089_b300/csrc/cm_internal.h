@@ -14,7 +14,9 @@ constexpr int kMaxP = 192;         // L*m + 128 <= 192
 constexpr int kHashTile = 64;      // descriptors per hash tile
 constexpr int kHashThreads = 256;
 constexpr int kMatchThreads = 1024;
-constexpr int kDefaultQueryTile = 2048;
+constexpr int kDefaultQueryTile = 2048;  // queries per work item
+constexpr int kWqThreads = 256;          // warp-per-query matcher: 8 warps per CTA
+constexpr int kWqBlocksPerSM = 3;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 // One resident image, as the kernels see it.  All pointers are into the arena
@@ -27,6 +29,7 @@ struct DevImage {
     uint16_t* sidx;        // [L][n] local indices sorted by bucket (ascending inside a bucket)
     uint32_t* off;         // [L][B+1] bucket offsets
     uint32_t* hist;        // [L][B] bucket counts (zero between hashing passes)
+    uint8_t* brank;        // [L][256] rank of each bucket by run length (ties by bucket id)
     uint32_t* norm;        // [n]   squared norm of the raw descriptor (tensor-core forms)
     void* xq;              // [n][128] BF16 or FP8 copy (tensor-core forms)
     float* xscale;         // [n]   FP8 scale (FP8 form)
@@ -59,10 +62,11 @@ struct MatchLaunch {
     const DevPair* pairs;
     int32_t n_pairs;
     int32_t n_items;
-    int32_t S;                 // queries per item
+    int32_t S;                 // queries per work item
     int32_t L, m, K;
     int32_t ratio_num, ratio_den;
     int32_t rerank;
+    int32_t algo;              // CM_ALGO_TILE or CM_ALGO_WARP
     unsigned* counter;         // work counter (zeroed before each launch)
     cm_match_out out;
 };
@@ -75,7 +79,8 @@ cudaError_t launch_mean(const unsigned long long* sums, const unsigned long long
 cudaError_t launch_count_rows(const HashLaunch& h, unsigned long long* n_total, cudaStream_t s);
 cudaError_t launch_hash(const HashLaunch& h, int sm_count, cudaStream_t s);
 cudaError_t launch_bucket(const HashLaunch& h, cudaStream_t s);
-cudaError_t launch_match(const MatchLaunch& m, int sm_count, cudaStream_t s);
+cudaError_t launch_match(const MatchLaunch& m, int sm_count, cudaStream_t s);      // lane per query (cm_match.cu)
+cudaError_t launch_match_wq(const MatchLaunch& m, int sm_count, cudaStream_t s);   // warp per query (cm_match_wq.cu)
 size_t match_smem_bytes(int S, int K);
 int hash_npg(int P_pad);
 

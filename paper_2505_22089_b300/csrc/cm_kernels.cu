@@ -8,9 +8,7 @@
 //  k_bucket     per (image, table): exclusive scan of the histogram and a stable
 //               scatter of codes and indices into bucket order (the lookup tables
 //               of Sec. 2.3.1 step (1))
-//  k_match      persistent fused matcher over all pairs of a block: bucket lookup,
-//               Hamming ranking to the top K, Euclidean rerank and ratio test
-//               (Sec. 2.3.1 steps (1)-(4))
+//  (the fused matcher k_match is in cm_match.cu)
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -251,10 +249,29 @@ __global__ void __launch_bounds__(128) k_bucket(HashLaunch h) {
             base[b] = run;
             off[b] = run;
             run += hist[b];
-            hist[b] = 0;              // histograms are zero between hashing passes
         }
     }
     if (lane == 0) off[B] = (uint32_t)e.n;
+    __syncwarp();
+    // rank of each bucket by run length (ties by bucket id), for the match kernel's
+    // query order; then clear the histogram (zero between hashing passes)
+    for (int q = 0; q < per; ++q) {
+        const int b = lane * per + q;
+        if (b < B) {
+            const uint32_t lb = hist[b];
+            uint32_t r = 0;
+            for (int b2 = 0; b2 < B; ++b2) {
+                const uint32_t l2 = hist[b2];
+                r += (l2 < lb || (l2 == lb && b2 < b)) ? 1u : 0u;
+            }
+            e.brank[t * 256 + b] = (uint8_t)r;
+        }
+    }
+    __syncwarp();
+    for (int q = 0; q < per; ++q) {
+        const int b = lane * per + q;
+        if (b < B) hist[b] = 0;
+    }
     __syncwarp();
 
     const unsigned lt = (1u << lane) - 1u;
@@ -275,264 +292,6 @@ __global__ void __launch_bounds__(128) k_bucket(HashLaunch h) {
             sidx[p0 + rank] = (uint16_t)i;
         }
         __syncwarp();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// matching
-// ---------------------------------------------------------------------------
-
-template <int K>
-__device__ __forceinline__ void topk_insert(uint32_t (&s)[K], uint32_t key) {
-    bool dup = false;
-#pragma unroll
-    for (int i = 0; i < K; ++i) dup |= (s[i] == key);
-    if (dup) return;
-#pragma unroll
-    for (int i = K - 1; i > 0; --i) s[i] = (key < s[i - 1]) ? s[i - 1] : ((key < s[i]) ? key : s[i]);
-    s[0] = min(s[0], key);
-}
-
-__device__ __forceinline__ int ham128(uint4 a, uint4 b) {
-    return __popc(a.x ^ b.x) + __popc(a.y ^ b.y) + __popc(a.z ^ b.z) + __popc(a.w ^ b.w);
-}
-
-// Scan one bucket run [c0, c1) of the database image for one query.
-template <int K>
-__device__ __forceinline__ void scan_run(const uint4* __restrict__ codes, const uint16_t* __restrict__ idx,
-                                         uint32_t c0, uint32_t c1, uint4 q, uint32_t (&s)[K]) {
-    uint32_t kth_h = s[K - 1] >> 16;
-    uint32_t c = c0;
-    for (; c + 1 < c1; c += 2) {
-        const uint4 v0 = __ldg(codes + c);
-        const uint4 v1 = __ldg(codes + c + 1);
-        const uint32_t h0 = (uint32_t)ham128(v0, q);
-        const uint32_t h1 = (uint32_t)ham128(v1, q);
-        if (min(h0, h1) <= kth_h) {
-            if (h0 <= kth_h) {
-                const uint32_t key = (h0 << 16) | __ldg(idx + c);
-                if (key < s[K - 1]) topk_insert<K>(s, key);
-            }
-            if (h1 <= (s[K - 1] >> 16)) {
-                const uint32_t key = (h1 << 16) | __ldg(idx + c + 1);
-                if (key < s[K - 1]) topk_insert<K>(s, key);
-            }
-            kth_h = s[K - 1] >> 16;
-        }
-    }
-    if (c < c1) {
-        const uint4 v0 = __ldg(codes + c);
-        const uint32_t h0 = (uint32_t)ham128(v0, q);
-        if (h0 <= kth_h) {
-            const uint32_t key = (h0 << 16) | __ldg(idx + c);
-            if (key < s[K - 1]) topk_insert<K>(s, key);
-        }
-    }
-}
-
-// Exact ratio test dis(q1) < t_r dis(q2), t_r = num/den.  FP32 where the ratio is
-// at least 1e-3 away from t_r (FP32 error is ~1e-7 there), FP64 re-check otherwise
-// (d^2 < 2^24, so den^2 d1^2 and num^2 d2^2 are exact in FP64).
-__device__ __forceinline__ bool ratio_pass(uint32_t d1, uint32_t d2, int num, int den, uint32_t& rechecks) {
-    if (d2 == 0u) return false;
-    const float r = sqrtf((float)d1 / (float)d2);
-    const float tr = (float)num / (float)den;
-    if (fabsf(r - tr) >= 1e-3f) return r < tr;
-    ++rechecks;
-    return (double)den * (double)den * (double)d1 < (double)num * (double)num * (double)d2;
-}
-
-__device__ __forceinline__ float byte_as_offset_float(uint32_t w, int b) {
-    // 2^23 + byte, exactly; differences of two such values are exact
-    return __uint_as_float(0x4B000000u | ((w >> (8 * b)) & 0xFFu));
-}
-
-template <int K>
-__global__ void __launch_bounds__(kMatchThreads, 1) k_match(MatchLaunch ml) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int S = ml.S;
-    uint32_t* st = reinterpret_cast<uint32_t*>(smem_raw);          // [S][K] running top-K keys (h<<16|j)
-    uint4* qcode = reinterpret_cast<uint4*>(st + (size_t)S * K);  // [S]
-    uint64_t* qkey = reinterpret_cast<uint64_t*>(qcode + S);      // [S]
-    uint16_t* perm = reinterpret_cast<uint16_t*>(qkey + S);       // [S] table-order permutation
-    uint16_t* rnk = perm + S;                                     // [S]
-    uint32_t* hist = reinterpret_cast<uint32_t*>(rnk + S);        // [256]
-    __shared__ int s_item;
-    __shared__ uint32_t s_stats[2];
-
-    const int tid = threadIdx.x;
-    const int B = 1 << ml.m;
-    if (tid < 2) s_stats[tid] = 0;
-    uint32_t rechecks = 0, matches = 0;
-
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s_item = (int)atomicAdd(ml.counter, 1u);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= ml.n_items) break;
-        // pair of this item: last p with item0 <= item
-        int lo = 0, hi = ml.n_pairs;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (ml.pairs[mid].item0 <= item) lo = mid; else hi = mid;
-        }
-        const DevPair P = ml.pairs[lo];
-        const DevImage I = ml.imgs[P.i];
-        const DevImage J = ml.imgs[P.j];
-        const int q0 = (item - P.item0) * S;
-        const int nq = min(S, I.n - q0);
-
-        for (int q = tid; q < nq; q += kMatchThreads) {
-            qcode[q] = I.code[q0 + q];
-            qkey[q] = I.key[q0 + q];
-        }
-        for (int e = tid; e < nq * K; e += kMatchThreads) st[e] = kEmpty;
-        __syncthreads();
-
-        // Sec. 2.3.1 steps (1)-(3): one pass per hash table, queries in bucket order
-        for (int t = 0; t < ml.L; ++t) {
-            for (int b = tid; b < B; b += kMatchThreads) hist[b] = 0;
-            __syncthreads();
-            for (int q = tid; q < nq; q += kMatchThreads) {
-                const int b = (int)((qkey[q] >> (8 * t)) & 0xFFu);
-                rnk[q] = (uint16_t)atomicAdd(&hist[b], 1u);
-            }
-            __syncthreads();
-            if (tid < 32) {
-                const int per = (B + 31) / 32;
-                uint32_t local = 0;
-                for (int q = 0; q < per; ++q) {
-                    const int b = tid * per + q;
-                    if (b < B) local += hist[b];
-                }
-                uint32_t incl = local;
-#pragma unroll
-                for (int s = 1; s < 32; s <<= 1) {
-                    const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, s);
-                    if (tid >= s) incl += v;
-                }
-                uint32_t run = incl - local;
-                for (int q = 0; q < per; ++q) {
-                    const int b = tid * per + q;
-                    if (b < B) {
-                        const uint32_t c = hist[b];
-                        hist[b] = run;
-                        run += c;
-                    }
-                }
-            }
-            __syncthreads();
-            for (int q = tid; q < nq; q += kMatchThreads) {
-                const int b = (int)((qkey[q] >> (8 * t)) & 0xFFu);
-                perm[hist[b] + rnk[q]] = (uint16_t)q;
-            }
-            __syncthreads();
-
-            const uint4* Jc = J.scode + (size_t)t * J.n;
-            const uint16_t* Ji = J.sidx + (size_t)t * J.n;
-            const uint32_t* Jo = J.off + t * (B + 1);
-            for (int pos = tid; pos < nq; pos += kMatchThreads) {
-                const int q = perm[pos];
-                const int b = (int)((qkey[q] >> (8 * t)) & 0xFFu);
-                const uint32_t c0 = __ldg(Jo + b), c1 = __ldg(Jo + b + 1);
-                uint32_t s[K];
-#pragma unroll
-                for (int i = 0; i < K; ++i) s[i] = st[q * K + i];
-                scan_run<K>(Jc, Ji, c0, c1, qcode[q], s);
-#pragma unroll
-                for (int i = 0; i < K; ++i) st[q * K + i] = s[i];
-            }
-            __syncthreads();
-        }
-
-        // Sec. 2.3.1 step (4): exact distances of the top K, q1 / q2, ratio test.
-        // 8 lanes per query, 16 descriptor bytes per lane.
-        const int g = tid >> 3, l8 = tid & 7;
-        const int rounds = (nq + (kMatchThreads / 8) - 1) / (kMatchThreads / 8);
-        for (int r = 0; r < rounds; ++r) {
-            const int q = g + r * (kMatchThreads / 8);
-            const bool active = q < nq;
-            const int qq = active ? q : 0;
-            const uint4 xv = __ldg(reinterpret_cast<const uint4*>(I.desc + (size_t)(q0 + qq) * kDim) + l8);
-            float xf[16];
-            if (ml.rerank == CM_RERANK_FP32) {
-                const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
-#pragma unroll
-                for (int u = 0; u < 16; ++u) xf[u] = byte_as_offset_float(xw[u >> 2], u & 3);
-            }
-            uint32_t d1 = kEmpty, d2 = kEmpty;
-            int j1 = -1, j2 = -1;
-#pragma unroll 1
-            for (int k = 0; k < K; ++k) {
-                const uint32_t key = active ? st[qq * K + k] : kEmpty;
-                const bool valid = key != kEmpty;
-                const int j = valid ? (int)(key & 0xFFFFu) : 0;
-                const uint8_t* yrow = valid ? (J.desc + (size_t)j * kDim) : (I.desc + (size_t)(q0 + qq) * kDim);
-                const uint4 yv = __ldg(reinterpret_cast<const uint4*>(yrow) + l8);
-                uint32_t dd;
-                if (ml.rerank == CM_RERANK_FP32) {
-                    const uint32_t yw[4] = {yv.x, yv.y, yv.z, yv.w};
-                    float acc = 0.f;
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const float df = byte_as_offset_float(yw[u >> 2], u & 3) - xf[u];
-                        acc = fmaf(df, df, acc);
-                    }
-                    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
-                    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
-                    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4);
-                    dd = (uint32_t)acc;
-                } else {
-                    uint32_t a0 = __vabsdiffu4(xv.x, yv.x), a1 = __vabsdiffu4(xv.y, yv.y);
-                    uint32_t a2 = __vabsdiffu4(xv.z, yv.z), a3 = __vabsdiffu4(xv.w, yv.w);
-                    uint32_t acc = __dp4a(a0, a0, 0u);
-                    acc = __dp4a(a1, a1, acc);
-                    acc = __dp4a(a2, a2, acc);
-                    acc = __dp4a(a3, a3, acc);
-                    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
-                    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
-                    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4);
-                    dd = acc;
-                }
-                if (valid) {
-                    if (j1 < 0 || dd < d1 || (dd == d1 && j < j1)) {
-                        d2 = d1; j2 = j1; d1 = dd; j1 = j;
-                    } else if (j2 < 0 || dd < d2 || (dd == d2 && j < j2)) {
-                        d2 = dd; j2 = j;
-                    }
-                }
-            }
-            if (active) {
-                const int64_t row = P.row_off + q0 + q;
-                bool pass = false;
-                if (j2 >= 0) pass = ratio_pass(d1, d2, ml.ratio_num, ml.ratio_den, rechecks);
-                if (l8 == 0) {
-                    ml.out.best_j[row] = pass ? j1 : -1;
-                    if (ml.out.d1sq) ml.out.d1sq[row] = d1;
-                    if (ml.out.d2sq) ml.out.d2sq[row] = d2;
-                    matches += pass ? 1u : 0u;
-                }
-                if (ml.out.topk) {
-                    for (int k = l8; k < K; k += 8) {
-                        const uint32_t key = st[q * K + k];
-                        ml.out.topk[row * K + k] = key == kEmpty ? -1 : (int)(key & 0xFFFFu);
-                    }
-                }
-            }
-        }
-    }
-    if (ml.out.stats) {
-        // rechecks were counted by all 8 lanes of a group; keep lane 0's count
-        if ((tid & 7) == 0) {
-            atomicAdd(&s_stats[0], rechecks);
-            atomicAdd(&s_stats[1], matches);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            atomicAdd(&ml.out.stats[0], s_stats[0]);
-            atomicAdd(&ml.out.stats[1], s_stats[1]);
-        }
     }
 }
 
@@ -599,30 +358,6 @@ cudaError_t launch_bucket(const HashLaunch& h, cudaStream_t s) {
     if (warps == 0) return cudaSuccess;
     k_bucket<<<(warps + 3) / 4, 128, 0, s>>>(h);
     return cudaGetLastError();
-}
-
-size_t match_smem_bytes(int S, int K) {
-    return (size_t)S * K * 4 + (size_t)S * 16 + (size_t)S * 8 + (size_t)S * 2 * 2 + 256 * 4;
-}
-
-template <int K>
-static cudaError_t launch_match_t(const MatchLaunch& m, int sms, cudaStream_t s) {
-    const size_t smem = match_smem_bytes(m.S, K);
-    cudaError_t e = cudaFuncSetAttribute(k_match<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int grid = m.n_items < sms ? (m.n_items ? m.n_items : 1) : sms;
-    k_match<K><<<grid, kMatchThreads, smem, s>>>(m);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_match(const MatchLaunch& m, int sms, cudaStream_t s) {
-    switch (m.K) {
-        case 2: return launch_match_t<2>(m, sms, s);
-        case 4: return launch_match_t<4>(m, sms, s);
-        case 8: return launch_match_t<8>(m, sms, s);
-        case 16: return launch_match_t<16>(m, sms, s);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 }  // namespace cm

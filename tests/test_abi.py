@@ -37,7 +37,7 @@ def test_params_validation():
     assert lib.cm_params_default(p) == cm.CM_OK
     assert (p.L, p.m, p.n_bits, p.K, p.ratio_num, p.ratio_den) == (6, 8, 128, 8, 4, 5)
     for bad in (dict(L=0), dict(L=9), dict(m=9), dict(K=3), dict(K=32), dict(ratio=(1, 0)), dict(ratio=(-1, 2)),
-                dict(query_tile=100), dict(n_bits=64), dict(rerank=7)):
+                dict(query_tile=100), dict(query_tile=32), dict(query_tile=8192, algo="tile"), dict(algo=5), dict(n_bits=64), dict(rerank=7)):
         q = cm.Params.make(**bad)
         assert lib.cm_params_check(q) == cm.CM_ERR_INVALID
         assert lib.cm_last_error()

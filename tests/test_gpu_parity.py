@@ -44,40 +44,46 @@ def test_pair2k_paper_defaults():
     assert 500 < (res["best_j"] >= 0).sum() < 1000
 
 
-@pytest.mark.parametrize("tile", [64, 256, 640])
-def test_pair2k_query_tiles_with_ragged_tail(tile):
-    _run(synth.pair2k(), cm.Params.make(query_tile=tile))
+@pytest.mark.parametrize("algo", ["tile", "warp"])
+@pytest.mark.parametrize("tile", [64, 256, 640, 2048])
+def test_pair2k_query_tiles_with_ragged_tail(tile, algo):
+    _run(synth.pair2k(), cm.Params.make(query_tile=tile, algo=algo))
 
 
-def test_pair2k_integer_rerank():
-    _run(synth.pair2k(), cm.Params.make(rerank="int"))
+@pytest.mark.parametrize("algo", ["tile", "warp"])
+def test_pair2k_integer_rerank(algo):
+    _run(synth.pair2k(), cm.Params.make(rerank="int", algo=algo))
 
 
-def test_strip30_full_block():
+@pytest.mark.parametrize("algo", ["tile", "warp"])
+def test_strip30_full_block(algo):
     # 30 images x 8,000 descriptors, 120 ordered pairs: one MBR block
-    _run(synth.strip30(), cm.Params.make(), threads=16)
+    _run(synth.strip30(), cm.Params.make(algo=algo), threads=16)
 
 
-def test_uneven_sizes_including_tiny_images():
+@pytest.mark.parametrize("algo", ["tile", "warp"])
+def test_uneven_sizes_including_tiny_images(algo):
     wl = synth.grid500(gx=5, gy=4, nmin=1, nmax=5000)
     wl.images["n"][[0, 7]] = [1, 63]
-    _run(wl, cm.Params.make(query_tile=512))
+    _run(wl, cm.Params.make(query_tile=512, algo=algo))
 
 
 @pytest.mark.parametrize("kw", [dict(K=2), dict(K=4), dict(K=16), dict(m=4), dict(m=0, K=16), dict(L=1),
                                 dict(L=8), dict(L=8, m=6), dict(ratio=(0, 1)), dict(ratio=(1, 2)),
                                 dict(ratio=(1, 1)), dict(seed=12345)])
-def test_parameter_variants(kw):
+@pytest.mark.parametrize("algo", ["tile", "warp"])
+def test_parameter_variants(kw, algo):
     wl = synth.pair2k(n=1500, shared=600)
-    _run(wl, cm.Params.make(**kw))
+    _run(wl, cm.Params.make(algo=algo, **kw))
 
 
-def test_one_bucket_full_rerank_is_exhaustive_nn():
+@pytest.mark.parametrize("algo", ["tile", "warp"])
+def test_one_bucket_full_rerank_is_exhaustive_nn(algo):
     # m = 0 and K >= N_J: every database point is reranked, so the GPU result
     # equals exhaustive L2 nearest neighbours with the ratio test.
     wl = synth.pair2k(n=16, shared=6)
     desc = wl.generate()
-    p = cm.Params.make(m=0, K=16)
+    p = cm.Params.make(m=0, K=16, algo=algo)
     index = cm.Index.build(p, wl.n_desc, torch.from_numpy(desc).cuda())
     plan, res = gpu_match(index, wl.pairs)
     bf = oracle.brute_nn(desc[:16], desc[16:], 4, 5)
