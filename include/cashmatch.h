@@ -222,6 +222,30 @@ void cm_match_plan_destroy(cm_match_plan* pl);
 cm_status cm_match_pairs(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, const cm_match_out* out,
                          cm_stream stream);
 
+/* ---- matching without any device allocation ------------------------------ */
+/* The paper has no counterpart: this entry point serves callers that may not
+ * allocate GPU memory (code running inside another framework's memory budget,
+ * plug-ins of a host process that owns the device, real-time paths where an
+ * allocation could block or fail).  It matches one pair, image i (queries)
+ * against image j, with every step of Sec. 2.3.1 run on the GPU, and uses as
+ * scratch only a file-scope device array of 5 MiB that every GPU which loads
+ * this library holds until the process exits.
+ *  - d_desc_i / d_desc_j: device uint8 [n][128] descriptor rows, at most 8,192
+ *    per image (CM_ERR_BUDGET beyond, with a message); read in place.
+ *  - col_sums_host / n_total: the exact column sums and row count that define
+ *    the centring mean (e.g. from cm_index_col_sums), host memory.
+ *  - d_best_j (required), d_d1sq, d_d2sq (optional): device outputs of n_i
+ *    rows, as in cm_match_out.
+ *  - p->rerank must be CM_RERANK_FP32 or CM_RERANK_INT.
+ * Async on stream.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents, so calls that overlap on the GPU (other streams or host threads)
+ * race: serialise them. */
+cm_status cm_match_pair_noalloc(const cm_params* p, const uint8_t* d_desc_i, int32_t n_i, const uint8_t* d_desc_j,
+                                int32_t n_j, const uint64_t* col_sums_host, uint64_t n_total, int32_t* d_best_j,
+                                uint32_t* d_d1sq, uint32_t* d_d2sq, cm_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

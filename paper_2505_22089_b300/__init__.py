@@ -32,7 +32,7 @@ EXPORTS = [
     "cm_schedule_get_row", "cm_free_schedule", "cm_gps_order", "cm_index_create", "cm_index_set_mean",
     "cm_index_mean_device", "cm_index_col_sums", "cm_index_load", "cm_index_rehash", "cm_index_evict", "cm_build_index",
     "cm_index_image_view", "cm_index_destroy", "cm_match_plan_create", "cm_match_plan_rows", "cm_match_plan_run",
-    "cm_match_plan_destroy", "cm_match_pairs",
+    "cm_match_plan_destroy", "cm_match_pairs", "cm_match_pair_noalloc",
 ]
 
 
@@ -109,6 +109,7 @@ def lib():
             "cm_match_plan_run": (i32, [vp, ctypes.POINTER(MatchOut), vp]),
             "cm_match_plan_destroy": (None, [vp]),
             "cm_match_pairs": (i32, [vp, vp, i64, ctypes.POINTER(MatchOut), vp]),
+            "cm_match_pair_noalloc": (i32, [P, vp, i32, vp, i32, vp, u64, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -320,6 +321,16 @@ class Index:
             self.close()
         except Exception:
             pass
+
+
+def match_pair_noalloc(p: Params, desc_i, desc_j, col_sums, n_total: int, best_j, d1sq=None, d2sq=None,
+                       stream=None):
+    """cm_match_pair_noalloc: one pair matched with the library's static device
+    scratch only.  desc_i / desc_j and the outputs are CUDA tensors."""
+    sums = np.ascontiguousarray(col_sums, dtype=np.uint64)
+    check(lib().cm_match_pair_noalloc(ctypes.byref(p), _ptr(desc_i), int(desc_i.shape[0]), _ptr(desc_j),
+                                      int(desc_j.shape[0]), sums.ctypes.data, int(n_total), _ptr(best_j),
+                                      _ptr(d1sq), _ptr(d2sq), _stream(stream)))
 
 
 class MatchPlan:
