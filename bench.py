@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--rerank", default="fp32", choices=["fp32", "int", "bf16", "fp8"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--algo", default="auto", choices=["auto", "tile", "warp"], help="match kernel thread mapping")
+    ap.add_argument("--projection", default="tc", choices=["tc", "ffma"], help="hash projection: tensor cores or FP32 FFMA")
     ap.add_argument("--block-images", type=int, default=400, help="Size_blk: images per schedule chunk")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="HBM budget of the MBR schedule")
     ap.add_argument("--plain-pairs", type=int, default=200, help="pairs timed in the plain per-pair form")
@@ -163,7 +164,7 @@ def run_ours(args, rank, world, local):
     host = torch.empty((total, 128), dtype=torch.uint8, pin_memory=True)
     wl.generate(desc=host.numpy())
     gen_s = time.time() - t0
-    p = cm.Params.make(rerank=args.rerank, algo=args.algo)
+    p = cm.Params.make(rerank=args.rerank, algo=args.algo, projection=args.projection)
     stream = torch.cuda.Stream(device=dev)
 
     # schedule blocks (MBR) under the HBM budget
@@ -274,7 +275,7 @@ def run_ours(args, rank, world, local):
         "vs_baseline": None, "dtype": "u8/fp32" if args.rerank == "fp32" else "u8/" + args.rerank,
         "data": "synthetic (seeded track model, %s)" % args.workload,
         "config": {"workload": args.workload, "images": wl.n_images, "pairs": n_pairs,
-                   "descriptors": total, "rerank": args.rerank, "algo": args.algo, "L": p.L, "m": p.m, "K": p.K,
+                   "descriptors": total, "rerank": args.rerank, "algo": args.algo, "projection": args.projection, "L": p.L, "m": p.m, "K": p.K,
                    "ratio": "%d/%d" % (p.ratio_num, p.ratio_den), "block_rows": len(rows),
                    "size_blk": args.block_images, "budget_gb": args.budget_gb,
                    "l2": "inputs (%.1f GB descriptors) larger than L2" % (total * 128 / 1e9),

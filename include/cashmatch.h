@@ -62,6 +62,13 @@ typedef enum {
     CM_ALGO_WARP = 2     /* one warp per query; top-K kept across the warp with ballots and shuffles */
 } cm_algo;
 
+/* How the projections onto the hyperplanes are computed (both decide the same
+ * sign bits up to projections within FP32 rounding of zero). */
+typedef enum {
+    CM_PROJ_TC = 0,      /* tensor cores: x in BF16 (exact), W as a sum of three BF16 parts, FP32 accumulate */
+    CM_PROJ_FFMA = 1     /* CUDA cores: FP32 fused multiply-add */
+} cm_projection;
+
 /* Where descriptor pointers given to the library live. */
 typedef enum {
     CM_MEM_HOST = 0,          /* host memory: the library copies it into the arena (H2D) */
@@ -85,6 +92,7 @@ typedef struct cm_params {
     int32_t query_tile;  /* queries per work item of the match kernel, multiple of 64; 0 = default (2048, less
                             for K = 16 so the tile kernel's shared memory fits) */
     int32_t algo;        /* cm_algo */
+    int32_t projection;  /* cm_projection */
 } cm_params;
 
 typedef struct { int32_t i, j; } cm_pair;  /* query image i, database image j (i != j) */
@@ -186,6 +194,10 @@ cm_status cm_index_col_sums(cm_index* ix, uint64_t* sums_host, uint64_t* n_total
  * Errors: CM_ERR_STATE (already resident / mean unset), CM_ERR_BUDGET (arena full). */
 cm_status cm_index_load(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc,
                         int32_t mem, cm_stream stream);
+/* Waits for stream and reports whether a bounded device wait of the index's
+ * kernels gave up since the last check (CM_ERR_TIMEOUT; the results of that
+ * work are invalid).  Clears the flag. */
+cm_status cm_index_check(cm_index* ix, cm_stream stream);
 /* Recomputes centring statistics from the resident descriptors, then keys,
  * codes and buckets of every resident image (async; a whole hashing pass). */
 cm_status cm_index_rehash(cm_index* ix, cm_stream stream);

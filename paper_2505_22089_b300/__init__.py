@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libcashmatch.so")
 CM_OK, CM_ERR_INVALID, CM_ERR_BUDGET, CM_ERR_CUDA, CM_ERR_TIMEOUT, CM_ERR_NOMEM, CM_ERR_STATE = range(7)
 RERANK = {"fp32": 0, "bf16": 1, "fp8": 2, "int": 3}
 ALGO = {"auto": 0, "tile": 1, "warp": 2}
+PROJ = {"tc": 0, "ffma": 1}
 MEM_HOST, MEM_DEVICE, MEM_DEVICE_INPLACE = 0, 1, 2
 # Arena headroom the binding adds to cm_index_bytes for match-plan tables
 # (24 bytes per planned pair): room for about 600,000 pairs of plans.
@@ -30,7 +31,7 @@ EXPORTS = [
     "cm_version", "cm_last_error", "cm_params_default", "cm_params_check", "cm_make_weights", "cm_image_bytes",
     "cm_index_bytes", "cm_schedule_blocks", "cm_schedule_num_rows", "cm_schedule_num_iterations",
     "cm_schedule_get_row", "cm_free_schedule", "cm_gps_order", "cm_index_create", "cm_index_set_mean",
-    "cm_index_mean_device", "cm_index_col_sums", "cm_index_load", "cm_index_rehash", "cm_index_evict", "cm_build_index",
+    "cm_index_mean_device", "cm_index_col_sums", "cm_index_check", "cm_index_load", "cm_index_rehash", "cm_index_evict", "cm_build_index",
     "cm_index_image_view", "cm_index_destroy", "cm_match_plan_create", "cm_match_plan_rows", "cm_match_plan_run",
     "cm_match_plan_destroy", "cm_match_pairs", "cm_match_pair_noalloc",
 ]
@@ -45,12 +46,15 @@ class CMError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("m", ctypes.c_int32), ("n_bits", ctypes.c_int32), ("K", ctypes.c_int32),
                 ("ratio_num", ctypes.c_int32), ("ratio_den", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("rerank", ctypes.c_int32), ("query_tile", ctypes.c_int32), ("algo", ctypes.c_int32)]
+                ("rerank", ctypes.c_int32), ("query_tile", ctypes.c_int32), ("algo", ctypes.c_int32),
+                ("projection", ctypes.c_int32)]
 
     @classmethod
-    def make(cls, L=6, m=8, K=8, ratio=(4, 5), seed=0x5EED, rerank="fp32", query_tile=0, n_bits=128, algo="auto"):
+    def make(cls, L=6, m=8, K=8, ratio=(4, 5), seed=0x5EED, rerank="fp32", query_tile=0, n_bits=128, algo="auto",
+             projection="tc"):
         return cls(L, m, n_bits, K, ratio[0], ratio[1], seed, RERANK[rerank] if isinstance(rerank, str) else rerank,
-                   query_tile, ALGO[algo] if isinstance(algo, str) else algo)
+                   query_tile, ALGO[algo] if isinstance(algo, str) else algo,
+                   PROJ[projection] if isinstance(projection, str) else projection)
 
     @property
     def P(self):
@@ -98,6 +102,7 @@ def lib():
             "cm_index_set_mean": (i32, [vp, vp, u64, vp]),
             "cm_index_mean_device": (i32, [vp, vp, u64, vp]),
             "cm_index_col_sums": (i32, [vp, vp, ctypes.POINTER(u64), vp]),
+            "cm_index_check": (i32, [vp, vp]),
             "cm_index_load": (i32, [vp, i32, vp, vp, i32, vp]),
             "cm_index_rehash": (i32, [vp, vp]),
             "cm_index_evict": (i32, [vp, i32, vp, vp]),
@@ -292,6 +297,10 @@ class Index:
 
     def rehash(self, stream=None):
         check(lib().cm_index_rehash(self.h, _stream(stream)))
+
+    def check(self, stream=None):
+        """Raises CMError(CM_ERR_TIMEOUT) if a bounded device wait gave up."""
+        check(lib().cm_index_check(self.h, _stream(stream)))
 
     def image_view(self, image: int) -> dict:
         """Copies of a resident image's keys, codes and bucket tables (host numpy)."""

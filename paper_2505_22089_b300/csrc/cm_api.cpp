@@ -59,6 +59,7 @@ extern "C" cm_status cm_params_default(cm_params* p) {
     p->rerank = CM_RERANK_FP32;
     p->query_tile = 0;
     p->algo = CM_ALGO_AUTO;
+    p->projection = CM_PROJ_TC;
     return CM_OK;
 }
 
@@ -86,6 +87,8 @@ extern "C" cm_status cm_params_check(const cm_params* p) {
         return fail(CM_ERR_INVALID, "params: query_tile=%d must be 0 or a multiple of 64 in 64..8192",
                     p->query_tile);
     if (p->algo < CM_ALGO_AUTO || p->algo > CM_ALGO_WARP) return fail(CM_ERR_INVALID, "params: algo %d", p->algo);
+    if (p->projection != CM_PROJ_TC && p->projection != CM_PROJ_FFMA)
+        return fail(CM_ERR_INVALID, "params: projection %d", p->projection);
     const int S = query_tile(p);
     if (p->algo == CM_ALGO_TILE && match_smem_bytes(S, p->K) > 226 * 1024)
         return fail(CM_ERR_INVALID, "params: query_tile=%d with K=%d needs %zu bytes of shared memory (> 227 KB)", S,
@@ -165,7 +168,7 @@ SlotLayout slot_layout(const cm_params* p, int64_t n, bool inplace) {
 
 // Fixed tables at the start of the arena.
 struct FixedLayout {
-    uint64_t imgs, W, mu, sums, ntot, batch, tiles, rbatch, rtiles, total;
+    uint64_t imgs, W, mu, sums, ntot, batch, tiles, rbatch, rtiles, tiles128, rtiles128, bias, err, total;
 };
 
 FixedLayout fixed_layout(const cm_params* p, int n_images) {
@@ -181,6 +184,10 @@ FixedLayout fixed_layout(const cm_params* p, int n_images) {
     f.tiles = take((uint64_t)(n_images + 1) * 4);
     f.rbatch = take((uint64_t)n_images * 4);
     f.rtiles = take((uint64_t)(n_images + 1) * 4);
+    f.tiles128 = take((uint64_t)(n_images + 1) * 4);
+    f.rtiles128 = take((uint64_t)(n_images + 1) * 4);
+    f.bias = take((uint64_t)kMaxP * 4);
+    f.err = take(4);
     f.total = o;
     return f;
 }
@@ -327,13 +334,17 @@ struct cm_index {
     template <class T>
     T* at(uint64_t off) const { return reinterpret_cast<T*>(arena + off); }
 
-    HashLaunch hash_launch(bool resident_set, int n_batch, int n_tiles) const {
+    HashLaunch hash_launch(bool resident_set, int n_batch, int n_tiles, int n_tiles128) const {
         HashLaunch h{};
         h.imgs = at<DevImage>(fx.imgs);
         h.batch = at<int32_t>(resident_set ? fx.rbatch : fx.batch);
         h.tile_pref = at<int32_t>(resident_set ? fx.rtiles : fx.tiles);
+        h.tile_pref128 = at<int32_t>(resident_set ? fx.rtiles128 : fx.tiles128);
         h.n_batch = n_batch;
         h.n_tiles = n_tiles;
+        h.n_tiles128 = n_tiles128;
+        h.bias = at<float>(fx.bias);
+        h.err = at<int>(fx.err);
         h.W = at<float>(fx.W);
         h.mu = at<float>(fx.mu);
         h.L = p.L;
@@ -400,6 +411,7 @@ extern "C" cm_status cm_index_create(const cm_params* p, int32_t n_images, const
     if (e == cudaSuccess)
         e = cudaMemcpy(ix->arena + ix->fx.imgs, ix->h_imgs.data(), ix->h_imgs.size() * sizeof(DevImage),
                        cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(ix->arena + ix->fx.err, 0, 4);
     if (e != cudaSuccess) {
         delete ix;
         return fail(CM_ERR_CUDA, "cm_index_create: %s", cudaGetErrorString(e));
@@ -454,7 +466,7 @@ extern "C" cm_status cm_index_mean_device(cm_index* ix, const uint8_t* d_desc, u
 // Allocate slots, copy descriptors, refresh the device image table and the
 // load-batch table.  Returns the batch's hash-tile count.
 static cm_status stage_images(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc,
-                              int32_t mem, cudaStream_t s, int* n_tiles_out) {
+                              int32_t mem, cudaStream_t s, int* n_tiles_out, int* n_tiles128_out) {
     if (count < 0 || (count && (!ids || !desc))) return fail(CM_ERR_INVALID, "load: bad argument");
     if (mem != CM_MEM_HOST && mem != CM_MEM_DEVICE && mem != CM_MEM_DEVICE_INPLACE)
         return fail(CM_ERR_INVALID, "load: bad memory kind %d", mem);
@@ -467,7 +479,7 @@ static cm_status stage_images(cm_index* ix, int32_t count, const int32_t* ids, c
         seen[i] = 1;
     }
     const bool inplace = mem == CM_MEM_DEVICE_INPLACE;
-    std::vector<int32_t> batch(count), tiles(count + 1, 0);
+    std::vector<int32_t> batch(count), tiles(count + 1, 0), tiles128(count + 1, 0);
     int k_done = 0;
     for (int k = 0; k < count; ++k, ++k_done) {
         const int i = ids[k];
@@ -500,6 +512,7 @@ static cm_status stage_images(cm_index* ix, int32_t count, const int32_t* ids, c
         ix->resident[i] = 1;
         batch[k] = i;
         tiles[k + 1] = tiles[k] + (int)((n + kHashTile - 1) / kHashTile);
+        tiles128[k + 1] = tiles128[k] + (int)((n + 127) / 128);
         if (!inplace && n) {
             const cudaMemcpyKind kind = mem == CM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
             CM_CUDA(cudaMemcpyAsync(base + L.desc, desc[k], (size_t)n * kDim, kind, s));
@@ -509,23 +522,27 @@ static cm_status stage_images(cm_index* ix, int32_t count, const int32_t* ids, c
     cm_status st = upload_table(ix, ix->fx.imgs, ix->h_imgs.data(), ix->h_imgs.size() * sizeof(DevImage), s);
     if (st == CM_OK) st = upload_table(ix, ix->fx.batch, batch.data(), batch.size() * 4, s);
     if (st == CM_OK) st = upload_table(ix, ix->fx.tiles, tiles.data(), tiles.size() * 4, s);
+    if (st == CM_OK) st = upload_table(ix, ix->fx.tiles128, tiles128.data(), tiles128.size() * 4, s);
     if (st != CM_OK) return st;
     *n_tiles_out = tiles[count];
+    *n_tiles128_out = tiles128[count];
     return CM_OK;
 }
 
 // The resident-set table used by cm_index_rehash.
 static cm_status refresh_resident(cm_index* ix, cudaStream_t s, int* n_batch, int* n_tiles, uint64_t* rows) {
-    std::vector<int32_t> batch, tiles(1, 0);
+    std::vector<int32_t> batch, tiles(1, 0), tiles128(1, 0);
     uint64_t r = 0;
     for (int i = 0; i < ix->n_images; ++i) {
         if (!ix->resident[i]) continue;
         batch.push_back(i);
         tiles.push_back(tiles.back() + (ix->n_desc[i] + kHashTile - 1) / kHashTile);
+        tiles128.push_back(tiles128.back() + (ix->n_desc[i] + 127) / 128);
         r += (uint64_t)ix->n_desc[i];
     }
     cm_status st = upload_table(ix, ix->fx.rbatch, batch.data(), batch.size() * 4, s);
     if (st == CM_OK) st = upload_table(ix, ix->fx.rtiles, tiles.data(), tiles.size() * 4, s);
+    if (st == CM_OK) st = upload_table(ix, ix->fx.rtiles128, tiles128.data(), tiles128.size() * 4, s);
     *n_batch = (int)batch.size();
     *n_tiles = tiles.back();
     *rows = r;
@@ -534,8 +551,34 @@ static cm_status refresh_resident(cm_index* ix, cudaStream_t s, int* n_batch, in
 
 static cm_status hash_batch(cm_index* ix, const HashLaunch& h, cudaStream_t s) {
     if (h.n_batch == 0) return CM_OK;
-    CM_CUDA(launch_hash(h, ix->sms, s));
+    if (ix->p.projection == CM_PROJ_TC) {
+        CM_CUDA(launch_bias(ix->at<float>(ix->fx.W), ix->at<float>(ix->fx.mu), ix->P_pad, ix->at<float>(ix->fx.bias), s));
+        CM_CUDA(launch_hash_tc(h, ix->sms, s));
+    } else {
+        CM_CUDA(launch_hash(h, ix->sms, s));
+    }
     CM_CUDA(launch_bucket(h, s));
+    return CM_OK;
+}
+
+static int tiles_of(const cm_index* ix, int rows_per_tile) {
+    int t = 0;
+    for (int i = 0; i < ix->n_images; ++i)
+        if (ix->resident[i]) t += (ix->n_desc[i] + rows_per_tile - 1) / rows_per_tile;
+    return t;
+}
+
+extern "C" cm_status cm_index_check(cm_index* ix, cm_stream stream) {
+    if (!ix) return fail(CM_ERR_INVALID, "cm_index_check: NULL index");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int err = 0;
+    CM_CUDA(cudaMemcpyAsync(&err, ix->arena + ix->fx.err, 4, cudaMemcpyDeviceToHost, s));
+    CM_CUDA(cudaStreamSynchronize(s));
+    if (err) {
+        CM_CUDA(cudaMemsetAsync(ix->arena + ix->fx.err, 0, 4, s));
+        CM_CUDA(cudaStreamSynchronize(s));
+        return fail(CM_ERR_TIMEOUT, "a bounded device wait gave up; the affected results are invalid");
+    }
     return CM_OK;
 }
 
@@ -544,14 +587,14 @@ extern "C" cm_status cm_index_load(cm_index* ix, int32_t count, const int32_t* i
     if (!ix) return fail(CM_ERR_INVALID, "cm_index_load: NULL index");
     if (!ix->mean_set) return fail(CM_ERR_STATE, "cm_index_load: centring mean not set");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    int n_tiles = 0;
-    cm_status st = stage_images(ix, count, ids, desc, mem, s, &n_tiles);
+    int n_tiles = 0, n_tiles128 = 0;
+    cm_status st = stage_images(ix, count, ids, desc, mem, s, &n_tiles, &n_tiles128);
     if (st != CM_OK) return st;
     int rb = 0, rt = 0;
     uint64_t rows = 0;
     st = refresh_resident(ix, s, &rb, &rt, &rows);
     if (st != CM_OK) return st;
-    return hash_batch(ix, ix->hash_launch(false, count, n_tiles), s);
+    return hash_batch(ix, ix->hash_launch(false, count, n_tiles, n_tiles128), s);
 }
 
 extern "C" cm_status cm_index_rehash(cm_index* ix, cm_stream stream) {
@@ -567,7 +610,7 @@ extern "C" cm_status cm_index_rehash(cm_index* ix, cm_stream stream) {
             rows += (uint64_t)ix->n_desc[i];
         }
     if (!nb) return fail(CM_ERR_STATE, "cm_index_rehash: no resident image");
-    const HashLaunch h = ix->hash_launch(true, nb, nt);
+    const HashLaunch h = ix->hash_launch(true, nb, nt, tiles_of(ix, 128));
     unsigned long long* sums = ix->at<unsigned long long>(ix->fx.sums);
     CM_CUDA(cudaMemsetAsync(sums, 0, kDim * 8, s));
     CM_CUDA(launch_colsum_images(h, sums, s));
@@ -618,14 +661,14 @@ extern "C" cm_status cm_build_index(const cm_params* p, int32_t n_images, const 
         ptrs[i] = desc + row * kDim;
         row += (uint64_t)n_desc[i];
     }
-    int n_tiles = 0;
-    st = stage_images(ix, n_images, ids.data(), ptrs.data(), mem, s, &n_tiles);
+    int n_tiles = 0, n_tiles128 = 0;
+    st = stage_images(ix, n_images, ids.data(), ptrs.data(), mem, s, &n_tiles, &n_tiles128);
     int rb = 0, rt = 0;
     uint64_t rows = 0;
     if (st == CM_OK) st = refresh_resident(ix, s, &rb, &rt, &rows);
     if (st == CM_OK) {
         // centring mean over every descriptor of the index, then hash all images
-        const HashLaunch h = ix->hash_launch(false, n_images, n_tiles);
+        const HashLaunch h = ix->hash_launch(false, n_images, n_tiles, n_tiles128);
         unsigned long long* sums = ix->at<unsigned long long>(ix->fx.sums);
         cudaError_t e = cudaMemsetAsync(sums, 0, kDim * 8, s);
         if (e == cudaSuccess) e = launch_colsum_images(h, sums, s);

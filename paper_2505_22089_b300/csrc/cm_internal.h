@@ -48,9 +48,13 @@ struct DevPair {
 struct HashLaunch {
     const DevImage* imgs;
     const int32_t* batch;      // image ids of the batch
-    const int32_t* tile_pref;  // [n_batch+1] prefix of hash tiles per image
+    const int32_t* tile_pref;  // [n_batch+1] prefix of 64-row tiles per image
+    const int32_t* tile_pref128;  // [n_batch+1] prefix of 128-row tiles per image (tensor-core kernel)
     int32_t n_batch;
     int32_t n_tiles;
+    int32_t n_tiles128;
+    const float* bias;         // [P_pad] mu . W (tensor-core kernel)
+    int* err;                  // set to 1 when a bounded device wait gives up
     const float* W;            // [128][P_pad]
     const float* mu;           // [128]
     int32_t L, m, P_pad;
@@ -77,7 +81,9 @@ cudaError_t launch_colsum_images(const HashLaunch& h, unsigned long long* sums, 
 cudaError_t launch_mean(const unsigned long long* sums, const unsigned long long* n_total_dev, uint64_t n_total,
                         float* mu, cudaStream_t s);
 cudaError_t launch_count_rows(const HashLaunch& h, unsigned long long* n_total, cudaStream_t s);
-cudaError_t launch_hash(const HashLaunch& h, int sm_count, cudaStream_t s);
+cudaError_t launch_hash(const HashLaunch& h, int sm_count, cudaStream_t s);       // CUDA-core FP32 projection
+cudaError_t launch_hash_tc(const HashLaunch& h, int sm_count, cudaStream_t s);    // tensor-core projection (cm_hash_tc.cu)
+cudaError_t launch_bias(const float* W, const float* mu, int P_pad, float* bias, cudaStream_t s);
 cudaError_t launch_bucket(const HashLaunch& h, cudaStream_t s);
 cudaError_t launch_match(const MatchLaunch& m, int sm_count, cudaStream_t s);      // lane per query (cm_match.cu)
 cudaError_t launch_match_wq(const MatchLaunch& m, int sm_count, cudaStream_t s);   // warp per query (cm_match_wq.cu)

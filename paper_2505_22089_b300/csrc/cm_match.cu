@@ -51,16 +51,24 @@ __device__ __forceinline__ uint32_t ham128(uint4 a, uint4 b) {
 }
 
 // Lockstep flush of the buffered hits (Hamming << 16 | run offset) of every lane.
+// Database indices of 8 entries are requested together, then merged.
 template <int K>
 __device__ __forceinline__ void flush_hits(const uint32_t* __restrict__ buf, int cnt, const uint16_t* __restrict__ idx,
                                            uint32_t c0, uint32_t (&s)[K]) {
     const int cmax = (int)__reduce_max_sync(kFull, (unsigned)cnt);
-    for (int e = 0; e < cmax; ++e) {
-        if (e < cnt) {
-            const uint32_t v = buf[e * kMatchThreads];
-            const uint32_t key = (v & 0xFFFF0000u) | (uint32_t)__ldg(idx + c0 + (v & 0xFFFFu));
-            if (key < s[K - 1]) topk_insert<K>(s, key);
+    for (int e0 = 0; e0 < cmax; e0 += 8) {
+        uint32_t key[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            key[u] = kEmpty;
+            if (e0 + u < cnt) {
+                const uint32_t v = buf[(e0 + u) * kMatchThreads];
+                key[u] = (v & 0xFFFF0000u) | (uint32_t)__ldg(idx + c0 + (v & 0xFFFFu));
+            }
         }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (key[u] < s[K - 1]) topk_insert<K>(s, key[u]);
     }
 }
 
@@ -73,19 +81,50 @@ __device__ __forceinline__ void scan_run(const uint4* __restrict__ codes, const 
     const uint32_t len = c1 - c0;
     const uint32_t lmax = __reduce_max_sync(kFull, len);
     uint32_t i = 0;
-    // while a list is not full every candidate is a hit for every lane: insert directly
+    // while a list is not full every candidate is a hit for every lane: insert
+    // directly, 8 candidates' loads at a time
     if (__any_sync(kFull, s[K - 1] == kEmpty)) {
         const uint32_t n = min(lmax, (uint32_t)kFill);
-        for (; i < n; ++i) {
-            if (i < len) {
-                const uint32_t h = ham128(__ldg(codes + c0 + i), q);
-                const uint32_t key = (h << 16) | (uint32_t)__ldg(idx + c0 + i);
-                if (key < s[K - 1]) topk_insert<K>(s, key);
+        for (; i < n; i += 8) {
+            uint32_t key[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                key[u] = kEmpty;
+                if (i + u < min(len, n)) {
+                    const uint32_t h = ham128(__ldg(codes + c0 + i + u), q);
+                    key[u] = (h << 16) | (uint32_t)__ldg(idx + c0 + i + u);
+                }
             }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (key[u] < s[K - 1]) topk_insert<K>(s, key[u]);
         }
+        i = n;
     }
     uint32_t kth = s[K - 1];
     int cnt = 0;
+    // common part: every lane has kUnroll candidates left (no per-candidate predicates)
+    const uint32_t lmin = __reduce_min_sync(kFull, len);
+    for (; i + kUnroll <= lmin; i += kUnroll) {
+        uint4 x[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) x[u] = __ldg(codes + c0 + i + u);
+        const uint32_t kh = kth >> 16;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint32_t h = ham128(x[u], q);
+            if (h <= kh) {
+                buf[cnt * kMatchThreads] = (h << 16) | (i + u);
+                ++cnt;
+            }
+        }
+        if (__any_sync(kFull, cnt > kHitCap - kUnroll)) {
+            flush_hits<K>(buf, cnt, idx, c0, s);
+            cnt = 0;
+            kth = s[K - 1];
+        }
+    }
+    // ragged part
     for (; i < lmax; i += kUnroll) {
         uint4 x[kUnroll];
 #pragma unroll

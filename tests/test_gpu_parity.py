@@ -61,6 +61,14 @@ def test_strip30_full_block(algo):
     _run(synth.strip30(), cm.Params.make(algo=algo), threads=16)
 
 
+@pytest.mark.parametrize("projection", ["tc", "ffma"])
+@pytest.mark.parametrize("kw", [dict(), dict(L=8, m=8), dict(L=1, m=0), dict(L=3, m=5)])
+def test_projection_forms(projection, kw):
+    # tensor-core (BF16x3, FP32 accumulate) and CUDA-core FP32 projections: every
+    # bit that differs from the FP64 oracle must be marginal
+    _run(synth.pair2k(n=3000, shared=1000), cm.Params.make(projection=projection, **kw))
+
+
 @pytest.mark.parametrize("algo", ["tile", "warp"])
 def test_uneven_sizes_including_tiny_images(algo):
     wl = synth.grid500(gx=5, gy=4, nmin=1, nmax=5000)
