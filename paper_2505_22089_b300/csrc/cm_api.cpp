@@ -68,7 +68,7 @@ extern "C" cm_status cm_params_default(cm_params* p) {
 static int query_tile(const cm_params* p) {
     if (p->query_tile) return p->query_tile;
     int S = kDefaultQueryTile;
-    while (S > 64 && match_smem_bytes(S, p->K) > 226 * 1024) S -= 64;
+    while (S > 64 && match_smem_bytes(S, p->K) > kMatchSmemLimit) S -= 64;
     return S;
 }
 
@@ -81,7 +81,7 @@ extern "C" cm_status cm_params_check(const cm_params* p) {
         return fail(CM_ERR_INVALID, "params: K=%d not in {2,4,8,16}", p->K);
     if (p->ratio_den < 1 || p->ratio_num < 0 || p->ratio_num > 4 * p->ratio_den)
         return fail(CM_ERR_INVALID, "params: ratio %d/%d out of range", p->ratio_num, p->ratio_den);
-    if (p->rerank != CM_RERANK_FP32 && p->rerank != CM_RERANK_INT)
+    if (p->rerank < CM_RERANK_FP32 || p->rerank > CM_RERANK_INT)
         return fail(CM_ERR_INVALID, "params: rerank mode %d not available", p->rerank);
     if (p->query_tile != 0 && (p->query_tile < 64 || p->query_tile > 8192 || p->query_tile % 64))
         return fail(CM_ERR_INVALID, "params: query_tile=%d must be 0 or a multiple of 64 in 64..8192",
@@ -90,7 +90,9 @@ extern "C" cm_status cm_params_check(const cm_params* p) {
     if (p->projection != CM_PROJ_TC && p->projection != CM_PROJ_FFMA)
         return fail(CM_ERR_INVALID, "params: projection %d", p->projection);
     const int S = query_tile(p);
-    if (p->algo == CM_ALGO_TILE && match_smem_bytes(S, p->K) > 226 * 1024)
+    if ((p->rerank == CM_RERANK_BF16 || p->rerank == CM_RERANK_FP8) && p->algo == CM_ALGO_WARP)
+        return fail(CM_ERR_INVALID, "params: the tensor-core reranks run in the tile kernel (algo tile or auto)");
+    if (p->algo == CM_ALGO_TILE && match_smem_bytes(S, p->K) > kMatchSmemLimit)
         return fail(CM_ERR_INVALID, "params: query_tile=%d with K=%d needs %zu bytes of shared memory (> 227 KB)", S,
                     p->K, match_smem_bytes(S, p->K));
     return CM_OK;
@@ -159,9 +161,8 @@ SlotLayout slot_layout(const cm_params* p, int64_t n, bool inplace) {
     s.hist = take((uint64_t)p->L * B * 4);
     s.brank = take((uint64_t)p->L * 256);
     s.norm = take((uint64_t)n * 4);
-    const uint64_t xq_bytes = p->rerank == CM_RERANK_BF16 ? 256 : (p->rerank == CM_RERANK_FP8 ? 128 : 0);
-    s.xq = xq_bytes ? take((uint64_t)n * xq_bytes) : 0;
-    s.xscale = p->rerank == CM_RERANK_FP8 ? take((uint64_t)n * 4) : 0;
+    s.xq = 0;       // tensor-core reranks convert rows while staging them: no stored copy
+    s.xscale = 0;
     s.total = o;
     return s;
 }
@@ -777,7 +778,8 @@ extern "C" cm_status cm_match_plan_run(cm_match_plan* pl, const cm_match_out* ou
     m.counter = counter;
     m.out = *out;
     m.algo = ix->p.algo == CM_ALGO_WARP ? CM_ALGO_WARP : CM_ALGO_TILE;   // auto: tile, if its tile fits
-    if (m.algo == CM_ALGO_TILE && match_smem_bytes(m.S, m.K) > 226 * 1024) m.algo = CM_ALGO_WARP;
+    if (m.algo == CM_ALGO_TILE && match_smem_bytes(m.S, m.K) > kMatchSmemLimit) m.algo = CM_ALGO_WARP;
+    m.err = ix->at<int>(ix->fx.err);
     CM_CUDA(m.algo == CM_ALGO_TILE ? launch_match(m, ix->sms, s) : launch_match_wq(m, ix->sms, s));
     return CM_OK;
 }

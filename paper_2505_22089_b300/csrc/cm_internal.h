@@ -15,6 +15,7 @@ constexpr int kHashTile = 64;      // descriptors per hash tile
 constexpr int kHashThreads = 256;
 constexpr int kMatchThreads = 1024;
 constexpr int kDefaultQueryTile = 2048;  // queries per work item
+constexpr size_t kMatchSmemLimit = 220 * 1024;  // dynamic shared memory of the tile kernel (static extra)
 constexpr int kWqThreads = 256;          // warp-per-query matcher: 8 warps per CTA
 constexpr int kWqBlocksPerSM = 3;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
@@ -72,6 +73,7 @@ struct MatchLaunch {
     int32_t rerank;
     int32_t algo;              // CM_ALGO_TILE or CM_ALGO_WARP
     unsigned* counter;         // work counter (zeroed before each launch)
+    int* err;                  // set to 1 when a bounded device wait gives up
     cm_match_out out;
 };
 

@@ -27,6 +27,11 @@
 #include "cm_internal.h"
 
 namespace cm {
+__device__ __forceinline__ bool ratio_pass(uint32_t d1, uint32_t d2, int num, int den, uint32_t& rechecks);
+}
+#include "cm_rerank_tc.cuh"
+
+namespace cm {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kUnroll = 4;        // candidates per lane per loop step
@@ -177,12 +182,23 @@ __global__ void __launch_bounds__(kMatchThreads, 1) k_match(MatchLaunch ml) {
     uint32_t* order = hist + 256;                                 // [256] bucket -> rank by run length
     uint32_t* hitbuf = order + 256;                               // [kHitCap][kMatchThreads]
     __shared__ int s_item;
-    __shared__ uint32_t s_stats[2];
+    __shared__ uint32_t s_stats[3];
+    __shared__ uint64_t s_mbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ float s_scales[6 * 192];   // FP8 rerank: per-row scales of the staged sub-tiles
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int B = 1 << ml.m;
-    if (tid < 2) s_stats[tid] = 0;
-    uint32_t rechecks = 0, matches = 0;
+    const bool tcr = ml.rerank == CM_RERANK_BF16 || ml.rerank == CM_RERANK_FP8;
+    if (tid < 3) s_stats[tid] = 0;
+    uint32_t rechecks = 0, matches = 0, swaps = 0, parity = 0;
+    if (tcr) {
+        if (tid == 0) tc::mbar_init(&s_mbar, 1);
+        if ((tid >> 5) == 0) tc::tmem_alloc(&s_tmem, 256);
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+    }
 
     for (;;) {
         __syncthreads();
@@ -283,7 +299,20 @@ __global__ void __launch_bounds__(kMatchThreads, 1) k_match(MatchLaunch ml) {
             __syncthreads();
         }
 
-        // Sec. 2.3.1 step (4): exact distances of the top K, q1 / q2, ratio test.
+        // Sec. 2.3.1 step (4) on the tensor cores (BF16 / FP8 forms)
+        if (tcr) {
+            unsigned char* region = reinterpret_cast<unsigned char*>(qcode);
+            // qcode .. the end of the hit buffer is free after the table passes
+            const uint32_t region_bytes = (uint32_t)S * 28 + 2 * 256 * 4 + (uint32_t)kHitCap * kMatchThreads * 4;
+            if (ml.rerank == CM_RERANK_BF16)
+                rerank_tc<K, false>(ml, P, I, J, q0, nq, st, region, region_bytes, s_scales, s_tmem, &s_mbar, parity,
+                                    rechecks, matches, swaps);
+            else
+                rerank_tc<K, true>(ml, P, I, J, q0, nq, st, region, region_bytes, s_scales, s_tmem, &s_mbar, parity,
+                                   rechecks, matches, swaps);
+            continue;
+        }
+        // Sec. 2.3.1 step (4) on CUDA cores: exact distances of the top K, q1 / q2, ratio test.
         // 8 lanes per query, 16 descriptor bytes per lane.
         const int g = tid >> 3, l8 = tid & 7;
         const int rounds = (nq + (kMatchThreads / 8) - 1) / (kMatchThreads / 8);
@@ -348,7 +377,9 @@ __global__ void __launch_bounds__(kMatchThreads, 1) k_match(MatchLaunch ml) {
             if (active) {
                 const int64_t row = P.row_off + q0 + q;
                 bool pass = false;
-                if (j2 >= 0) pass = ratio_pass(d1, d2, ml.ratio_num, ml.ratio_den, rechecks);
+                uint32_t rc = 0;
+                if (j2 >= 0) pass = ratio_pass(d1, d2, ml.ratio_num, ml.ratio_den, rc);
+                if (l8 == 0) rechecks += rc;
                 if (l8 == 0) {
                     ml.out.best_j[row] = pass ? j1 : -1;
                     if (ml.out.d1sq) ml.out.d1sq[row] = d1;
@@ -364,16 +395,19 @@ __global__ void __launch_bounds__(kMatchThreads, 1) k_match(MatchLaunch ml) {
             }
         }
     }
+    if (tcr) {
+        __syncthreads();
+        if ((tid >> 5) == 0) tc::tmem_dealloc(s_tmem, 256);
+    }
     if (ml.out.stats) {
-        // every lane of an 8-lane group counted the same re-checks; keep one per group
-        if ((tid & 7) == 0) {
-            atomicAdd(&s_stats[0], rechecks);
-            atomicAdd(&s_stats[1], matches);
-        }
+        if (rechecks) atomicAdd(&s_stats[0], rechecks);
+        if (matches) atomicAdd(&s_stats[1], matches);
+        if (swaps) atomicAdd(&s_stats[2], swaps);
         __syncthreads();
         if (tid == 0) {
             atomicAdd(&ml.out.stats[0], s_stats[0]);
             atomicAdd(&ml.out.stats[1], s_stats[1]);
+            atomicAdd(&ml.out.stats[2], s_stats[2]);
         }
     }
     (void)lane;

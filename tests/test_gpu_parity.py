@@ -184,3 +184,43 @@ def test_plan_rerun_is_deterministic():
     for o in outs[1:]:
         for k in o:
             assert np.array_equal(o[k], outs[0][k])
+
+
+@pytest.mark.parametrize("K", [2, 4, 8, 16])
+def test_bf16_tensor_core_rerank_is_exact(K):
+    # BF16 holds uint8 exactly and the FP32 accumulation of integer products is
+    # exact, so the tcgen05 rerank must equal the oracle bit for bit
+    _run(synth.pair2k(n=1500, shared=600), cm.Params.make(rerank="bf16", K=K))
+
+
+def test_bf16_tensor_core_rerank_full_strip():
+    _run(synth.strip30(), cm.Params.make(rerank="bf16"), threads=16)
+
+
+@pytest.mark.parametrize("K", [2, 4, 8, 16])
+def test_fp8_tensor_core_rerank(K):
+    # E4M3 distances pick q1, q2, which are re-scored exactly: top-K lists are
+    # exact, re-scored distances are exact wherever the decision agrees, and the
+    # decisions agree with the oracle on >= 99.5 % of queries
+    wl = synth.strip30(n_images=6, n=4000)
+    desc = wl.generate()
+    p = cm.Params.make(rerank="fp8", K=K)
+    index = cm.Index.build(p, wl.n_desc, torch.from_numpy(desc).cuda())
+    plan, res = gpu_match(index, wl.pairs)
+    oix = oracle.Index(desc, wl.n_desc, oparams(p))
+    affected, *_ = compare_hash(index, oix, range(wl.n_images), p)
+    same = total = 0
+    for k, (i, j) in enumerate(wl.pairs):
+        r0, r1 = plan.row_off[k], plan.row_off[k + 1]
+        o = oracle.match_pair(oix.image(i), oix.image(j), oparams(p), topk=True)
+        from gpu_common import affected_queries
+        ok = ~affected_queries(p, oix, int(i), int(j), affected, o["topk"])
+        assert np.array_equal(res["topk"][r0:r1][ok], o["topk"][ok])
+        g = res["best_j"][r0:r1]
+        agree = (g == o["best_j"]) & ok
+        same += int(agree.sum())
+        total += int(ok.sum())
+        both = agree & (g >= 0)
+        assert np.array_equal(res["d1sq"][r0:r1][both], o["d1sq"][both])
+    assert same / total >= 0.995, same / total
+    print("fp8 K=%d decision agreement %.5f, top-2 re-score swaps %d" % (K, same / total, res["stats"][2]))
