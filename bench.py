@@ -2,15 +2,18 @@
 """Throughput of cascade-hashing feature matching on one B300: pairs matched/s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload grid5000]
-                    [--rerank fp32|int|bf16|fp8] [--impl ours|reference]
+                    [--rerank bf16|fp8|fp32|int] [--impl ours|reference]
 
-A step is one pass of the whole hot path over the workload: centring
-statistics, projection to bucket keys and codes, bucket construction, and the
-persistent fused match launch of every block row (lookup, Hamming top-K,
-rerank, ratio test).  `value` times steps whose descriptors are already
-resident in HBM; `e2e` times the same work through the C ABI with the
-descriptors in pinned host memory (H2D inside the step) and the per-query
-results copied back (D2H inside the step).
+A step is one pass of the whole hot path over the workload's MBR block rows:
+centring statistics, projection to bucket keys and codes, bucket
+construction, then per block row one persistent fused match launch (lookup,
+Hamming top-K, rerank, ratio test) and the compaction of its decisions into
+per-pair match lists.  `value` replays that step as one captured CUDA graph
+with the descriptors already resident in HBM (headline rerank form; the other
+forms are timed the same way under "forms").  `e2e` runs the public pipeline
+call with the descriptors in pinned host memory: H2D, matching and the D2H of
+the match lists are inside its timed region.  "pipeline_verified" repeats it
+with affine RANSAC on the host cores overlapped with the GPU rows.
 
 The workloads are synthetic stand-ins for the paper's UAV datasets (see
 synth/).  `--impl reference` times the FP64 CPU oracle on the host cores on a
@@ -45,7 +48,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="grid5000", choices=sorted(synth.WORKLOADS))
-    ap.add_argument("--rerank", default="fp32", choices=["fp32", "int", "bf16", "fp8"])
+    ap.add_argument("--rerank", default="bf16", choices=["fp32", "int", "bf16", "fp8"], help="headline form")
+    ap.add_argument("--forms", default="all", choices=["all", "one"], help="also time the other rerank forms")
+    ap.add_argument("--K", type=int, default=8)
+    ap.add_argument("--verify-workers", type=int, default=-1,
+                    help="CPU threads of the overlapped RANSAC run (-1: all host cores, 0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--algo", default="auto", choices=["auto", "tile", "warp"], help="match kernel thread mapping")
     ap.add_argument("--projection", default="tc", choices=["tc", "ffma"], help="hash projection: tensor cores or FP32 FFMA")
@@ -148,6 +155,139 @@ def make_workload(args):
     return synth.workload(args.workload)
 
 
+def _sync_ms(ms, world, dev):
+    """Max over ranks of a per-rank time (weak scaling: the job ends with the slowest rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def device_forms(args, wl, desc_dev, rows, stream, dev, world, forms):
+    """Device-resident steps, one per rerank form: descriptors already in HBM;
+    a step = the captured block sequence (rehash of every resident image, then
+    per block row one fused match launch and its compaction) replayed as one
+    CUDA graph.  The headline form (first) is also run once more per step
+    without the graph with CUDA events around each match launch, which gives
+    the k_match launch duration behind the roofline figure."""
+    import torch
+    import paper_2505_22089_b300 as cm
+    pairs = wl.pairs
+    res = {}
+    ref_best = None
+    headline = forms[0]
+    for form in forms:
+        p = cm.Params.make(rerank=form, algo=args.algo, projection=args.projection, K=args.K)
+        with torch.cuda.stream(stream):
+            index = cm.Index.build(p, wl.n_desc, desc_dev, stream=stream)
+            plans = [cm.MatchPlan(index, pairs[r], stream=stream) for r in rows]
+            outs = [pl.alloc_out(d12=False) for pl in plans]
+            comps = [cm.compact_out(pl) for pl in plans]
+        stream.synchronize()
+        seq = cm.Sequence(index, plans, outs, comps, rehash=True, stream=stream)
+        for _ in range(args.warmup):
+            seq.launch(stream)
+        stream.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            start.record(stream)
+            for _ in range(args.steps):
+                seq.launch(stream)
+            stop.record(stream)
+            stop.synchronize()
+        torch.cuda.synchronize()
+        ms = _sync_ms(start.elapsed_time(stop) / args.steps, world, dev)
+        index.check(stream)
+        r = {"ms_per_step": ms, "value": len(pairs) * world / (ms / 1e3), "graph_kernels": seq.kernels,
+             "clocks": clk.summary()}
+        best = torch.cat([o["best_j"][:pl.rows] for pl, o in zip(plans, outs)])
+        n_match = int(sum(int(c["total"].item()) for c in comps))
+        r["matches"] = n_match
+        assert n_match == int((best >= 0).sum().item())
+        if form == "fp32":
+            ref_best = best
+        elif ref_best is not None:
+            same = int((best == ref_best).sum().item())
+            inter = int(((best == ref_best) & (best >= 0)).sum().item())
+            union = int((best >= 0).sum().item()) + int((ref_best >= 0).sum().item()) - inter
+            r["decision_agreement_vs_fp32"] = same / best.numel()
+            r["match_jaccard_vs_fp32"] = inter / union if union else 1.0
+        if form == headline:
+            # the same launches without the graph, events around every match launch
+            evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in plans]
+                   for _ in range(args.steps)]
+            for s in range(args.steps):
+                index.rehash(stream)
+                for k, (pl, o) in enumerate(zip(plans, outs)):
+                    evs[s][k][0].record(stream)
+                    pl.run(o, stream)
+                    evs[s][k][1].record(stream)
+            stream.synchronize()
+            launch_ms = [e[k][0].elapsed_time(e[k][1]) for e in evs for k in range(len(plans))]
+            r["match_launch_ms"] = float(np.mean(launch_ms))
+            r["match_ms_per_step"] = float(np.sum(launch_ms)) / args.steps
+            r["evals_per_step"] = bucket_evaluations(index, wl, pairs)
+            r["launches"] = len(plans)
+            gpu_rows = {}
+            for pl, o, rr in zip(plans, outs, rows):
+                bj = o["best_j"].cpu().numpy()
+                for q, k in enumerate(rr):
+                    gpu_rows[int(k)] = bj[pl.row_off[q]:pl.row_off[q + 1]]
+            r["_gpu_rows"] = gpu_rows
+            r["_sums"] = index.col_sums(stream)[0]
+        res[form] = r
+        seq.close()
+        for pl in plans:
+            pl.close()
+        index.close()
+        del seq, plans, outs, comps, index, best
+        torch.cuda.empty_cache()
+    return res
+
+
+def pipeline_e2e(args, wl, host, kp, sums, stream, world, dev):
+    """End to end through the public pipeline call (cm_run_schedule): per block
+    row, H2D of the row's new images from pinned host memory, hashing, one fused
+    match launch, compaction straight into pinned host memory, release of the
+    freed images.  Timed by the host clock around the call."""
+    import torch
+    import paper_2505_22089_b300 as cm
+    p = cm.Params.make(rerank=args.rerank, algo=args.algo, projection=args.projection, K=args.K)
+    sched = cm.schedule_blocks(wl.pairs, wl.n_desc, p, int(args.budget_gb * 2 ** 30), args.block_images)
+    index = cm.Index(p, wl.n_desc, arena_bytes=cm.schedule_arena_bytes(sched, p, wl.n_desc))
+    index.set_mean(sums, wl.total_desc, stream)
+    off = wl.row_off
+    hl = [host[off[i]:off[i + 1]] for i in range(wl.n_images)]
+    walls, stats = [], None
+    for s in range(args.e2e_steps + 1):
+        if world > 1:
+            torch.distributed.barrier()
+        stats, _ = cm.run_schedule(index, sched, hl, verify=None, workers=1, stream=stream)
+        if s > 0:
+            walls.append(stats["wall_ms"])
+    ms = _sync_ms(float(np.mean(walls)), world, dev)
+    out = {"value": len(wl.pairs) * world / (ms / 1e3), "unit": "pairs/s", "ms_per_step": ms,
+           "h2d_bytes_per_step": int(stats["h2d_bytes"]), "d2h_bytes_per_step": int(stats["d2h_bytes"]),
+           "block_rows": stats["rows"], "kernels_per_step": int(stats["kernels"]),
+           "form": "cm_run_schedule, host descriptors (pinned) in, per-pair match lists (pinned host) out"}
+    ver = None
+    if kp is not None and args.verify_workers > 0:
+        kl = [kp[off[i]:off[i + 1]] for i in range(wl.n_images)]
+        st, inl = cm.run_schedule(index, sched, hl, verify="affine", keypoints=kl, thresh_px=4.0,
+                                  workers=args.verify_workers, stream=stream)
+        ver = {k: (round(v, 2) if isinstance(v, float) else v) for k, v in st.items()}
+        ver["inlier_share"] = float(inl.sum() / max(1, st["matches"]))
+        ver["overlap"] = "GPU rows overlap CPU verification when wall_ms < gpu_ms + verify_ms / workers"
+    index.close()
+    sched.close()
+    return out, ver
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2505_22089_b300 as cm
@@ -162,104 +302,49 @@ def run_ours(args, rank, world, local):
     pairs = wl.pairs
     t0 = time.time()
     host = torch.empty((total, 128), dtype=torch.uint8, pin_memory=True)
-    wl.generate(desc=host.numpy())
+    kp = None
+    if args.verify_workers > 0:
+        _, kp = wl.generate(desc=host.numpy(), want_kp=True)
+    else:
+        wl.generate(desc=host.numpy())
     gen_s = time.time() - t0
-    p = cm.Params.make(rerank=args.rerank, algo=args.algo, projection=args.projection)
     stream = torch.cuda.Stream(device=dev)
-
-    # schedule blocks (MBR) under the HBM budget
+    p = cm.Params.make(rerank=args.rerank, algo=args.algo, projection=args.projection, K=args.K)
     sched = cm.schedule_blocks(pairs, n_desc, p, int(args.budget_gb * 2 ** 30), args.block_images)
     rows = [np.asarray(r["pairs"], dtype=np.int64) for r in sched.rows if r["pairs"]]
+    n_iter = sched.iterations
+    sched.close()
 
-    # ---- device-resident: descriptors in HBM before the timed region
+    # ---- device-resident steps (graph replay), every form
+    forms = [args.rerank] + ([f for f in ("fp32", "int", "bf16", "fp8") if f != args.rerank]
+                             if args.forms == "all" else [])
     desc_dev = host.to(dev, non_blocking=False)
-    with torch.cuda.stream(stream):
-        index = cm.Index.build(p, n_desc, desc_dev, stream=stream)
-        plans = [cm.MatchPlan(index, pairs[r], stream=stream) for r in rows]
-        n_rows = sum(pl.rows for pl in plans)
-        outs = [{"best_j": torch.empty(max(pl.rows, 1), dtype=torch.int32, device=dev)} for pl in plans]
-    stream.synchronize()
-    sums, _ = index.col_sums(stream)
+    fr = device_forms(args, wl, desc_dev, rows, stream, dev, world, forms)
+    head = fr[args.rerank]
+    gpu_rows, sums = head.pop("_gpu_rows"), head.pop("_sums")
+    del desc_dev
+    torch.cuda.empty_cache()
+    ms = head["ms_per_step"]
+    value = head["value"]
 
-    def step(ev=None):
-        index.rehash(stream)
-        for k, (pl, o) in enumerate(zip(plans, outs)):
-            if ev is not None:
-                ev[k][0].record(stream)
-            pl.run(o, stream)
-            if ev is not None:
-                ev[k][1].record(stream)
-
-    for _ in range(args.warmup):
-        step()
-    stream.synchronize()
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in plans] for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        start.record(stream)
-        for s in range(args.steps):
-            step(evs[s])
-        stop.record(stream)
-        stop.synchronize()
-    torch.cuda.synchronize()
-    ms = start.elapsed_time(stop) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    match_ms = [sum(e[k][0].elapsed_time(e[k][1]) for k in range(len(plans))) for e in evs]
-    gpu_rows = {}
-    for pl, o, r in zip(plans, outs, rows):
-        bj = o["best_j"].cpu().numpy()
-        for q, k in enumerate(r):
-            gpu_rows[int(k)] = bj[pl.row_off[q]:pl.row_off[q + 1]]
-    match_launch_ms = float(np.mean(match_ms)) / max(1, len(plans))
-    n_pairs = len(pairs)
-    value = n_pairs * world / (ms / 1e3)
-
-    # algorithmic work of the match kernel: candidate evaluations (4 POPC each)
-    evals = bucket_evaluations(index, wl, pairs)
-    clocks = clk.summary()
+    # roofline: candidate evaluations of the match launch (4 POPC each) against the POPC pipe
     pk, pk_kind = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2032.0))
     popc_peak = POPC_PER_CLK_PER_SM * SM_COUNT * sm_mhz * 1e6
-    achieved = 4.0 * evals / len(plans) / (match_launch_ms / 1e3)
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": popc_peak / 1e12,
-                "unit": "Tpopc/s", "frac": achieved / popc_peak, "traffic": None,
+    evals = head["evals_per_step"]
+    achieved = 4.0 * evals / head["launches"] / (head["match_launch_ms"] / 1e3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": popc_peak / 1e12, "unit": "Tpopc/s",
+                "frac": achieved / popc_peak, "traffic": None,
                 "peak_kind": "derived: %d POPC/clk/SM (measured) x %d SMs x %.0f MHz (%s max clock)"
                              % (POPC_PER_CLK_PER_SM, SM_COUNT, sm_mhz, pk_kind),
-                "kernel": "k_match", "evals_per_step": evals, "match_ms_per_step": float(np.mean(match_ms))}
+                "kernel": "k_match", "evals_per_step": evals, "match_launch_ms": head["match_launch_ms"],
+                "match_ms_per_step": head["match_ms_per_step"],
+                "match_share_of_step": head["match_ms_per_step"] / ms}
 
-    # ---- end to end through the C ABI: host descriptors in, host results out
-    e2e_ms = [float("nan")]
-    h2d = total * 128
-    best_host = torch.empty(n_rows, dtype=torch.int32, pin_memory=True)
-    del plans, outs, index
-    torch.cuda.empty_cache()
+    # ---- end to end through the pipeline call, then the same with CPU verification overlapped
+    e2e, verified = (None, None)
     if args.e2e_steps > 0:
-        e2e_ms = []
-    for s in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        with torch.cuda.stream(stream):
-            ix = cm.Index.build(p, n_desc, host, mem=cm.MEM_HOST, stream=stream)
-            off = 0
-            for r in rows:
-                pl = cm.MatchPlan(ix, pairs[r], stream=stream)
-                o = {"best_j": torch.empty(max(pl.rows, 1), dtype=torch.int32, device=dev)}
-                pl.run(o, stream)
-                best_host[off:off + pl.rows].copy_(o["best_j"][:pl.rows], non_blocking=True)
-                off += pl.rows
-                pl.close()
-        stream.synchronize()
-        if s > 0:
-            e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        ix.close()
-        del ix
-    e2e_value = n_pairs * world / (np.mean(e2e_ms) / 1e3)
+        e2e, verified = pipeline_e2e(args, wl, host, kp, sums, stream, world, dev)
 
     # ---- plain per-pair form (no schedule): upload both images, hash, match, download, free
     plain = plain_per_pair(args, wl, host, sums, stream, dev) if args.plain_pairs > 0 else None
@@ -269,29 +354,35 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.oracle_pairs > 0:
         cpu = cpu_baseline_and_agreement(args, wl, host.numpy(), sums, pairs, rows, gpu_rows)
 
+    forms_out = {}
+    for f, r in fr.items():
+        forms_out[f] = {k: (round(v, 6) if isinstance(v, float) else v) for k, v in r.items()
+                        if k in ("value", "ms_per_step", "matches", "decision_agreement_vs_fp32",
+                                 "match_jaccard_vs_fp32", "graph_kernels")}
     res = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8/fp32" if args.rerank == "fp32" else "u8/" + args.rerank,
         "data": "synthetic (seeded track model, %s)" % args.workload,
-        "config": {"workload": args.workload, "images": wl.n_images, "pairs": n_pairs,
-                   "descriptors": total, "rerank": args.rerank, "algo": args.algo, "projection": args.projection, "L": p.L, "m": p.m, "K": p.K,
-                   "ratio": "%d/%d" % (p.ratio_num, p.ratio_den), "block_rows": len(rows),
-                   "size_blk": args.block_images, "budget_gb": args.budget_gb,
+        "config": {"workload": args.workload, "images": wl.n_images, "pairs": len(pairs),
+                   "descriptors": total, "rerank": args.rerank, "algo": args.algo, "projection": args.projection,
+                   "L": p.L, "m": p.m, "K": p.K, "ratio": "%d/%d" % (p.ratio_num, p.ratio_den),
+                   "block_rows": len(rows), "gps_iterations": n_iter, "size_blk": args.block_images,
+                   "budget_gb": args.budget_gb, "step": "one CUDA graph: rehash + per block row match + compaction",
                    "l2": "inputs (%.1f GB descriptors) larger than L2" % (total * 128 / 1e9),
                    "generate_s": round(gen_s, 1)},
-        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": n_rows * 4, "ms_per_step": float(np.mean(e2e_ms))},
+        "e2e": e2e,
+        "forms": forms_out,
         "plain_fp32_per_pair": plain,
-        # per step: colsum, mean, hash, bucket, then one match launch per block row
-        "gpu_launches": args.steps * (4 + len(rows)),
+        "pipeline_verified": verified,
+        "gpu_launches": args.steps * head["graph_kernels"],
         "roofline": roofline,
-        "clocks": clocks,
+        "clocks": head["clocks"],
     }
     if cpu is not None:
         res["cpu_baseline"] = cpu.pop("cpu_baseline")
         res["agreement"] = cpu
-    return res, {"wl": wl, "host": host, "p": p, "stream": stream, "dev": dev}
+    return res, None
 
 
 def plain_per_pair(args, wl, host, sums, stream, dev):
@@ -391,6 +482,8 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    if args.verify_workers < 0:
+        args.verify_workers = os.cpu_count() or 1
     rank, world, local = dist_env()
     if world > 1:
         import torch

@@ -100,6 +100,7 @@ typedef struct { int32_t i, j; } cm_pair;  /* query image i, database image j (i
 typedef struct cm_index cm_index;
 typedef struct cm_schedule cm_schedule;
 typedef struct cm_match_plan cm_match_plan;
+typedef struct cm_sequence cm_sequence;
 
 /* Outputs of a match launch: per query row, device pointers, any may be NULL
  * except best_j.  Rows of pair k start at row_off(k) = sum of N_i over the
@@ -229,10 +230,136 @@ int64_t cm_match_plan_rows(const cm_match_plan* pl);
 /* One persistent fused launch over every pair of the plan (async): bucket
  * lookup, Hamming ranking, top-K, rerank and ratio test. */
 cm_status cm_match_plan_run(cm_match_plan* pl, const cm_match_out* out, cm_stream stream);
+/* Compaction of the plan's decisions into per-pair match lists, the initial
+ * matches handed to outlier removal (Algorithm 1).  From d_best_j (a
+ * cm_match_plan_run output) writes, all device memory: d_counts [n_pairs]
+ * matches per pair; d_offsets [n_pairs] exclusive prefix of the counts;
+ * d_total (optional) the sum; d_matches (optional) the matches, entry
+ * query << 16 | database index, pair k's at d_offsets[k] in query order.
+ * Entries past `capacity` are dropped (counts stay exact).  Async. */
+cm_status cm_match_plan_compact(cm_match_plan* pl, const int32_t* d_best_j, uint32_t* d_counts, uint64_t* d_offsets,
+                                uint64_t* d_total, uint32_t* d_matches, uint64_t capacity, cm_stream stream);
 void cm_match_plan_destroy(cm_match_plan* pl);
 /* Convenience: plan, run on stream, wait for the stream, destroy the plan. */
 cm_status cm_match_pairs(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, const cm_match_out* out,
                          cm_stream stream);
+
+/* ---- captured block sequence (CUDA graph) -------------------------------- */
+/* Compaction outputs of one plan inside a sequence (see cm_match_plan_compact);
+ * counts == NULL means no compaction for that plan. */
+typedef struct cm_compact_out {
+    uint32_t* counts;    /* device [n_pairs] */
+    uint64_t* offsets;   /* device [n_pairs] */
+    uint64_t* total;     /* device [1], optional */
+    uint32_t* matches;   /* device [capacity], optional */
+    uint64_t capacity;
+} cm_compact_out;
+/* Captures, without running it, the device work of a block sequence whose
+ * images are resident as one CUDA graph (stream capture on `stream`, which
+ * must not be the legacy default stream): if rehash != 0 a cm_index_rehash
+ * (centring statistics, keys, codes, buckets: Sec. 2.3.1 steps (1)-(2)), then
+ * for each plan k in order its fused match launch into outs[k] and, when
+ * compacts != NULL and compacts[k].counts != NULL, its compaction.  Buffers
+ * named in outs / compacts are baked into the graph and must outlive it.
+ * Errors: CM_ERR_INVALID (arguments, default stream), CM_ERR_STATE (a plan of
+ * another index or detached), CM_ERR_CUDA (capture or instantiation failed;
+ * the stream is left out of capture mode). */
+cm_status cm_sequence_create(cm_index* ix, int32_t rehash, int32_t n_plans, cm_match_plan* const* plans,
+                             const cm_match_out* outs, const cm_compact_out* compacts, cm_stream stream,
+                             cm_sequence** out);
+/* Replays the captured graph on stream (async; one graph launch).
+ * CM_ERR_STATE when the index changed since capture (an image loaded or
+ * evicted, a plan destroyed) or was destroyed: the graph's tables would be stale. */
+cm_status cm_sequence_launch(cm_sequence* q, cm_stream stream);
+/* Kernel nodes of the captured graph (launch accounting). */
+int32_t cm_sequence_kernels(const cm_sequence* q);
+void cm_sequence_destroy(cm_sequence* q);
+
+/* ---- block-row pipeline (Sec. 2.3.2, Algorithm 1) ------------------------ */
+/* Geometric verification callback.  Called on a library worker thread for
+ * each pair of a block row whose matches have reached host memory, while the
+ * GPU already works on the following rows (the GPU/CPU overlap of Sec. 2.3.2).
+ * pair_id indexes the caller's pair list; matches[k] = query << 16 | database
+ * index, in query order, valid during the call only.  Several workers call it
+ * at once for different pairs: it must be thread-safe.  A non-zero return
+ * stops the pipeline (cm_run_schedule returns CM_ERR_STATE). */
+typedef int32_t (*cm_verify_fn)(void* user, int32_t row, int64_t pair_id, const cm_pair* pair, int64_t n_matches,
+                                const uint32_t* matches);
+
+typedef struct cm_pipeline_stats {
+    int32_t rows;            /* block rows run */
+    int32_t workers;         /* verification threads */
+    int64_t pairs;           /* pairs matched */
+    int64_t queries;         /* query rows matched (sum of N_i over pairs) */
+    int64_t matches;         /* initial matches handed to verification */
+    int64_t kernels;         /* kernel launches enqueued */
+    uint64_t h2d_bytes;      /* descriptor bytes copied host to device */
+    uint64_t d2h_bytes;      /* result bytes device to host: per row the offsets and the match lists */
+    double wall_ms;          /* host wall time of the whole call */
+    double gpu_ms;           /* sum over rows of the device time from the row's first copy to its last write */
+    double verify_ms;        /* time spent inside the callback, summed over workers */
+    double stall_ms;         /* host time spent waiting for a result buffer still held by verification */
+    double tail_ms;          /* wall time after the last row's device work completed */
+} cm_pipeline_stats;
+
+/* Arena bytes for an index that runs schedule s with cm_run_schedule: the
+ * fixed tables, the largest set of images resident at once (a row's loads
+ * count before the row, its frees after it), a margin for fragmentation of
+ * the arena's first-fit placement (1/8 of that set plus its largest image),
+ * and the largest row's plan table. */
+cm_status cm_schedule_arena_bytes(const cm_schedule* s, const cm_params* p, int32_t n_images, const int32_t* n_desc,
+                                  uint64_t* bytes);
+/* Device workspace of cm_run_schedule for this schedule (bytes). */
+cm_status cm_pipeline_workspace_bytes(const cm_index* ix, const cm_schedule* s, const cm_pair* pairs, int64_t n_pairs,
+                                      uint64_t* bytes);
+/* Runs a schedule row by row (Algorithm 1): for row r, on `stream`, make the
+ * row's new images resident from host memory (H2D, hashing, buckets), match
+ * all its pairs in one fused launch, compact the decisions into per-pair match
+ * lists written straight into mapped pinned host memory, then release the
+ * row's freed images; worker threads verify row r while the GPU runs rows
+ * r+1, r+2 (two result buffers).  Returns when every row is verified.
+ *  - ix: an index whose centring mean is set (cm_index_set_mean) and on which
+ *    no image of the schedule is resident; images still resident at the end
+ *    are released.
+ *  - s / pairs / n_pairs: a schedule from cm_schedule_blocks and the pair list
+ *    it was made from.
+ *  - desc_host[i]: host rows of image i (pinned memory gives async copies).
+ *  - d_work / work_bytes: device workspace, at least cm_pipeline_workspace_bytes.
+ *  - verify (may be NULL: matches are only counted), user: the callback.
+ *  - n_workers: verification threads, 1..256.
+ *  - stats (optional): filled on return.
+ * Blocks the calling thread.  Errors: those of the calls it makes,
+ * CM_ERR_STATE if a callback stops the pipeline, CM_ERR_TIMEOUT if a bounded
+ * device wait gave up. */
+cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const cm_pair* pairs, int64_t n_pairs,
+                          const uint8_t* const* desc_host, void* d_work, uint64_t work_bytes, cm_verify_fn verify,
+                          void* user, int32_t n_workers, cm_stream stream, cm_pipeline_stats* stats);
+
+/* RANSAC fit of a 2-D affine map u = A [x y 1]^T from the query image's
+ * keypoints to the database image's over one pair's matches (the global
+ * geometric constraint of Sec. 2.3.2; an affine map is exact for the planar
+ * scenes seen by near-nadir views).  kp_i / kp_j: host float [n][2] pixel
+ * positions of the two images' descriptors; matches: as in cm_verify_fn.
+ * Minimal samples of 3 matches drawn by splitmix64 from seed; at most
+ * max_iters samples, fewer once a sample with the best inlier share makes a
+ * better one unlikely (p = 0.999); a match is an inlier when its residual is
+ * <= thresh_px; the best model is refit by least squares on its inliers and
+ * the inliers recounted.  Outputs (any may be NULL): A[6] row-major 2x3,
+ * inlier_mask[n_matches] (0/1), *n_inliers (0 when fewer than 3 matches or no
+ * non-degenerate sample).  Host only, thread-safe. */
+cm_status cm_verify_affine(const float* kp_i, const float* kp_j, int64_t n_matches, const uint32_t* matches,
+                           float thresh_px, int32_t max_iters, uint64_t seed, float* A, uint8_t* inlier_mask,
+                           int64_t* n_inliers);
+/* A ready-made cm_verify_fn running cm_verify_affine; user = cm_affine_verifier*. */
+typedef struct cm_affine_verifier {
+    const float* const* keypoints;  /* per image: host float [n][2] */
+    float thresh_px;
+    int32_t max_iters;
+    uint64_t seed;                  /* pair k uses seed ^ k */
+    int64_t* inliers;               /* [n_pairs of the caller's list]: inlier count written per pair */
+} cm_affine_verifier;
+int32_t cm_affine_verify_cb(void* user, int32_t row, int64_t pair_id, const cm_pair* pair, int64_t n_matches,
+                            const uint32_t* matches);
 
 /* ---- matching without any device allocation ------------------------------ */
 /* The paper has no counterpart: this entry point serves callers that may not

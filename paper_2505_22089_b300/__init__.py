@@ -33,7 +33,9 @@ EXPORTS = [
     "cm_schedule_get_row", "cm_free_schedule", "cm_gps_order", "cm_index_create", "cm_index_set_mean",
     "cm_index_mean_device", "cm_index_col_sums", "cm_index_check", "cm_index_load", "cm_index_rehash", "cm_index_evict", "cm_build_index",
     "cm_index_image_view", "cm_index_destroy", "cm_match_plan_create", "cm_match_plan_rows", "cm_match_plan_run",
-    "cm_match_plan_destroy", "cm_match_pairs", "cm_match_pair_noalloc",
+    "cm_match_plan_compact", "cm_match_plan_destroy", "cm_match_pairs", "cm_sequence_create", "cm_sequence_launch",
+    "cm_sequence_kernels", "cm_sequence_destroy", "cm_schedule_arena_bytes", "cm_pipeline_workspace_bytes", "cm_run_schedule",
+    "cm_verify_affine", "cm_affine_verify_cb", "cm_match_pair_noalloc",
 ]
 
 
@@ -64,6 +66,31 @@ class Params(ctypes.Structure):
 class MatchOut(ctypes.Structure):
     _fields_ = [("best_j", ctypes.c_void_p), ("d1sq", ctypes.c_void_p), ("d2sq", ctypes.c_void_p),
                 ("topk", ctypes.c_void_p), ("stats", ctypes.c_void_p)]
+
+
+class CompactOut(ctypes.Structure):
+    _fields_ = [("counts", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("total", ctypes.c_void_p),
+                ("matches", ctypes.c_void_p), ("capacity", ctypes.c_uint64)]
+
+
+class PipelineStats(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("workers", ctypes.c_int32), ("pairs", ctypes.c_int64),
+                ("queries", ctypes.c_int64), ("matches", ctypes.c_int64), ("kernels", ctypes.c_int64),
+                ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64), ("wall_ms", ctypes.c_double),
+                ("gpu_ms", ctypes.c_double), ("verify_ms", ctypes.c_double), ("stall_ms", ctypes.c_double),
+                ("tail_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class AffineVerifier(ctypes.Structure):
+    _fields_ = [("keypoints", ctypes.c_void_p), ("thresh_px", ctypes.c_float), ("max_iters", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("inliers", ctypes.c_void_p)]
+
+
+VERIFY_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                             ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32))
 
 
 class ScheduleRow(ctypes.Structure):
@@ -113,8 +140,19 @@ def lib():
             "cm_match_plan_rows": (i64, [vp]),
             "cm_match_plan_run": (i32, [vp, ctypes.POINTER(MatchOut), vp]),
             "cm_match_plan_destroy": (None, [vp]),
+            "cm_match_plan_compact": (i32, [vp, vp, vp, vp, vp, vp, u64, vp]),
             "cm_match_pairs": (i32, [vp, vp, i64, ctypes.POINTER(MatchOut), vp]),
             "cm_match_pair_noalloc": (i32, [P, vp, i32, vp, i32, vp, u64, vp, vp, vp, vp]),
+            "cm_sequence_create": (i32, [vp, i32, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]),
+            "cm_sequence_launch": (i32, [vp, vp]),
+            "cm_sequence_kernels": (i32, [vp]),
+            "cm_sequence_destroy": (None, [vp]),
+            "cm_schedule_arena_bytes": (i32, [vp, P, i32, vp, ctypes.POINTER(u64)]),
+            "cm_pipeline_workspace_bytes": (i32, [vp, vp, vp, i64, ctypes.POINTER(u64)]),
+            "cm_run_schedule": (i32, [vp, vp, vp, i64, vp, vp, u64, vp, vp, i32, vp,
+                                      ctypes.POINTER(PipelineStats)]),
+            "cm_verify_affine": (i32, [vp, vp, i64, vp, ctypes.c_float, i32, u64, vp, vp, ctypes.POINTER(i64)]),
+            "cm_affine_verify_cb": (i32, [vp, i32, i64, vp, i64, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -171,10 +209,33 @@ def gps_order(n: int, edges) -> list:
     return [int(x) for x in order[:cnt.value]]
 
 
-@dataclass
 class Schedule:
-    rows: list
-    iterations: int
+    """A cm_schedule: rows (load / free / pair ids per block row) read into
+    Python, and the handle, kept for cm_run_schedule."""
+
+    def __init__(self, h: ctypes.c_void_p, pairs: np.ndarray):
+        self.h = h
+        self.pairs = pairs
+        self.rows = []
+        r = ScheduleRow()
+        for k in range(lib().cm_schedule_num_rows(h)):
+            check(lib().cm_schedule_get_row(h, k, ctypes.byref(r)))
+            self.rows.append({"iteration": r.iteration,
+                              "load": [r.load[q] for q in range(r.n_load)],
+                              "free": [r.free_ids[q] for q in range(r.n_free)],
+                              "pairs": [r.pairs[q] for q in range(r.n_pairs)]})
+        self.iterations = lib().cm_schedule_num_iterations(h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cm_free_schedule(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def schedule_blocks(pairs, n_desc, p: Params, budget: int, max_images_per_block: int) -> Schedule:
@@ -183,18 +244,29 @@ def schedule_blocks(pairs, n_desc, p: Params, budget: int, max_images_per_block:
     h = ctypes.c_void_p()
     check(lib().cm_schedule_blocks(pr.ctypes.data, pr.shape[0], len(nd), nd.ctypes.data, ctypes.byref(p),
                                    int(budget), int(max_images_per_block), ctypes.byref(h)))
-    try:
-        rows = []
-        r = ScheduleRow()
-        for k in range(lib().cm_schedule_num_rows(h)):
-            check(lib().cm_schedule_get_row(h, k, ctypes.byref(r)))
-            rows.append({"iteration": r.iteration,
-                         "load": [r.load[q] for q in range(r.n_load)],
-                         "free": [r.free_ids[q] for q in range(r.n_free)],
-                         "pairs": [r.pairs[q] for q in range(r.n_pairs)]})
-        return Schedule(rows, lib().cm_schedule_num_iterations(h))
-    finally:
-        lib().cm_free_schedule(h)
+    return Schedule(h, pr)
+
+
+def schedule_arena_bytes(sched: Schedule, p: Params, n_desc) -> int:
+    """cm_schedule_arena_bytes: arena an index needs to run `sched` with run_schedule."""
+    nd = np.ascontiguousarray(n_desc, dtype=np.int32)
+    b = ctypes.c_uint64()
+    check(lib().cm_schedule_arena_bytes(sched.h, ctypes.byref(p), len(nd), nd.ctypes.data, ctypes.byref(b)))
+    return b.value
+
+
+def verify_affine(kp_i, kp_j, matches, thresh_px: float = 3.0, max_iters: int = 1000, seed: int = 1):
+    """cm_verify_affine on host arrays: returns (A 2x3, inlier mask, inlier count)."""
+    ki = np.ascontiguousarray(kp_i, dtype=np.float32)
+    kj = np.ascontiguousarray(kp_j, dtype=np.float32)
+    mt = np.ascontiguousarray(matches, dtype=np.uint32)
+    A = np.zeros(6, dtype=np.float32)
+    mask = np.zeros(max(len(mt), 1), dtype=np.uint8)
+    n = ctypes.c_int64()
+    check(lib().cm_verify_affine(ki.ctypes.data, kj.ctypes.data, len(mt), mt.ctypes.data if len(mt) else None,
+                                 float(thresh_px), int(max_iters), int(seed), A.ctypes.data, mask.ctypes.data,
+                                 ctypes.byref(n)))
+    return A.reshape(2, 3), mask[: len(mt)].astype(bool), n.value
 
 
 def _cudart():
@@ -374,6 +446,21 @@ class MatchPlan:
                         for k in ("best_j", "d1sq", "d2sq", "topk", "stats")])
         check(lib().cm_match_plan_run(self.h, ctypes.byref(mo), _stream(stream)))
 
+    def compact(self, best_j, capacity: int | None = None, stream=None):
+        """Per-pair match lists from a run's best_j: returns CUDA tensors
+        (counts int32 [P], offsets int64 [P], total int64 [1], matches int32 [capacity]);
+        a match is query << 16 | database index."""
+        import torch
+        n = max(len(self.pairs), 1)
+        cap = self.rows if capacity is None else int(capacity)
+        counts = torch.empty(n, dtype=torch.int32, device=best_j.device)
+        offsets = torch.empty(n, dtype=torch.int64, device=best_j.device)
+        total = torch.zeros(1, dtype=torch.int64, device=best_j.device)
+        matches = torch.empty(max(cap, 1), dtype=torch.int32, device=best_j.device)
+        check(lib().cm_match_plan_compact(self.h, _ptr(best_j), _ptr(counts), _ptr(offsets), _ptr(total),
+                                          _ptr(matches), cap, _stream(stream)))
+        return counts, offsets, total, matches
+
     def close(self):
         if getattr(self, "h", None):
             lib().cm_match_plan_destroy(self.h)
@@ -384,3 +471,97 @@ class MatchPlan:
             self.close()
         except Exception:
             pass
+
+
+class Sequence:
+    """cm_sequence: the device work of a resident block sequence (optional
+    rehash, then each plan's match launch and compaction) captured once as a
+    CUDA graph and replayed with one launch."""
+
+    def __init__(self, index: Index, plans, outs, compacts=None, rehash: bool = True, stream=None):
+        import torch
+        self.index = index
+        self._keep = (list(plans), list(outs), list(compacts or []))
+        n = len(plans)
+        ph = (ctypes.c_void_p * max(n, 1))(*[pl.h for pl in plans])
+        mo = (MatchOut * max(n, 1))(*[MatchOut(*[ctypes.c_void_p(o[k].data_ptr()) if o.get(k) is not None else None
+                                                 for k in ("best_j", "d1sq", "d2sq", "topk", "stats")])
+                                      for o in outs])
+        co = None
+        if compacts is not None:
+            co = (CompactOut * max(n, 1))(*[CompactOut(_ptr(c["counts"]), _ptr(c["offsets"]), _ptr(c.get("total")),
+                                                       _ptr(c.get("matches")), int(c.get("capacity", 0)))
+                                            if c is not None else CompactOut() for c in compacts])
+        cap = torch.cuda.Stream() if stream is None else stream
+        if stream is None:
+            cap.wait_stream(torch.cuda.current_stream())
+        self.h = ctypes.c_void_p()
+        check(lib().cm_sequence_create(index.h, int(rehash), n, ph, mo, co, _stream(cap), ctypes.byref(self.h)))
+        self.kernels = int(lib().cm_sequence_kernels(self.h))
+
+    def launch(self, stream=None):
+        check(lib().cm_sequence_launch(self.h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cm_sequence_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def compact_out(plan: "MatchPlan", capacity: int | None = None) -> dict:
+    """Device buffers for one plan's compaction inside a Sequence."""
+    import torch
+    n = max(len(plan.pairs), 1)
+    cap = plan.rows if capacity is None else int(capacity)
+    return {"counts": torch.empty(n, dtype=torch.int32, device="cuda"),
+            "offsets": torch.empty(n, dtype=torch.int64, device="cuda"),
+            "total": torch.zeros(1, dtype=torch.int64, device="cuda"),
+            "matches": torch.empty(max(cap, 1), dtype=torch.int32, device="cuda"), "capacity": cap}
+
+
+def run_schedule(index: Index, sched: Schedule, desc_host, verify=None, keypoints=None, thresh_px: float = 3.0,
+                 max_iters: int = 500, seed: int = 7, workers: int = 4, stream=None):
+    """cm_run_schedule.  desc_host: per image a host uint8 [n][128] array or
+    pinned CPU tensor.  verify: None (count matches only), "affine" (the
+    library's RANSAC callback over `keypoints`, per image float [n][2]), or a
+    Python callable f(row, pair_id, (i, j), matches: np.ndarray uint32) -> int.
+    Returns (stats dict, inliers per pair or None)."""
+    import torch
+    pairs = sched.pairs
+    ws = ctypes.c_uint64()
+    check(lib().cm_pipeline_workspace_bytes(index.h, sched.h, pairs.ctypes.data, len(pairs), ctypes.byref(ws)))
+    work = torch.empty(int(ws.value) + 256, dtype=torch.uint8, device="cuda")
+    wbase = (work.data_ptr() + 255) // 256 * 256
+    ptrs = (ctypes.c_void_p * len(desc_host))(*[d.data_ptr() if hasattr(d, "data_ptr") else
+                                                np.ascontiguousarray(d).ctypes.data for d in desc_host])
+    keep = [desc_host, work]
+    inliers = None
+    fn, user = None, None
+    if verify == "affine":
+        kps = [np.ascontiguousarray(k, dtype=np.float32) for k in keypoints]
+        kp_ptrs = (ctypes.c_void_p * len(kps))(*[k.ctypes.data for k in kps])
+        inliers = np.full(len(pairs), -1, dtype=np.int64)
+        v = AffineVerifier(ctypes.cast(kp_ptrs, ctypes.c_void_p), float(thresh_px), int(max_iters), int(seed),
+                           inliers.ctypes.data)
+        keep += [kps, kp_ptrs, v]
+        fn = ctypes.cast(lib().cm_affine_verify_cb, ctypes.c_void_p)
+        user = ctypes.cast(ctypes.pointer(v), ctypes.c_void_p)
+    elif callable(verify):
+        def _cb(_user, row, pair_id, pair_p, n, matches):
+            ij = ctypes.cast(pair_p, ctypes.POINTER(ctypes.c_int32))
+            arr = np.ctypeslib.as_array(matches, shape=(n,)).copy() if n else np.zeros(0, np.uint32)
+            return int(verify(row, pair_id, (ij[0], ij[1]), arr))
+        cb = VERIFY_FN(_cb)
+        keep.append(cb)
+        fn = ctypes.cast(cb, ctypes.c_void_p)
+    st = PipelineStats()
+    check(lib().cm_run_schedule(index.h, sched.h, pairs.ctypes.data, len(pairs), ptrs, ctypes.c_void_p(wbase),
+                                int(ws.value), fn, user, int(workers), _stream(stream), ctypes.byref(st)))
+    del keep
+    return st.as_dict(), inliers

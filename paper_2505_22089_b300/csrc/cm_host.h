@@ -1,0 +1,244 @@
+// Host-side internals shared by the C-ABI translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <set>
+#include <vector>
+
+#include "cm_internal.h"
+
+namespace cm {
+
+// Records a failure for cm_last_error() and returns st (cm_api.cpp).
+cm_status host_fail(cm_status st, const char* fmt, ...);
+
+#define CM_CUDA(call)                                                                                    \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return ::cm::host_fail(CM_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+inline static int proj_count(const cm_params* p) { return p->L * p->m + p->n_bits; }
+inline static int proj_pad(const cm_params* p) { return (proj_count(p) + 15) / 16 * 16; }
+
+// Default work-item size: kDefaultQueryTile, shrunk until the tile kernel's
+// shared memory (top-K lists and hit buffers of the tile) fits.
+inline int query_tile(const cm_params* p) {
+    if (p->query_tile) return p->query_tile;
+    int S = kDefaultQueryTile;
+    while (S > 64 && match_smem_bytes(S, p->K) > kMatchSmemLimit) S -= 64;
+    return S;
+}
+
+constexpr uint64_t kAlign = 256;
+inline uint64_t align_up(uint64_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct SlotLayout {
+    uint64_t desc, key, code, scode, sidx, off, hist, brank, norm, xq, xscale, total;
+};
+
+inline SlotLayout slot_layout(const cm_params* p, int64_t n, bool inplace) {
+    const int64_t B = 1ll << p->m;
+    SlotLayout s{};
+    uint64_t o = 0;
+    auto take = [&](uint64_t bytes) { uint64_t at = o; o = align_up(o + bytes); return at; };
+    s.desc = inplace ? 0 : take((uint64_t)n * kDim);
+    s.key = take((uint64_t)n * 8);
+    s.code = take((uint64_t)n * 16);
+    s.scode = take((uint64_t)p->L * n * 16);
+    s.sidx = take((uint64_t)p->L * n * 2);
+    s.off = take((uint64_t)p->L * (B + 1) * 4);
+    s.hist = take((uint64_t)p->L * B * 4);
+    s.brank = take((uint64_t)p->L * 256);
+    s.norm = take((uint64_t)n * 4);
+    s.xq = 0;       // tensor-core reranks convert rows while staging them: no stored copy
+    s.xscale = 0;
+    s.total = o;
+    return s;
+}
+
+// Fixed tables at the start of the arena.
+struct FixedLayout {
+    uint64_t imgs, W, mu, sums, ntot, batch, tiles, rbatch, rtiles, tiles128, rtiles128, bias, err, total;
+};
+
+inline FixedLayout fixed_layout(const cm_params* p, int n_images) {
+    FixedLayout f{};
+    uint64_t o = 0;
+    auto take = [&](uint64_t bytes) { uint64_t at = o; o = align_up(o + bytes); return at; };
+    f.imgs = take((uint64_t)n_images * sizeof(DevImage));
+    f.W = take((uint64_t)kDim * proj_pad(p) * 4);
+    f.mu = take(kDim * 4);
+    f.sums = take(kDim * 8);
+    f.ntot = take(8);
+    f.batch = take((uint64_t)n_images * 4);
+    f.tiles = take((uint64_t)(n_images + 1) * 4);
+    f.rbatch = take((uint64_t)n_images * 4);
+    f.rtiles = take((uint64_t)(n_images + 1) * 4);
+    f.tiles128 = take((uint64_t)(n_images + 1) * 4);
+    f.rtiles128 = take((uint64_t)(n_images + 1) * 4);
+    f.bias = take((uint64_t)kMaxP * 4);
+    f.err = take(4);
+    f.total = o;
+    return f;
+}
+
+// First-fit allocator over [begin, end) of the arena (host bookkeeping only).
+class ArenaAlloc {
+   public:
+    void init(uint64_t begin, uint64_t end) {
+        free_.clear();
+        if (end > begin) free_[begin] = end - begin;
+    }
+    bool alloc(uint64_t bytes, uint64_t* at) {
+        bytes = align_up(bytes ? bytes : kAlign);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *at = it->first;
+                const uint64_t rest = it->second - bytes, base = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[base] = rest;
+                used_[*at] = bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(uint64_t at) {
+        auto u = used_.find(at);
+        if (u == used_.end()) return;
+        uint64_t base = at, size = u->second;
+        used_.erase(u);
+        auto next = free_.lower_bound(base);
+        if (next != free_.end() && base + size == next->first) {
+            size += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == base) {
+                prev->second += size;
+                return;
+            }
+        }
+        free_[base] = size;
+    }
+
+   private:
+    std::map<uint64_t, uint64_t> free_, used_;
+};
+
+// Pinned host buffers for table uploads; a buffer is reused once the copy that
+// read it has completed on its stream.
+class Staging {
+   public:
+    ~Staging() {
+        for (auto& b : bufs_) {
+            cudaEventDestroy(b.ev);
+            cudaFreeHost(b.p);
+        }
+    }
+    cudaError_t upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+        if (!bytes) return cudaSuccess;
+        Buf* use = nullptr;
+        for (auto& b : bufs_) {
+            if (b.cap >= bytes && (!b.pending || cudaEventQuery(b.ev) == cudaSuccess)) {
+                use = &b;
+                break;
+            }
+        }
+        if (!use) {
+            Buf b{};
+            b.cap = std::max<size_t>(bytes, 1 << 16);
+            cudaError_t e = cudaHostAlloc(&b.p, b.cap, cudaHostAllocDefault);
+            if (e != cudaSuccess) return e;
+            e = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+            bufs_.push_back(b);
+            use = &bufs_.back();
+        }
+        memcpy(use->p, src, bytes);
+        cudaError_t e = cudaMemcpyAsync(dst, use->p, bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+        e = cudaEventRecord(use->ev, s);
+        use->pending = true;
+        return e;
+    }
+
+   private:
+    struct Buf {
+        void* p;
+        size_t cap;
+        cudaEvent_t ev;
+        bool pending;
+    };
+    std::vector<Buf> bufs_;
+};
+
+}  // namespace cm
+
+using namespace cm;
+
+struct cm_match_plan;
+struct cm_sequence;
+void cm_sequence_detach(cm_sequence* q);   // the index is going away (cm_pipeline.cpp)
+
+struct cm_index {
+    cm_params p{};
+    std::set<cm_match_plan*> plans;    // live plans (detached when the index is destroyed)
+    std::set<cm_sequence*> seqs;       // live captured sequences (detached likewise)
+    uint64_t generation = 0;           // bumped by load, evict and plan destruction
+    int P = 0, P_pad = 0, B = 0, sms = 148;
+    int n_images = 0;
+    std::vector<int32_t> n_desc;
+    uint8_t* arena = nullptr;
+    uint64_t arena_bytes = 0;
+    FixedLayout fx{};
+    ArenaAlloc alloc;
+    std::vector<DevImage> h_imgs;
+    std::vector<uint64_t> slot_at;     // arena offset of each image's slot (valid if resident)
+    std::vector<char> resident;
+    bool mean_set = false;
+    bool sums_on_host = false;         // the mean came from cm_index_set_mean
+    uint64_t host_sums[kDim] = {};
+    uint64_t n_total = 0;              // rows behind the current mean
+    Staging staging;
+
+    template <class T>
+    T* at(uint64_t off) const { return reinterpret_cast<T*>(arena + off); }
+
+    HashLaunch hash_launch(bool resident_set, int n_batch, int n_tiles, int n_tiles128) const {
+        HashLaunch h{};
+        h.imgs = at<DevImage>(fx.imgs);
+        h.batch = at<int32_t>(resident_set ? fx.rbatch : fx.batch);
+        h.tile_pref = at<int32_t>(resident_set ? fx.rtiles : fx.tiles);
+        h.tile_pref128 = at<int32_t>(resident_set ? fx.rtiles128 : fx.tiles128);
+        h.n_batch = n_batch;
+        h.n_tiles = n_tiles;
+        h.n_tiles128 = n_tiles128;
+        h.bias = at<float>(fx.bias);
+        h.err = at<int>(fx.err);
+        h.W = at<float>(fx.W);
+        h.mu = at<float>(fx.mu);
+        h.L = p.L;
+        h.m = p.m;
+        h.P_pad = P_pad;
+        h.rerank = p.rerank;
+        return h;
+    }
+};
+
+struct cm_match_plan {
+    cm_index* ix = nullptr;
+    uint64_t table_at = 0;   // arena offset: [n_pairs] DevPair, then the work counter
+    int64_t n_pairs = 0;
+    int64_t rows = 0;
+    int32_t n_items = 0;
+};
+
+

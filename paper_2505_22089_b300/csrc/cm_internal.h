@@ -15,7 +15,7 @@ constexpr int kHashTile = 64;      // descriptors per hash tile
 constexpr int kHashThreads = 256;
 constexpr int kMatchThreads = 1024;
 constexpr int kDefaultQueryTile = 2048;  // queries per work item
-constexpr size_t kMatchSmemLimit = 220 * 1024;  // dynamic shared memory of the tile kernel (static extra)
+constexpr size_t kMatchSmemLimit = 214 * 1024;  // dynamic shared memory of the tile kernel (static extra)
 constexpr int kWqThreads = 256;          // warp-per-query matcher: 8 warps per CTA
 constexpr int kWqBlocksPerSM = 3;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
@@ -90,6 +90,9 @@ cudaError_t launch_bucket(const HashLaunch& h, cudaStream_t s);
 cudaError_t launch_match(const MatchLaunch& m, int sm_count, cudaStream_t s);      // lane per query (cm_match.cu)
 cudaError_t launch_match_wq(const MatchLaunch& m, int sm_count, cudaStream_t s);   // warp per query (cm_match_wq.cu)
 size_t match_smem_bytes(int S, int K);
+cudaError_t launch_compact(const DevPair* pairs, int n_pairs, const DevImage* imgs, const int32_t* best,
+                           uint32_t* counts, unsigned long long* offsets, unsigned long long* total, uint32_t* out,
+                           unsigned long long capacity, cudaStream_t s);                 // cm_compact.cu
 int hash_npg(int P_pad);
 
 }  // namespace cm

@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(kMatchThreads, 1) k_match(MatchLaunch ml) {
     __shared__ uint64_t s_mbar;
     __shared__ uint32_t s_tmem;
     __shared__ float s_scales[6 * 192];   // FP8 rerank: per-row scales of the staged sub-tiles
+    __shared__ uint32_t s_norms[6 * 192]; // tensor-core reranks: squared norms of the staged rows
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int B = 1 << ml.m;
@@ -305,10 +306,10 @@ __global__ void __launch_bounds__(kMatchThreads, 1) k_match(MatchLaunch ml) {
             // qcode .. the end of the hit buffer is free after the table passes
             const uint32_t region_bytes = (uint32_t)S * 28 + 2 * 256 * 4 + (uint32_t)kHitCap * kMatchThreads * 4;
             if (ml.rerank == CM_RERANK_BF16)
-                rerank_tc<K, false>(ml, P, I, J, q0, nq, st, region, region_bytes, s_scales, s_tmem, &s_mbar, parity,
+                rerank_tc<K, false>(ml, P, I, J, q0, nq, st, region, region_bytes, s_scales, s_norms, s_tmem, &s_mbar, parity,
                                     rechecks, matches, swaps);
             else
-                rerank_tc<K, true>(ml, P, I, J, q0, nq, st, region, region_bytes, s_scales, s_tmem, &s_mbar, parity,
+                rerank_tc<K, true>(ml, P, I, J, q0, nq, st, region, region_bytes, s_scales, s_norms, s_tmem, &s_mbar, parity,
                                    rechecks, matches, swaps);
             continue;
         }

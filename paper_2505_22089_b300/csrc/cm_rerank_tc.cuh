@@ -75,7 +75,7 @@ __device__ __forceinline__ uint32_t exact_d2(const uint8_t* x, const uint8_t* y,
 template <int K, bool FP8>
 __device__ void rerank_tc(const MatchLaunch& ml, const DevPair& P, const DevImage& I, const DevImage& J, int q0,
                           int nq, const uint32_t* __restrict__ st, unsigned char* region, uint32_t region_bytes,
-                          float* scales, uint32_t tmem, uint64_t* mbar, uint32_t& parity, uint32_t& rechecks,
+                          float* scales, uint32_t* norms, uint32_t tmem, uint64_t* mbar, uint32_t& parity, uint32_t& rechecks,
                           uint32_t& matches, uint32_t& swaps) {
     using RS = RerankShape<K, FP8>;
     constexpr int QS = RS::QS, NB = RS::NB;
@@ -85,46 +85,72 @@ __device__ void rerank_tc(const MatchLaunch& ml, const DevPair& P, const DevImag
     const uint32_t idesc = FP8 ? tc::idesc_e4m3(128, NB) : tc::idesc_f16(128, NB, 1);
 
     for (int base = 0; base < nq; base += slots * QS) {
-        // ---- stage: rows of every slot, 8 threads x 16 bytes per row
-        const int total = slots * RS::ROWS * 8;
-        for (int f = tid; f < total; f += kMatchThreads) {
-            const int seg = f & 7, rr = f >> 3;
-            const int s = rr / RS::ROWS, r = rr % RS::ROWS;
-            const uint8_t* src = nullptr;
-            if (r < 128) {
-                const int qi = base + s * QS + r / K;
-                if (qi < nq) {
-                    const uint32_t key = st[qi * K + (r % K)];
-                    if (key != kEmpty) src = J.desc + (size_t)(key & 0xFFFFu) * kDim;
+        // ---- stage: rows of every slot, 8 threads x 16 bytes per row; each thread
+        // requests up to 4 segments before converting any.  Row norms and (FP8)
+        // row scales are reduced over the 8 lanes of a row into shared memory.
+        const int total = slots * RS::ROWS * 8;   // a multiple of 32: every warp is full or idle
+        for (int f0 = tid; f0 < total; f0 += 4 * kMatchThreads) {
+            uint4 v[4];
+            bool real[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = f0 + u * kMatchThreads;
+                const int seg = f & 7, rr = f >> 3;
+                const int s = rr / RS::ROWS, r = rr % RS::ROWS;
+                const uint8_t* src = nullptr;
+                if (f < total) {
+                    if (r < 128) {
+                        const int qi = base + s * QS + r / K;
+                        if (qi < nq) {
+                            const uint32_t key = st[qi * K + (r % K)];
+                            if (key != kEmpty) src = J.desc + (size_t)(key & 0xFFFFu) * kDim;
+                        }
+                    } else {
+                        const int n = r - 128, qi = base + s * QS + n;
+                        if (n < QS && qi < nq) src = I.desc + (size_t)(q0 + qi) * kDim;
+                    }
                 }
-            } else {
-                const int n = r - 128, qi = base + s * QS + n;
-                if (n < QS && qi < nq) src = I.desc + (size_t)(q0 + qi) * kDim;
+                real[u] = src != nullptr;
+                v[u] = src ? __ldg(reinterpret_cast<const uint4*>(src) + seg) : make_uint4(0, 0, 0, 0);
             }
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (src) v = __ldg(reinterpret_cast<const uint4*>(src) + seg);
-            unsigned char* slot = region + (size_t)s * RS::SLOT;
-            unsigned char* tile = r < 128 ? slot : slot + RS::A_BYTES;
-            const int trow = r < 128 ? r : r - 128, trows = r < 128 ? 128 : NB;
-            if (!FP8) {
-                uint4 lo, hi;
-                lo.x = tc_bf16x2(v.x, 0); lo.y = tc_bf16x2(v.x, 2); lo.z = tc_bf16x2(v.y, 0); lo.w = tc_bf16x2(v.y, 2);
-                hi.x = tc_bf16x2(v.z, 0); hi.y = tc_bf16x2(v.z, 2); hi.z = tc_bf16x2(v.w, 0); hi.w = tc_bf16x2(v.w, 2);
-                *reinterpret_cast<uint4*>(tile + tc::chunk_off(trow, 2 * seg, trows)) = lo;
-                *reinterpret_cast<uint4*>(tile + tc::chunk_off(trow, 2 * seg + 1, trows)) = hi;
-            } else {
-                // per-row scale max/448, from the 8 lanes that hold the row
-                uint32_t mx = row_max_u8(v);
-                mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 1));
-                mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 2));
-                mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 4));
-                const float scale = mx ? (float)mx / 448.f : 1.f;
-                const float inv = 1.f / scale;
-                uint4 o;
-                o.x = tc_e4m3x4(v.x, inv); o.y = tc_e4m3x4(v.y, inv);
-                o.z = tc_e4m3x4(v.z, inv); o.w = tc_e4m3x4(v.w, inv);
-                *reinterpret_cast<uint4*>(tile + tc::chunk_off(trow, seg, trows)) = o;
-                if (seg == 0) scales[s * RS::ROWS + r] = src ? scale : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = f0 + u * kMatchThreads;
+                if (f >= total) break;               // uniform per warp
+                const int seg = f & 7, rr = f >> 3;
+                const int s = rr / RS::ROWS, r = rr % RS::ROWS;
+                unsigned char* slot = region + (size_t)s * RS::SLOT;
+                unsigned char* tile = r < 128 ? slot : slot + RS::A_BYTES;
+                const int trow = r < 128 ? r : r - 128, trows = r < 128 ? 128 : NB;
+                unsigned nn = __dp4a(v[u].x, v[u].x, 0u);
+                nn = __dp4a(v[u].y, v[u].y, nn);
+                nn = __dp4a(v[u].z, v[u].z, nn);
+                nn = __dp4a(v[u].w, v[u].w, nn);
+                nn += __shfl_xor_sync(0xFFFFFFFFu, nn, 1);
+                nn += __shfl_xor_sync(0xFFFFFFFFu, nn, 2);
+                nn += __shfl_xor_sync(0xFFFFFFFFu, nn, 4);
+                if (seg == 0) norms[s * RS::ROWS + r] = nn;
+                if (!FP8) {
+                    uint4 lo, hi;
+                    lo.x = tc_bf16x2(v[u].x, 0); lo.y = tc_bf16x2(v[u].x, 2);
+                    lo.z = tc_bf16x2(v[u].y, 0); lo.w = tc_bf16x2(v[u].y, 2);
+                    hi.x = tc_bf16x2(v[u].z, 0); hi.y = tc_bf16x2(v[u].z, 2);
+                    hi.z = tc_bf16x2(v[u].w, 0); hi.w = tc_bf16x2(v[u].w, 2);
+                    *reinterpret_cast<uint4*>(tile + tc::chunk_off(trow, 2 * seg, trows)) = lo;
+                    *reinterpret_cast<uint4*>(tile + tc::chunk_off(trow, 2 * seg + 1, trows)) = hi;
+                } else {
+                    uint32_t mx = row_max_u8(v[u]);
+                    mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 1));
+                    mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 2));
+                    mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 4));
+                    const float scale = mx ? (float)mx / 448.f : 1.f;
+                    const float inv = 1.f / scale;
+                    uint4 o;
+                    o.x = tc_e4m3x4(v[u].x, inv); o.y = tc_e4m3x4(v[u].y, inv);
+                    o.z = tc_e4m3x4(v[u].z, inv); o.w = tc_e4m3x4(v[u].w, inv);
+                    *reinterpret_cast<uint4*>(tile + tc::chunk_off(trow, seg, trows)) = o;
+                    if (seg == 0) scales[s * RS::ROWS + r] = real[u] ? scale : 0.f;
+                }
             }
         }
         tc::fence_proxy_async();
@@ -182,7 +208,7 @@ __device__ void rerank_tc(const MatchLaunch& ml, const DevPair& P, const DevImag
                 const int64_t row = P.row_off + q0 + (qv ? qi : 0);
                 uint64_t mine = ~0ull;
                 if (have) {
-                    const float nx = (float)I.norm[q0 + qi], ny = (float)J.norm[j];
+                    const float ny = (float)norms[s * RS::ROWS + r], nx = (float)norms[s * RS::ROWS + 128 + c];
                     if (!FP8) {
                         const uint32_t d2 = (uint32_t)(nx + ny - 2.f * dot);   // exact: integers below 2^24
                         mine = ((uint64_t)d2 << 32) | (uint32_t)j;
