@@ -180,8 +180,10 @@ def device_forms(args, wl, desc_dev, rows, stream, dev, world, forms):
     headline = forms[0]
     for form in forms:
         p = cm.Params.make(rerank=form, algo=args.algo, projection=args.projection, K=args.K)
+        arena = (cm.index_bytes(p, wl.n_desc, inplace=True) + cm.PLAN_HEADROOM +
+                 sum(cm.pairs_plan_bytes(p, wl.n_desc, pairs[r]) for r in rows))
         with torch.cuda.stream(stream):
-            index = cm.Index.build(p, wl.n_desc, desc_dev, stream=stream)
+            index = cm.Index.build(p, wl.n_desc, desc_dev, stream=stream, arena_bytes=arena)
             plans = [cm.MatchPlan(index, pairs[r], stream=stream) for r in rows]
             outs = [pl.alloc_out(d12=False) for pl in plans]
             comps = [cm.compact_out(pl) for pl in plans]

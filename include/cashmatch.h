@@ -219,6 +219,12 @@ cm_status cm_index_image_view(const cm_index* ix, int32_t image, const void** ke
 void cm_index_destroy(cm_index* ix);
 
 /* ---- matching (Sec. 2.3.1 steps (1)-(4), one launch per block) ------------ */
+/* Arena bytes a plan of n_pairs pairs and `rows` query rows takes from its
+ * index: the pair table and work counter, and for the BF16 / FP8 reranks the
+ * top-K hand-over between the scan and the tensor-core rerank (index and
+ * squared norm of each kept candidate, 6 K bytes per row; FP8 adds its scale,
+ * 10 K bytes per row). */
+cm_status cm_plan_bytes(const cm_params* p, int64_t n_pairs, int64_t rows, uint64_t* bytes);
 /* Plans a batch of pairs (host list): validates ids and residency and uploads
  * the work table into the index arena (async, on stream).  A plan can be run
  * many times and captured in a CUDA graph; it must not outlive the residency
@@ -228,7 +234,9 @@ cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, int64_t n_pai
 /* Total query rows of the plan (sum of N_i) — the size of each output array. */
 int64_t cm_match_plan_rows(const cm_match_plan* pl);
 /* One persistent fused launch over every pair of the plan (async): bucket
- * lookup, Hamming ranking, top-K, rerank and ratio test. */
+ * lookup, Hamming ranking, top-K, rerank and ratio test.  With the BF16 / FP8
+ * reranks the rerank and ratio test run in a second, tensor-core launch that
+ * reads the first one's top-K lists. */
 cm_status cm_match_plan_run(cm_match_plan* pl, const cm_match_out* out, cm_stream stream);
 /* Compaction of the plan's decisions into per-pair match lists, the initial
  * matches handed to outlier removal (Algorithm 1).  From d_best_j (a
@@ -302,13 +310,13 @@ typedef struct cm_pipeline_stats {
     double tail_ms;          /* wall time after the last row's device work completed */
 } cm_pipeline_stats;
 
-/* Arena bytes for an index that runs schedule s with cm_run_schedule: the
- * fixed tables, the largest set of images resident at once (a row's loads
- * count before the row, its frees after it), a margin for fragmentation of
- * the arena's first-fit placement (1/8 of that set plus its largest image),
- * and the largest row's plan table. */
+/* Arena bytes for an index that runs schedule s (made from pairs[n_pairs])
+ * with cm_run_schedule: the fixed tables, the largest set of images resident
+ * at once (a row's loads count before the row, its frees after it), a margin
+ * for fragmentation of the arena's first-fit placement (1/8 of that set plus
+ * its largest image), and the largest row's plan (cm_plan_bytes). */
 cm_status cm_schedule_arena_bytes(const cm_schedule* s, const cm_params* p, int32_t n_images, const int32_t* n_desc,
-                                  uint64_t* bytes);
+                                  const cm_pair* pairs, int64_t n_pairs, uint64_t* bytes);
 /* Device workspace of cm_run_schedule for this schedule (bytes). */
 cm_status cm_pipeline_workspace_bytes(const cm_index* ix, const cm_schedule* s, const cm_pair* pairs, int64_t n_pairs,
                                       uint64_t* bytes);

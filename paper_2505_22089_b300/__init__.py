@@ -25,11 +25,24 @@ MEM_HOST, MEM_DEVICE, MEM_DEVICE_INPLACE = 0, 1, 2
 # Arena headroom the binding adds to cm_index_bytes for match-plan tables
 # (24 bytes per planned pair): room for about 600,000 pairs of plans.
 PLAN_HEADROOM = 16 << 20
+# With the BF16 / FP8 reranks a plan also holds its top-K hand-over (6 K bytes
+# per query row, 10 K with FP8); the default arena has room for plans totalling this many
+# times the index's descriptors as query rows.
+TC_PLAN_ROWS_FACTOR = 16
+
+
+def default_headroom(p, n_desc) -> int:
+    """Arena bytes the binding adds to cm_index_bytes by default."""
+    extra = 0
+    if p.rerank in (RERANK["bf16"], RERANK["fp8"]):
+        per_row = p.K * (10 if p.rerank == RERANK["fp8"] else 6)
+        extra = TC_PLAN_ROWS_FACTOR * int(np.asarray(n_desc, dtype=np.int64).sum()) * per_row
+    return PLAN_HEADROOM + extra
 
 # Every symbol include/cashmatch.h declares (checked by the CPU tests).
 EXPORTS = [
     "cm_version", "cm_last_error", "cm_params_default", "cm_params_check", "cm_make_weights", "cm_image_bytes",
-    "cm_index_bytes", "cm_schedule_blocks", "cm_schedule_num_rows", "cm_schedule_num_iterations",
+    "cm_index_bytes", "cm_plan_bytes", "cm_schedule_blocks", "cm_schedule_num_rows", "cm_schedule_num_iterations",
     "cm_schedule_get_row", "cm_free_schedule", "cm_gps_order", "cm_index_create", "cm_index_set_mean",
     "cm_index_mean_device", "cm_index_col_sums", "cm_index_check", "cm_index_load", "cm_index_rehash", "cm_index_evict", "cm_build_index",
     "cm_index_image_view", "cm_index_destroy", "cm_match_plan_create", "cm_match_plan_rows", "cm_match_plan_run",
@@ -147,7 +160,8 @@ def lib():
             "cm_sequence_launch": (i32, [vp, vp]),
             "cm_sequence_kernels": (i32, [vp]),
             "cm_sequence_destroy": (None, [vp]),
-            "cm_schedule_arena_bytes": (i32, [vp, P, i32, vp, ctypes.POINTER(u64)]),
+            "cm_schedule_arena_bytes": (i32, [vp, P, i32, vp, vp, i64, ctypes.POINTER(u64)]),
+            "cm_plan_bytes": (i32, [P, i64, i64, ctypes.POINTER(u64)]),
             "cm_pipeline_workspace_bytes": (i32, [vp, vp, vp, i64, ctypes.POINTER(u64)]),
             "cm_run_schedule": (i32, [vp, vp, vp, i64, vp, vp, u64, vp, vp, i32, vp,
                                       ctypes.POINTER(PipelineStats)]),
@@ -251,8 +265,23 @@ def schedule_arena_bytes(sched: Schedule, p: Params, n_desc) -> int:
     """cm_schedule_arena_bytes: arena an index needs to run `sched` with run_schedule."""
     nd = np.ascontiguousarray(n_desc, dtype=np.int32)
     b = ctypes.c_uint64()
-    check(lib().cm_schedule_arena_bytes(sched.h, ctypes.byref(p), len(nd), nd.ctypes.data, ctypes.byref(b)))
+    check(lib().cm_schedule_arena_bytes(sched.h, ctypes.byref(p), len(nd), nd.ctypes.data, sched.pairs.ctypes.data,
+                                        len(sched.pairs), ctypes.byref(b)))
     return b.value
+
+
+def plan_bytes(p: Params, n_pairs: int, rows: int) -> int:
+    """cm_plan_bytes: arena bytes a plan takes from its index."""
+    b = ctypes.c_uint64()
+    check(lib().cm_plan_bytes(ctypes.byref(p), int(n_pairs), int(rows), ctypes.byref(b)))
+    return b.value
+
+
+def pairs_plan_bytes(p: Params, n_desc, pairs) -> int:
+    """Arena bytes of one plan over `pairs` (query rows = sum of N_i)."""
+    pr = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    rows = int(np.asarray(n_desc, dtype=np.int64)[pr[:, 0]].sum()) if len(pr) else 0
+    return plan_bytes(p, len(pr), rows)
 
 
 def verify_affine(kp_i, kp_j, matches, thresh_px: float = 3.0, max_iters: int = 1000, seed: int = 1):
@@ -307,7 +336,7 @@ class Index:
         self.n_desc = np.ascontiguousarray(n_desc, dtype=np.int32)
         if arena is None:
             if arena_bytes is None:
-                arena_bytes = index_bytes(p, self.n_desc, inplace) + PLAN_HEADROOM
+                arena_bytes = index_bytes(p, self.n_desc, inplace) + default_headroom(p, self.n_desc)
             arena = torch.empty(int(arena_bytes) + 256, dtype=torch.uint8, device=device)
         self.arena = arena
         base = (self.arena.data_ptr() + 255) // 256 * 256
@@ -330,7 +359,7 @@ class Index:
         if mem is None:
             mem = MEM_DEVICE_INPLACE if on_dev else MEM_HOST
         if arena_bytes is None:
-            arena_bytes = index_bytes(p, self.n_desc, mem == MEM_DEVICE_INPLACE) + PLAN_HEADROOM
+            arena_bytes = index_bytes(p, self.n_desc, mem == MEM_DEVICE_INPLACE) + default_headroom(p, self.n_desc)
         self.arena = torch.empty(int(arena_bytes) + 256, dtype=torch.uint8, device="cuda")
         base = (self.arena.data_ptr() + 255) // 256 * 256
         ptr = desc.data_ptr() if isinstance(desc, torch.Tensor) else np.ascontiguousarray(desc).ctypes.data

@@ -131,6 +131,14 @@ extern "C" cm_status cm_image_bytes(const cm_params* p, int32_t n_desc, uint64_t
     return CM_OK;
 }
 
+extern "C" cm_status cm_plan_bytes(const cm_params* p, int64_t n_pairs, int64_t rows, uint64_t* bytes) {
+    cm_status st = cm_params_check(p);
+    if (st != CM_OK) return st;
+    if (!bytes || n_pairs < 0 || rows < 0) return fail(CM_ERR_INVALID, "cm_plan_bytes: bad argument");
+    *bytes = plan_bytes(p, n_pairs, rows);
+    return CM_OK;
+}
+
 extern "C" cm_status cm_index_bytes(const cm_params* p, int32_t n_images, const int32_t* n_desc, int32_t inplace,
                                     uint64_t* bytes) {
     cm_status st = cm_params_check(p);
@@ -344,6 +352,7 @@ static cm_status hash_batch(cm_index* ix, const HashLaunch& h, cudaStream_t s) {
         CM_CUDA(launch_hash(h, ix->sms, s));
     }
     CM_CUDA(launch_bucket(h, s));
+    if (tc_rerank(&ix->p)) CM_CUDA(launch_xcopy(h, s));
     return CM_OK;
 }
 
@@ -515,7 +524,7 @@ extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, in
     if (items > INT32_MAX / 2) return fail(CM_ERR_INVALID, "plan: too many work items");
     cm_match_plan* pl = new (std::nothrow) cm_match_plan();
     if (!pl) return fail(CM_ERR_NOMEM, "plan: host allocation");
-    const uint64_t bytes = align_up((uint64_t)n_pairs * sizeof(DevPair)) + kAlign;  // table, then the counter
+    const uint64_t bytes = plan_bytes(&ix->p, n_pairs, rows);
     if (!ix->alloc.alloc(bytes, &pl->table_at)) {
         delete pl;
         return fail(CM_ERR_BUDGET, "plan: arena full (%llu bytes for the pair table)", (unsigned long long)bytes);
@@ -566,6 +575,18 @@ extern "C" cm_status cm_match_plan_run(cm_match_plan* pl, const cm_match_out* ou
     m.algo = ix->p.algo == CM_ALGO_WARP ? CM_ALGO_WARP : CM_ALGO_TILE;   // auto: tile, if its tile fits
     if (m.algo == CM_ALGO_TILE && match_smem_bytes(m.S, m.K) > kMatchSmemLimit) m.algo = CM_ALGO_WARP;
     m.err = ix->at<int>(ix->fx.err);
+    if (tc_rerank(&ix->p)) {
+        // scan (top-K lists to the plan's hand-over area), then the tensor-core rerank
+        m.algo = CM_ALGO_TILE;
+        const HandOver ho = hand_over(&ix->p, pl->rows);
+        uint8_t* base = ix->arena + counter_at + kAlign;
+        m.topk16 = reinterpret_cast<uint16_t*>(base + ho.idx);
+        m.hnorm = reinterpret_cast<uint32_t*>(base + ho.norm);
+        m.hscale = ix->p.rerank == CM_RERANK_FP8 ? reinterpret_cast<float*>(base + ho.scale) : nullptr;
+        CM_CUDA(launch_match(m, ix->sms, s));
+        CM_CUDA(launch_rerank_tc(m, ix->sms, s));
+        return CM_OK;
+    }
     CM_CUDA(m.algo == CM_ALGO_TILE ? launch_match(m, ix->sms, s) : launch_match_wq(m, ix->sms, s));
     return CM_OK;
 }

@@ -42,6 +42,8 @@ struct SlotLayout {
     uint64_t desc, key, code, scode, sidx, off, hist, brank, norm, xq, xscale, total;
 };
 
+inline bool tc_rerank(const cm_params* p) { return p->rerank == CM_RERANK_BF16 || p->rerank == CM_RERANK_FP8; }
+
 inline SlotLayout slot_layout(const cm_params* p, int64_t n, bool inplace) {
     const int64_t B = 1ll << p->m;
     SlotLayout s{};
@@ -56,8 +58,13 @@ inline SlotLayout slot_layout(const cm_params* p, int64_t n, bool inplace) {
     s.hist = take((uint64_t)p->L * B * 4);
     s.brank = take((uint64_t)p->L * 256);
     s.norm = take((uint64_t)n * 4);
-    s.xq = 0;       // tensor-core reranks convert rows while staging them: no stored copy
+    s.xq = 0;
     s.xscale = 0;
+    if (p->rerank == CM_RERANK_BF16) s.xq = take((uint64_t)n * 256);   // rows start on 256-byte boundaries
+    if (p->rerank == CM_RERANK_FP8) {
+        s.xq = take((uint64_t)n * 128);
+        s.xscale = take((uint64_t)n * 4);
+    }
     s.total = o;
     return s;
 }
@@ -233,9 +240,30 @@ struct cm_index {
     }
 };
 
+// Arena bytes of a plan: its pair table, the work counter and, for the
+// tensor-core reranks, the [rows][K] top-K hand-over from scan to rerank
+// (index, squared norm and, for FP8, scale of every kept candidate).
+// Hand-over areas after the counter: indices u16, norms u32, scales f32 (FP8), [rows][K] each.
+struct HandOver {
+    uint64_t idx, norm, scale, total;
+};
+inline HandOver hand_over(const cm_params* p, int64_t rows) {
+    HandOver h{};
+    if (!tc_rerank(p)) return h;
+    const uint64_t e = (uint64_t)rows * (uint64_t)p->K;
+    h.idx = 0;
+    h.norm = align_up(e * 2);
+    h.scale = h.norm + align_up(e * 4);
+    h.total = h.scale + (p->rerank == CM_RERANK_FP8 ? align_up(e * 4) : 0);
+    return h;
+}
+inline uint64_t plan_bytes(const cm_params* p, int64_t n_pairs, int64_t rows) {
+    return align_up((uint64_t)n_pairs * sizeof(DevPair)) + kAlign + hand_over(p, rows).total;
+}
+
 struct cm_match_plan {
     cm_index* ix = nullptr;
-    uint64_t table_at = 0;   // arena offset: [n_pairs] DevPair, then the work counter
+    uint64_t table_at = 0;   // arena offset: [n_pairs] DevPair, the work counter, the top-K hand-over
     int64_t n_pairs = 0;
     int64_t rows = 0;
     int32_t n_items = 0;

@@ -32,8 +32,8 @@ struct DevImage {
     uint32_t* hist;        // [L][B] bucket counts (zero between hashing passes)
     uint8_t* brank;        // [L][256] rank of each bucket by run length (ties by bucket id)
     uint32_t* norm;        // [n]   squared norm of the raw descriptor (tensor-core forms)
-    void* xq;              // [n][128] BF16 or FP8 copy (tensor-core forms)
-    float* xscale;         // [n]   FP8 scale (FP8 form)
+    void* xq;              // [n] rows of the tensor-core rerank copy: BF16 [128] (256 B) or E4M3 [128] (128 B)
+    float* xscale;         // [n]   FP8 row scale (max / 448)
     int32_t n;
     int32_t pad;
 };
@@ -74,6 +74,10 @@ struct MatchLaunch {
     int32_t algo;              // CM_ALGO_TILE or CM_ALGO_WARP
     unsigned* counter;         // work counter (zeroed before each launch)
     int* err;                  // set to 1 when a bounded device wait gives up
+    // tensor-core forms, scan -> rerank hand-over, [rows][K] in rank order:
+    uint16_t* topk16;          // database indices (0xFFFF empty)
+    uint32_t* hnorm;           // their squared norms
+    float* hscale;             // their FP8 row scales (FP8 form)
     cm_match_out out;
 };
 
@@ -94,5 +98,9 @@ cudaError_t launch_compact(const DevPair* pairs, int n_pairs, const DevImage* im
                            uint32_t* counts, unsigned long long* offsets, unsigned long long* total, uint32_t* out,
                            unsigned long long capacity, cudaStream_t s);                 // cm_compact.cu
 int hash_npg(int P_pad);
+// Tensor-core rerank (cm_rerank_tc.cu): row copies written after hashing, and
+// the rerank of a plan's top-K lists.
+cudaError_t launch_xcopy(const HashLaunch& h, cudaStream_t s);
+cudaError_t launch_rerank_tc(const MatchLaunch& m, int sm_count, cudaStream_t s);
 
 }  // namespace cm

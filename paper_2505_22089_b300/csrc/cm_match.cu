@@ -25,11 +25,7 @@
 #include <cstdint>
 
 #include "cm_internal.h"
-
-namespace cm {
-__device__ __forceinline__ bool ratio_pass(uint32_t d1, uint32_t d2, int num, int den, uint32_t& rechecks);
-}
-#include "cm_rerank_tc.cuh"
+#include "cm_ratio.cuh"
 
 namespace cm {
 
@@ -152,17 +148,6 @@ __device__ __forceinline__ void scan_run(const uint4* __restrict__ codes, const 
     if (__any_sync(kFull, cnt > 0)) flush_hits<K>(buf, cnt, idx, c0, s);
 }
 
-// Exact ratio test dis(q1) < t_r dis(q2), t_r = num/den: FP32 where the ratio is
-// at least 1e-3 away from t_r (FP32 error is ~1e-7 there), FP64 re-check
-// otherwise (d^2 < 2^24, so den^2 d1^2 and num^2 d2^2 are exact in FP64).
-__device__ __forceinline__ bool ratio_pass(uint32_t d1, uint32_t d2, int num, int den, uint32_t& rechecks) {
-    if (d2 == 0u) return false;
-    const float r = sqrtf((float)d1 / (float)d2);
-    const float tr = (float)num / (float)den;
-    if (fabsf(r - tr) >= 1e-3f) return r < tr;
-    ++rechecks;
-    return (double)den * (double)den * (double)d1 < (double)num * (double)num * (double)d2;
-}
 
 __device__ __forceinline__ float offset_byte(uint32_t w, int b) {
     // 2^23 + byte exactly; the difference of two such values is exact
@@ -183,23 +168,12 @@ __global__ void __launch_bounds__(kMatchThreads, 1) k_match(MatchLaunch ml) {
     uint32_t* hitbuf = order + 256;                               // [kHitCap][kMatchThreads]
     __shared__ int s_item;
     __shared__ uint32_t s_stats[3];
-    __shared__ uint64_t s_mbar;
-    __shared__ uint32_t s_tmem;
-    __shared__ float s_scales[6 * 192];   // FP8 rerank: per-row scales of the staged sub-tiles
-    __shared__ uint32_t s_norms[6 * 192]; // tensor-core reranks: squared norms of the staged rows
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int B = 1 << ml.m;
     const bool tcr = ml.rerank == CM_RERANK_BF16 || ml.rerank == CM_RERANK_FP8;
     if (tid < 3) s_stats[tid] = 0;
-    uint32_t rechecks = 0, matches = 0, swaps = 0, parity = 0;
-    if (tcr) {
-        if (tid == 0) tc::mbar_init(&s_mbar, 1);
-        if ((tid >> 5) == 0) tc::tmem_alloc(&s_tmem, 256);
-        tc::fence_before();
-        __syncthreads();
-        tc::fence_after();
-    }
+    uint32_t rechecks = 0, matches = 0, swaps = 0;
 
     for (;;) {
         __syncthreads();
@@ -300,17 +274,22 @@ __global__ void __launch_bounds__(kMatchThreads, 1) k_match(MatchLaunch ml) {
             __syncthreads();
         }
 
-        // Sec. 2.3.1 step (4) on the tensor cores (BF16 / FP8 forms)
+        // Tensor-core forms: step (4) runs in k_rerank_tc; hand over the top-K lists
         if (tcr) {
-            unsigned char* region = reinterpret_cast<unsigned char*>(qcode);
-            // qcode .. the end of the hit buffer is free after the table passes
-            const uint32_t region_bytes = (uint32_t)S * 28 + 2 * 256 * 4 + (uint32_t)kHitCap * kMatchThreads * 4;
-            if (ml.rerank == CM_RERANK_BF16)
-                rerank_tc<K, false>(ml, P, I, J, q0, nq, st, region, region_bytes, s_scales, s_norms, s_tmem, &s_mbar, parity,
-                                    rechecks, matches, swaps);
-            else
-                rerank_tc<K, true>(ml, P, I, J, q0, nq, st, region, region_bytes, s_scales, s_norms, s_tmem, &s_mbar, parity,
-                                   rechecks, matches, swaps);
+            // each kept candidate with its squared norm (and FP8 scale): the rerank then
+            // reads one contiguous record per candidate instead of gathering them
+            const int64_t r0 = P.row_off + q0;
+            const bool fp8 = ml.rerank == CM_RERANK_FP8;
+#pragma unroll 4
+            for (int e = tid; e < nq * K; e += kMatchThreads) {
+                const uint32_t key = st[e];
+                const bool hv = key != kEmpty;
+                const int j = (int)(key & 0xFFFFu);
+                ml.topk16[r0 * K + e] = hv ? (uint16_t)j : (uint16_t)0xFFFFu;
+                ml.hnorm[r0 * K + e] = hv ? __ldg(J.norm + j) : 0u;
+                if (fp8) ml.hscale[r0 * K + e] = hv ? __ldg(J.xscale + j) : 0.f;
+                if (ml.out.topk) ml.out.topk[r0 * K + e] = hv ? j : -1;
+            }
             continue;
         }
         // Sec. 2.3.1 step (4) on CUDA cores: exact distances of the top K, q1 / q2, ratio test.
@@ -395,10 +374,6 @@ __global__ void __launch_bounds__(kMatchThreads, 1) k_match(MatchLaunch ml) {
                 }
             }
         }
-    }
-    if (tcr) {
-        __syncthreads();
-        if ((tid >> 5) == 0) tc::tmem_dealloc(s_tmem, 256);
     }
     if (ml.out.stats) {
         if (rechecks) atomicAdd(&s_stats[0], rechecks);

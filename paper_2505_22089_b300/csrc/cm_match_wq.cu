@@ -18,6 +18,7 @@
 #include <cstdint>
 
 #include "cm_internal.h"
+#include "cm_ratio.cuh"
 
 namespace cm {
 
@@ -75,17 +76,6 @@ __device__ __forceinline__ uint32_t list_merge(uint32_t mykey, uint32_t cand, in
         v = ((lane & j) == 0) ? min(v, o) : max(v, o);
     }
     return lane < K ? v : kEmpty;
-}
-
-// Exact ratio test dis(q1) < t_r dis(q2), t_r = num/den: FP32 where the ratio is
-// at least 1e-3 away from t_r, FP64 re-check otherwise (exact: d^2 < 2^24).
-__device__ __forceinline__ bool ratio_pass(uint32_t d1, uint32_t d2, int num, int den, uint32_t& rechecks) {
-    if (d2 == 0u) return false;
-    const float r = sqrtf((float)d1 / (float)d2);
-    const float tr = (float)num / (float)den;
-    if (fabsf(r - tr) >= 1e-3f) return r < tr;
-    ++rechecks;
-    return (double)den * (double)den * (double)d1 < (double)num * (double)num * (double)d2;
 }
 
 __device__ __forceinline__ float offset_byte(uint32_t w, int b) {

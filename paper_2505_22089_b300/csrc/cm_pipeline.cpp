@@ -408,14 +408,14 @@ struct Pipe {
 }  // namespace
 
 extern "C" cm_status cm_schedule_arena_bytes(const cm_schedule* s, const cm_params* p, int32_t n_images,
-                                             const int32_t* n_desc, uint64_t* bytes) {
+                                             const int32_t* n_desc, const cm_pair* pairs, int64_t n_pairs,
+                                             uint64_t* bytes) {
     cm_status st = cm_params_check(p);
     if (st != CM_OK) return st;
-    if (!s || !bytes || n_images < 0 || (n_images && !n_desc))
+    if (!s || !bytes || n_images < 0 || (n_images && !n_desc) || n_pairs < 0 || (n_pairs && !pairs))
         return fail(CM_ERR_INVALID, "cm_schedule_arena_bytes: bad argument");
     std::vector<char> res(n_images, 0);
-    uint64_t cur = 0, peak = 0, largest = 0;
-    int64_t max_pairs = 0;
+    uint64_t cur = 0, peak = 0, largest = 0, plan = 0;
     const int32_t R = cm_schedule_num_rows(s);
     for (int32_t r = 0; r < R; ++r) {
         cm_schedule_row row{};
@@ -429,7 +429,14 @@ extern "C" cm_status cm_schedule_arena_bytes(const cm_schedule* s, const cm_para
             largest = std::max(largest, b);
         }
         peak = std::max(peak, cur);
-        max_pairs = std::max<int64_t>(max_pairs, row.n_pairs);
+        int64_t rows = 0;
+        for (int64_t k = 0; k < row.n_pairs; ++k) {
+            const int64_t id = row.pairs[k];
+            if (id < 0 || id >= n_pairs || pairs[id].i < 0 || pairs[id].i >= n_images)
+                return fail(CM_ERR_INVALID, "cm_schedule_arena_bytes: pair %lld", (long long)id);
+            rows += n_desc[pairs[id].i];
+        }
+        plan = std::max(plan, plan_bytes(p, row.n_pairs, rows));
         for (int k = 0; k < row.n_free; ++k) {
             const int i = row.free_ids[k];
             if (i >= 0 && i < n_images && res[i]) {
@@ -439,7 +446,6 @@ extern "C" cm_status cm_schedule_arena_bytes(const cm_schedule* s, const cm_para
         }
     }
     // first-fit placement of unequal slots can fragment: 1/8 of the peak plus the largest slot of margin
-    const uint64_t plan = align_up((uint64_t)max_pairs * sizeof(DevPair)) + 2 * kAlign;
     *bytes = fixed_layout(p, n_images).total + peak + peak / 8 + largest + plan + 64 * kAlign;
     return CM_OK;
 }
@@ -531,7 +537,9 @@ extern "C" cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const c
             return bail(CM_ERR_CUDA);
         }
     for (int w = 0; w < n_workers; ++w) threads.emplace_back([&P] { P.worker(); });
-    const int hash_kernels = ix->p.projection == CM_PROJ_TC ? 3 : 2;
+    // hashing: (bias +) projection + buckets (+ the rerank row copies); matching: scan (+ tensor-core rerank)
+    const int hash_kernels = (ix->p.projection == CM_PROJ_TC ? 3 : 2) + (tc_rerank(&ix->p) ? 1 : 0);
+    const int match_kernels = tc_rerank(&ix->p) ? 2 : 1;
 
     for (int32_t r = 0; r < R; ++r) {
         cm_schedule_row row{};
@@ -573,7 +581,7 @@ extern "C" cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const c
                 st = cm_match_plan_compact(pl, d_best, d_counts, d_offsets, d_offsets + row.n_pairs, P.buf[b].d_matches,
                                            (uint64_t)pl->rows, stream);
             S.queries += pl->rows;
-            S.kernels += (pl->n_items ? 1 : 0) + 3;
+            S.kernels += (pl->n_items ? match_kernels : 0) + 3;
             cm_match_plan_destroy(pl);  // its table is reused only by work ordered after this row
             if (st != CM_OK) return bail(st);
             if (cudaMemcpyAsync(P.buf[b].offsets, d_offsets, (size_t)(row.n_pairs + 1) * 8, cudaMemcpyDeviceToHost,

@@ -1,0 +1,572 @@
+// Tensor-core rerank (Sec. 2.3.1 step (4), BF16 and FP8 forms).
+//
+// k_xcopy writes, after hashing, each resident descriptor once more in the
+// rerank's operand type: BF16 (exact for uint8, 256-byte rows) or E4M3 scaled
+// by the row maximum / 448 (128-byte rows, scale kept per row).
+//
+// k_rerank_tc takes the top-K lists the scan kernel left in global memory.  A
+// sub-tile holds QS = 128 / K queries of one pair: its A operand is their K
+// candidate rows each (M = 128), its B operand their QS query rows (N = NB >= 16,
+// padded).  One MMA chain (K = 128) gives every candidate's dot product with
+// every query of the sub-tile, of which candidate row r needs column r / K.
+// The kernel is persistent and warp-specialised, work items dealt round-robin:
+//   warps 0-7    producers: 16-byte cp.async copies of the A and B rows from the
+//                row copies into a ring of shared-memory stages, in the
+//                128-byte-swizzled K-major operand layout; a stage is handed to
+//                the MMA once its copies landed (wait_group, proxy fence,
+//                mbarrier arrive), several stages in flight per thread;
+//   warp 8       MMA issuer: one thread, tcgen05.mma into one of ACC TMEM
+//                accumulators, commits that free the stage and fill the
+//                accumulator;
+//   warps 9-16   two epilogue groups of 4 warps (each the 128 TMEM lanes),
+//                taking the sub-tiles in turn: d^2 = |x|^2 + |y|^2 - 2 x.y,
+//                q1 / q2 by (d^2, index) across the K lanes of a query, the
+//                exact ratio test, outputs.
+//   BF16: the dot is an exact integer in FP32, so d^2 is exact.
+//   FP8:  the approximate d^2 picks q1, q2, which are re-scored exactly on
+//         CUDA cores; a re-score that reverses their order is counted.
+// Every wait is bounded; a wait that gives up sets the error flag and ends the
+// kernel's loops.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <cstdint>
+
+#include "cm_internal.h"
+#include "cm_ratio.cuh"
+#include "cm_tc.cuh"
+
+namespace cm {
+
+namespace {
+
+constexpr int kProdWarps = 8;
+constexpr int kProd = kProdWarps * 32;            // producer threads
+constexpr int kMmaWarp = kProdWarps;              // the MMA warp
+constexpr int kEpiGroups = 2;                     // epilogue groups of 4 warps
+constexpr int kEpiWarp0 = kProdWarps + 1;
+constexpr int kRrThreads = (kProdWarps + 1 + 4 * kEpiGroups) * 32;
+constexpr int kRrPolls = 1 << 24;
+constexpr uint16_t kNoCand = 0xFFFFu;
+
+template <int K, bool FP8>
+struct RR {
+    static constexpr int QS = 128 / K;                    // queries per sub-tile
+    static constexpr int NB = QS < 16 ? 16 : QS;          // B rows = MMA N
+    static constexpr int HALVES = FP8 ? 1 : 2;            // 128-byte column blocks per row
+    static constexpr uint32_t A_HALF = 128u * 128u;       // 128 rows x 128 bytes
+    static constexpr uint32_t B_HALF = (uint32_t)NB * 128u;
+    static constexpr uint32_t STAGE = HALVES * (A_HALF + B_HALF);
+    static constexpr int STAGES_FIT = (int)((216u * 1024u) / STAGE);
+    static constexpr int STAGES = STAGES_FIT < 8 ? STAGES_FIT : 8;
+    static constexpr int DEPTH = STAGES - 1;              // cp.async groups in flight per producer thread
+    static constexpr int ACC_FIT = 256 / NB;
+    static constexpr int ACC = ACC_FIT < 8 ? ACC_FIT : 8;  // a multiple of the epilogue groups, which take turns
+    static constexpr int STEPS = FP8 ? 4 : 8;              // MMAs of 32 bytes of K each
+    static constexpr int CPR = FP8 ? 8 : 16;               // 16-byte chunks per row copy
+    static constexpr int ROWS = 128 + NB;                   // staged rows per sub-tile
+    static constexpr int CHUNKS = ROWS * CPR;
+    static constexpr int PER_THREAD = (CHUNKS + kProd - 1) / kProd;
+    // stages (1024-aligned) + barriers: full/empty per stage, full/empty per accumulator
+    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 8 * (2 * STAGES + 2 * ACC) + 64;
+    static_assert(ACC % kEpiGroups == 0, "accumulators are dealt to the epilogue groups in turn");
+    static_assert(STAGES >= 2, "stage ring");
+    static_assert(B_HALF % 1024 == 0, "B tile keeps 1024-byte alignment");
+};
+
+// A sub-tile: QS consecutive queries of one pair.  Sub-tile u is part u % per_item
+// of work item u / per_item; CTA b takes u = b, b + grid, ..., so at any moment
+// the CTAs work on neighbouring sub-tiles of the same one or two pairs and
+// share the database rows they read in L2.
+struct SubTile {
+    int q0;        // first query (local row of image i)
+    int nq;        // queries (<= QS); 0 = nothing to do
+    int64_t row;   // output row of the first query
+    // the pair's images: row copies, query norms / scales, raw rows (FP8 re-score)
+    const unsigned char *ixq, *jxq;
+    const uint32_t* inorm;
+    const float* iscale;
+    const uint8_t *idesc, *jdesc;
+};
+
+// Walks a CTA's increasing sequence of sub-tiles; the current pair's record is
+// kept in registers and reloaded only when the sequence crosses into a later pair.
+struct Cursor {
+    int pair = -1, item0 = 0, item_end = 0, n_i = 0;
+    int64_t row_off = 0;
+    const unsigned char *ixq = nullptr, *jxq = nullptr;
+    const uint32_t* inorm = nullptr;
+    const float* iscale = nullptr;
+    const uint8_t *idesc = nullptr, *jdesc = nullptr;
+
+    __device__ __forceinline__ SubTile at(const MatchLaunch& ml, int u, int per_item, int qs) {
+        const int item = u / per_item;
+        while (item >= item_end && pair + 1 < ml.n_pairs) {
+            ++pair;
+            const DevPair P = ml.pairs[pair];
+            item0 = P.item0;
+            item_end = P.item0 + P.nitems;
+            row_off = P.row_off;
+            const DevImage& I = ml.imgs[P.i];
+            const DevImage& J = ml.imgs[P.j];
+            n_i = I.n;
+            ixq = static_cast<const unsigned char*>(I.xq);
+            jxq = static_cast<const unsigned char*>(J.xq);
+            inorm = I.norm;
+            iscale = I.xscale;
+            idesc = I.desc;
+            jdesc = J.desc;
+        }
+        SubTile t;
+        t.q0 = (item - item0) * ml.S + (u % per_item) * qs;
+        t.nq = (item < item_end && t.q0 < n_i) ? min(qs, n_i - t.q0) : 0;
+        t.row = row_off + t.q0;
+        t.ixq = ixq;
+        t.jxq = jxq;
+        t.inorm = inorm;
+        t.iscale = iscale;
+        t.idesc = idesc;
+        t.jdesc = jdesc;
+        return t;
+    }
+};
+
+// Bounded wait for an mbarrier phase that also gives up once another role aborted.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, volatile int* abort_flag) {
+    for (int it = 0; it < kRrPolls; it += 32) {
+        if (tc::mbar_wait(mbar, parity, 32)) return true;
+        if (*abort_flag) return false;
+    }
+    return false;
+}
+
+// The same, decided once per warp (lane 0 polls) so the warp stays converged.
+__device__ __forceinline__ bool warp_wait(uint64_t* mbar, uint32_t parity, volatile int* abort_flag) {
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) ok = wait_or_abort(mbar, parity, abort_flag);
+    return __shfl_sync(0xFFFFFFFFu, ok ? 1 : 0, 0) != 0;
+}
+
+__device__ __forceinline__ uint32_t exact_d2(const uint8_t* x, const uint8_t* y, int nb) {
+    uint32_t acc = 0;
+    for (int o = 0; o < nb; o += 16) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4*>(x + o));
+        const uint4 b = __ldg(reinterpret_cast<const uint4*>(y + o));
+        const uint32_t d0 = __vabsdiffu4(a.x, b.x), d1 = __vabsdiffu4(a.y, b.y);
+        const uint32_t d2 = __vabsdiffu4(a.z, b.z), d3 = __vabsdiffu4(a.w, b.w);
+        acc = __dp4a(d0, d0, acc);
+        acc = __dp4a(d1, d1, acc);
+        acc = __dp4a(d2, d2, acc);
+        acc = __dp4a(d3, d3, acc);
+    }
+    return acc;
+}
+
+template <int K, bool FP8>
+__global__ void __launch_bounds__(kRrThreads, 1) k_rerank_tc(MatchLaunch ml) {
+    using C = RR<K, FP8>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)C::STAGES * C::STAGE);
+    uint64_t* empty = full + C::STAGES;
+    uint64_t* tfull = empty + C::STAGES;
+    uint64_t* tempty = tfull + C::ACC;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    __shared__ uint32_t s_stats[3];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            tc::mbar_init(&full[s], kProd);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < C::ACC; ++a) {
+            tc::mbar_init(&tfull[a], 1);
+            tc::mbar_init(&tempty[a], 128);
+        }
+        s_abort = 0;
+        s_stats[0] = s_stats[1] = s_stats[2] = 0;
+    }
+    if (warp == kMmaWarp) tc::tmem_alloc(&s_tmem, 256);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = s_tmem;
+    volatile int* abort_flag = &s_abort;
+
+    auto give_up = [&]() {
+        *abort_flag = 1;
+        if (ml.err) atomicExch(ml.err, 1);
+    };
+    const int per_item = ml.S / C::QS;
+    const int n_sub = ml.n_items * per_item;
+    // Every role walks the same sequence of non-empty sub-tiles, so the local
+    // counter `it` (stage it % STAGES, accumulator it % ACC) agrees across roles.
+
+    if (warp < kProdWarps) {
+        // ---------------- producers: thread t copies chunks t, t + kProd, ... of each sub-tile
+        // (chunk e: staged row e / CPR, 16-byte chunk e % CPR; rows 0-127 = A, then B)
+        const int rb = FP8 ? 128 : 256;   // bytes per row copy
+        int it = 0;          // sub-tiles issued
+        Cursor cursor;
+        bool ok = true;
+        int u = blockIdx.x - (int)gridDim.x;
+        // advances to the next non-empty sub-tile of this CTA's sequence
+        auto next = [&](SubTile& t) -> bool {
+            for (u += gridDim.x; u < n_sub; u += gridDim.x) {
+                t = cursor.at(ml, u, per_item, C::QS);
+                if (t.nq > 0) return true;
+            }
+            return false;
+        };
+        // candidate index of each of this thread's chunks (kNoCand: not a candidate row);
+        // loaded one sub-tile before it is used
+        auto idx_of = [&](const SubTile& t, uint32_t (&jr)[C::PER_THREAD]) {
+#pragma unroll
+            for (int q = 0; q < C::PER_THREAD; ++q) {
+                const int r = (tid + q * kProd) / C::CPR;
+                jr[q] = (r < 128 && r / K < t.nq) ? (uint32_t)ml.topk16[t.row * K + r] : (uint32_t)kNoCand;
+            }
+        };
+        // copies sub-tile t into stage it % STAGES; after DEPTH - 1 later groups have been
+        // issued a group has landed: proxy fence, then its stage goes to the MMA
+        auto issue = [&](const SubTile& t, const uint32_t (&jr)[C::PER_THREAD]) -> bool {
+            const int s = it % C::STAGES;
+            const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+            if (!warp_wait(&empty[s], ph ^ 1u, abort_flag)) return false;
+            const uint32_t A = tc::smem_addr(ring + (size_t)s * C::STAGE);
+            const uint32_t B = A + C::HALVES * C::A_HALF;
+            const unsigned char* qrow = t.ixq + (size_t)t.q0 * rb;   // a valid row for padding
+#pragma unroll
+            for (int q = 0; q < C::PER_THREAD; ++q) {
+                const int e = tid + q * kProd;
+                if (e < C::CHUNKS) {
+                    const int r = e / C::CPR, c = e % C::CPR;
+                    const int h = c >> 3, c8 = c & 7;     // 128-byte column block, chunk in it
+                    const uint32_t dst = r < 128
+                        ? A + (uint32_t)h * C::A_HALF + (uint32_t)r * 128u + (uint32_t)((c8 ^ (r & 7)) << 4)
+                        : B + (uint32_t)h * C::B_HALF + (uint32_t)(r - 128) * 128u +
+                              (uint32_t)((c8 ^ ((r - 128) & 7)) << 4);
+                    const unsigned char* src = r < 128 ? (jr[q] != kNoCand ? t.jxq + (size_t)jr[q] * rb : qrow)
+                                                        : qrow + (size_t)(r - 128 < t.nq ? r - 128 : 0) * rb;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src + c * 16)
+                                 : "memory");
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            if (it >= C::DEPTH - 1) {
+                asm volatile("cp.async.wait_group %0;" :: "n"(C::DEPTH - 1) : "memory");
+                tc::fence_proxy_async();
+                tc::mbar_arrive(&full[(it - (C::DEPTH - 1)) % C::STAGES]);
+            }
+            ++it;
+            return true;
+        };
+        // ping-pong between two register sets, so a prefetched index is never copied
+        // (a copy would wait for the load)
+        SubTile tA{}, tB{};
+        uint32_t jA[C::PER_THREAD], jB[C::PER_THREAD];
+        bool hA = next(tA), hB = false;
+        if (hA) idx_of(tA, jA);
+        while (hA) {
+            hB = next(tB);
+            if (hB) idx_of(tB, jB);
+            if (!issue(tA, jA)) { ok = false; break; }
+            if (!hB) break;
+            hA = next(tA);
+            if (hA) idx_of(tA, jA);
+            if (!issue(tB, jB)) { ok = false; break; }
+        }
+        if (!ok) give_up();
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        tc::fence_proxy_async();
+        for (int k2 = it - (C::DEPTH - 1) < 0 ? 0 : it - (C::DEPTH - 1); k2 < it; ++k2) tc::mbar_arrive(&full[k2 % C::STAGES]);
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = FP8 ? tc::idesc_e4m3(128, C::NB) : tc::idesc_f16(128, C::NB, 1);
+            int it = 0;
+        Cursor cursor;
+            for (int u = blockIdx.x; u < n_sub; u += gridDim.x) {
+                const SubTile t = cursor.at(ml, u, per_item, C::QS);
+                if (t.nq <= 0) continue;
+                const int s = it % C::STAGES, a = it % C::ACC;
+                const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u, aph = (uint32_t)(it / C::ACC) & 1u;
+                if (!wait_or_abort(&full[s], ph, abort_flag)) { give_up(); break; }
+                if (!wait_or_abort(&tempty[a], aph ^ 1u, abort_flag)) { give_up(); break; }
+                tc::fence_after();
+                const uint32_t a0 = tc::smem_addr(ring + (size_t)s * C::STAGE);
+                const uint32_t b0 = a0 + C::HALVES * C::A_HALF;
+#pragma unroll
+                for (int ks = 0; ks < C::STEPS; ++ks) {
+                    const uint32_t ah = a0 + (uint32_t)(ks >> 2) * C::A_HALF + (uint32_t)(ks & 3) * 32u;
+                    const uint32_t bh = b0 + (uint32_t)(ks >> 2) * C::B_HALF + (uint32_t)(ks & 3) * 32u;
+                    if (FP8)
+                        tc::mma_f8f6f4(tmem + (uint32_t)(a * C::NB), tc::smem_desc_sw128(ah), tc::smem_desc_sw128(bh),
+                                       idesc, ks != 0);
+                    else
+                        tc::mma_f16(tmem + (uint32_t)(a * C::NB), tc::smem_desc_sw128(ah), tc::smem_desc_sw128(bh),
+                                    idesc, ks != 0);
+                }
+                tc::commit(&empty[s]);   // the stage may be refilled once these MMAs have read it
+                tc::commit(&tfull[a]);   // the accumulator is complete
+                ++it;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: group g takes the sub-tiles with it % kEpiGroups == g
+        const int g = (warp - kEpiWarp0) >> 2;
+        const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31
+        const int r = 32 * quarter + lane;          // candidate row of the A tile
+        const int c = r / K, k = r % K;             // its query column and slot
+        const int chunk = (32 * quarter / K) / 16;  // 16-column chunk holding this warp's columns
+        uint32_t rechecks = 0, matches = 0, swaps = 0;
+        // inputs of one sub-tile for this thread: all contiguous (hand-over written by the scan)
+        struct In {
+            uint32_t j, ny, nx;
+            float sy, sx;
+        };
+        auto fetch = [&](const SubTile& t) {
+            In v{kNoCand, 0u, 0u, 1.f, 1.f};
+            if (c < t.nq) {
+                const int64_t e = (t.row + c) * K + k;
+                v.j = ml.topk16[e];
+                v.ny = ml.hnorm[e];
+                v.nx = __ldg(t.inorm + t.q0 + c);
+                if (FP8) {
+                    v.sy = ml.hscale[e];
+                    v.sx = __ldg(t.iscale + t.q0 + c);
+                }
+            }
+            return v;
+        };
+        int it = 0;          // position in the CTA's sequence of non-empty sub-tiles
+        Cursor cursor;
+        int u = blockIdx.x - (int)gridDim.x;
+        // advances to this group's next sub-tile (every kEpiGroups-th of the sequence)
+        auto next = [&](SubTile& t, int& myit) -> bool {
+            for (u += gridDim.x; u < n_sub; u += gridDim.x) {
+                t = cursor.at(ml, u, per_item, C::QS);
+                if (t.nq <= 0) continue;
+                const int pos = it++;
+                if (pos % kEpiGroups == g) {
+                    myit = pos;
+                    return true;
+                }
+            }
+            return false;
+        };
+        auto process = [&](const SubTile& t, const In& v, int myit) -> bool {
+            const int a = myit % C::ACC;
+            const uint32_t aph = (uint32_t)(myit / C::ACC) & 1u;
+            const bool qv = c < t.nq;
+            const int qi = t.q0 + (qv ? c : 0);
+            const bool hv = v.j != kNoCand;
+            const int j = hv ? (int)v.j : 0;
+            if (!warp_wait(&tfull[a], aph, abort_flag)) return false;
+            tc::fence_after();
+            uint32_t vv[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(a * C::NB + 16 * chunk), vv);
+            tc::tmem_wait_ld();
+            float dot = 0.f;
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (q == (c & 15)) dot = __uint_as_float(vv[q]);
+            tc::fence_before();
+            tc::mbar_arrive(&tempty[a]);   // this thread's lane of the accumulator is read
+
+            uint64_t mine = ~0ull;
+            if (hv) {
+                if (!FP8) {
+                    const uint32_t d2 = (uint32_t)((float)v.nx + (float)v.ny - 2.f * dot);   // exact: integers < 2^24
+                    mine = ((uint64_t)d2 << 32) | (uint32_t)j;
+                } else {
+                    const float d2a = fmaxf((float)v.nx + (float)v.ny - 2.f * dot * v.sx * v.sy, 0.f);
+                    mine = ((uint64_t)__float_as_uint(d2a) << 32) | (uint32_t)j;
+                }
+            }
+            // q1, q2 over the K lanes of this query
+            uint64_t m1 = mine;
+#pragma unroll
+            for (int o = K / 2; o > 0; o >>= 1) m1 = min(m1, __shfl_xor_sync(0xFFFFFFFFu, m1, o));
+            uint64_t m2 = mine == m1 ? ~0ull : mine;
+#pragma unroll
+            for (int o = K / 2; o > 0; o >>= 1) m2 = min(m2, __shfl_xor_sync(0xFFFFFFFFu, m2, o));
+            int j1 = m1 != ~0ull ? (int)(m1 & 0xFFFFu) : -1;
+            int j2 = m2 != ~0ull ? (int)(m2 & 0xFFFFu) : -1;
+            uint32_t d1 = j1 >= 0 ? (uint32_t)(m1 >> 32) : kEmpty;
+            uint32_t d2 = j2 >= 0 ? (uint32_t)(m2 >> 32) : kEmpty;
+            if (FP8) {
+                // exact re-score of q1 and q2: half of the K lanes per row
+                constexpr int LPR = K / 2 > 0 ? K / 2 : 1;
+                constexpr int NBYTES = 128 / LPR;
+                const int half = k / LPR, part = k % LPR;
+                const int jr = half == 0 ? j1 : j2;
+                uint32_t e = 0;
+                if (qv && jr >= 0)
+                    e = exact_d2(t.idesc + (size_t)qi * kDim + part * NBYTES,
+                                 t.jdesc + (size_t)jr * kDim + part * NBYTES, NBYTES);
+#pragma unroll
+                for (int o = LPR / 2; o > 0; o >>= 1) e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+                const int gbase = lane & ~(K - 1);
+                const uint32_t e1 = __shfl_sync(0xFFFFFFFFu, e, gbase);
+                const uint32_t e2 = __shfl_sync(0xFFFFFFFFu, e, gbase + LPR);
+                d1 = j1 >= 0 ? e1 : kEmpty;
+                d2 = j2 >= 0 ? e2 : kEmpty;
+                if (j2 >= 0 && (d2 < d1 || (d2 == d1 && j2 < j1))) {   // the re-score reverses q1, q2
+                    const uint32_t td = d1; d1 = d2; d2 = td;
+                    const int tj = j1; j1 = j2; j2 = tj;
+                    if (k == 0 && qv) ++swaps;
+                }
+            }
+            if (k == 0 && qv) {
+                const int64_t row = t.row + c;
+                bool pass = false;
+                if (j2 >= 0) pass = ratio_pass(d1, d2, ml.ratio_num, ml.ratio_den, rechecks);
+                ml.out.best_j[row] = pass ? j1 : -1;
+                if (ml.out.d1sq) ml.out.d1sq[row] = d1;
+                if (ml.out.d2sq) ml.out.d2sq[row] = d2;
+                matches += pass ? 1u : 0u;
+            }
+            return true;
+        };
+        // ping-pong between two register sets: inputs prefetched one sub-tile ahead are
+        // never copied (a copy would wait for the load)
+        SubTile tA{}, tB{};
+        In vA{}, vB{};
+        int iA = 0, iB = 0;
+        bool hA = next(tA, iA), hB = false;
+        if (hA) vA = fetch(tA);
+        bool ok = true;
+        while (hA) {
+            hB = next(tB, iB);
+            if (hB) vB = fetch(tB);
+            if (!process(tA, vA, iA)) { ok = false; break; }
+            if (!hB) break;
+            hA = next(tA, iA);
+            if (hA) vA = fetch(tA);
+            if (!process(tB, vB, iB)) { ok = false; break; }
+        }
+        if (!ok) give_up();
+        if (ml.out.stats) {
+            if (rechecks) atomicAdd(&s_stats[0], rechecks);
+            if (matches) atomicAdd(&s_stats[1], matches);
+            if (swaps) atomicAdd(&s_stats[2], swaps);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (ml.out.stats && tid == 0) {
+        if (s_stats[0]) atomicAdd(&ml.out.stats[0], s_stats[0]);
+        if (s_stats[1]) atomicAdd(&ml.out.stats[1], s_stats[1]);
+        if (s_stats[2]) atomicAdd(&ml.out.stats[2], s_stats[2]);
+    }
+    if (warp == kMmaWarp) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, 256);
+    }
+}
+
+// One row per 8 threads (16 descriptor bytes each): BF16 or scaled-E4M3 copy.
+template <bool FP8>
+__global__ void __launch_bounds__(256) k_xcopy(HashLaunch h) {
+    const int64_t rows_per_block = 256 / 8;
+    for (int tile = blockIdx.x; tile < h.n_tiles; tile += gridDim.x) {
+        int lo = 0, hi = h.n_batch;  // image of this 64-row tile
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (h.tile_pref[mid] <= tile) lo = mid; else hi = mid;
+        }
+        const DevImage e = h.imgs[h.batch[lo]];
+        const int row0 = (tile - h.tile_pref[lo]) * kHashTile;
+        for (int rr = threadIdx.x >> 3; rr < kHashTile; rr += (int)rows_per_block) {
+            const int row = row0 + rr, seg = threadIdx.x & 7;
+            const bool ok = row < e.n;   // uniform over the 8 lanes of a row
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (ok) v = __ldg(reinterpret_cast<const uint4*>(e.desc + (size_t)row * kDim) + seg);
+            if (!FP8) {
+                if (ok) {
+                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                    uint32_t o[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const uint32_t b0 = (w[q >> 1] >> (16 * (q & 1))) & 0xFFu;
+                        const uint32_t b1 = (w[q >> 1] >> (16 * (q & 1) + 8)) & 0xFFu;
+                        // an integer 0..255 is exact in BF16: the upper half of its FP32 value
+                        o[q] = (__float_as_uint((float)b0) >> 16) | (__float_as_uint((float)b1) & 0xFFFF0000u);
+                    }
+                    uint4* dst = reinterpret_cast<uint4*>(static_cast<unsigned char*>(e.xq) + (size_t)row * 256 + seg * 32);
+                    dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+                    dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+                }
+            } else {
+                uint32_t mx = __vmaxu4(__vmaxu4(v.x, v.y), __vmaxu4(v.z, v.w));
+                mx = __vmaxu4(mx, mx >> 16);
+                mx = __vmaxu4(mx, mx >> 8);
+                mx &= 0xFFu;
+                mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 1));
+                mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 2));
+                mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 4));
+                if (ok) {
+                    const float scale = mx ? (float)mx / 448.f : 1.f;
+                    const float inv = 1.f / scale;
+                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                    uint32_t o[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float f0 = (float)(w[q] & 0xFFu) * inv, f1 = (float)((w[q] >> 8) & 0xFFu) * inv;
+                        const float f2 = (float)((w[q] >> 16) & 0xFFu) * inv, f3 = (float)(w[q] >> 24) * inv;
+                        const uint32_t lo2 = __nv_cvt_float2_to_fp8x2(make_float2(f0, f1), __NV_SATFINITE, __NV_E4M3);
+                        const uint32_t hi2 = __nv_cvt_float2_to_fp8x2(make_float2(f2, f3), __NV_SATFINITE, __NV_E4M3);
+                        o[q] = lo2 | (hi2 << 16);
+                    }
+                    *reinterpret_cast<uint4*>(static_cast<unsigned char*>(e.xq) + (size_t)row * 128 + seg * 16) =
+                        make_uint4(o[0], o[1], o[2], o[3]);
+                    if (seg == 0) e.xscale[row] = scale;
+                }
+            }
+        }
+    }
+}
+
+template <int K, bool FP8>
+cudaError_t launch_rr(const MatchLaunch& m, int sms, cudaStream_t s) {
+    using C = RR<K, FP8>;
+    cudaError_t e = cudaFuncSetAttribute(k_rerank_tc<K, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    const int n_sub = m.n_items * (m.S / C::QS);
+    const int grid = n_sub < sms ? (n_sub ? n_sub : 1) : sms;
+    k_rerank_tc<K, FP8><<<grid, kRrThreads, C::SMEM, s>>>(m);
+    return cudaGetLastError();
+}
+
+template <bool FP8>
+cudaError_t launch_rr_k(const MatchLaunch& m, int sms, cudaStream_t s) {
+    switch (m.K) {
+        case 2: return launch_rr<2, FP8>(m, sms, s);
+        case 4: return launch_rr<4, FP8>(m, sms, s);
+        case 8: return launch_rr<8, FP8>(m, sms, s);
+        case 16: return launch_rr<16, FP8>(m, sms, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_xcopy(const HashLaunch& h, cudaStream_t s) {
+    if (h.n_tiles == 0) return cudaSuccess;
+    const int grid = h.n_tiles < 4096 ? h.n_tiles : 4096;
+    if (h.rerank == CM_RERANK_FP8) k_xcopy<true><<<grid, 256, 0, s>>>(h);
+    else k_xcopy<false><<<grid, 256, 0, s>>>(h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rerank_tc(const MatchLaunch& m, int sm_count, cudaStream_t s) {
+    if (m.n_items == 0) return cudaSuccess;
+    return m.rerank == CM_RERANK_FP8 ? launch_rr_k<true>(m, sm_count, s) : launch_rr_k<false>(m, sm_count, s);
+}
+
+}  // namespace cm

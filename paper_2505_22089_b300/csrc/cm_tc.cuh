@@ -30,6 +30,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
+// Descriptor of a K-major operand tile in the 128-byte swizzle layout: rows of
+// 128 bytes, 8-row groups of 1024 bytes (SBO), the 16-byte chunk c of row r
+// stored at chunk position c ^ (r % 8).  The tile must start on a 1024-byte
+// boundary; a K step inside the 128-byte row is taken by adding its byte offset
+// to saddr.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;               // LBO: unused by swizzled K-major layouts
+    d |= (uint64_t)(1024 >> 4) << 32;     // SBO: next group of 8 rows
+    d |= (uint64_t)1 << 46;               // descriptor version of tcgen05
+    d |= (uint64_t)2 << 61;               // layout: 128-byte swizzle
+    return d;
+}
+
 // Instruction descriptor, kind::f16 with FP32 accumulate; ab = 0 F16, 1 BF16.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int ab) {
     return (1u << 4) | ((uint32_t)ab << 7) | ((uint32_t)ab << 10) | ((uint32_t)(N >> 3) << 17) |
@@ -71,6 +86,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int l
                      : "=r"(done) : "r"(smem_addr(mbar)), "r"(parity));
     }
     return done != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(mbar)) : "memory");
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, int ncols) {  // one full warp
