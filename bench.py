@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--rerank", default="bf16", choices=["fp32", "int", "bf16", "fp8"], help="headline form")
     ap.add_argument("--forms", default="all", choices=["all", "one"], help="also time the other rerank forms")
     ap.add_argument("--K", type=int, default=8)
+    ap.add_argument("--tune-pairs", type=int, default=120,
+                    help="pairs of the first block row the autotuner times (0: no tuning)")
     ap.add_argument("--verify-workers", type=int, default=-1,
                     help="CPU threads of the overlapped RANSAC run (-1: all host cores, 0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -180,10 +182,16 @@ def device_forms(args, wl, desc_dev, rows, stream, dev, world, forms):
     headline = forms[0]
     for form in forms:
         p = cm.Params.make(rerank=form, algo=args.algo, projection=args.projection, K=args.K)
+        sample = pairs[rows[0][:args.tune_pairs]] if args.tune_pairs > 0 else None
         arena = (cm.index_bytes(p, wl.n_desc, inplace=True) + cm.PLAN_HEADROOM +
                  sum(cm.pairs_plan_bytes(p, wl.n_desc, pairs[r]) for r in rows))
+        if sample is not None:   # the tuner's plan and decision scratch
+            arena += cm.pairs_plan_bytes(p, wl.n_desc, sample) + 4 * int(wl.n_desc[sample[:, 0]].sum()) + (1 << 20)
+        tuned = None
         with torch.cuda.stream(stream):
             index = cm.Index.build(p, wl.n_desc, desc_dev, stream=stream, arena_bytes=arena)
+            if sample is not None and args.algo == "auto":
+                tuned = index.autotune(sample, stream=stream)   # work-item size and thread mapping
             plans = [cm.MatchPlan(index, pairs[r], stream=stream) for r in rows]
             outs = [pl.alloc_out(d12=False) for pl in plans]
             comps = [cm.compact_out(pl) for pl in plans]
@@ -206,7 +214,7 @@ def device_forms(args, wl, desc_dev, rows, stream, dev, world, forms):
         ms = _sync_ms(start.elapsed_time(stop) / args.steps, world, dev)
         index.check(stream)
         r = {"ms_per_step": ms, "value": len(pairs) * world / (ms / 1e3), "graph_kernels": seq.kernels,
-             "clocks": clk.summary()}
+             "clocks": clk.summary(), "tuned": tuned}
         best = torch.cat([o["best_j"][:pl.rows] for pl, o in zip(plans, outs)])
         n_match = int(sum(int(c["total"].item()) for c in comps))
         r["matches"] = n_match
@@ -360,7 +368,7 @@ def run_ours(args, rank, world, local):
     for f, r in fr.items():
         forms_out[f] = {k: (round(v, 6) if isinstance(v, float) else v) for k, v in r.items()
                         if k in ("value", "ms_per_step", "matches", "decision_agreement_vs_fp32",
-                                 "match_jaccard_vs_fp32", "graph_kernels")}
+                                 "match_jaccard_vs_fp32", "graph_kernels", "tuned")}
     res = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

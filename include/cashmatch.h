@@ -226,7 +226,8 @@ void cm_index_destroy(cm_index* ix);
  * 10 K bytes per row). */
 cm_status cm_plan_bytes(const cm_params* p, int64_t n_pairs, int64_t rows, uint64_t* bytes);
 /* Plans a batch of pairs (host list): validates ids and residency and uploads
- * the work table into the index arena (async, on stream).  A plan can be run
+ * the work table into the index arena (async, on stream).  The plan keeps the
+ * index's parameters of that moment (K, work-item size, thread mapping).  A plan can be run
  * many times and captured in a CUDA graph; it must not outlive the residency
  * of its images. */
 cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, cm_stream stream,
@@ -368,6 +369,28 @@ typedef struct cm_affine_verifier {
 } cm_affine_verifier;
 int32_t cm_affine_verify_cb(void* user, int32_t row, int64_t pair_id, const cm_pair* pair, int64_t n_matches,
                             const uint32_t* matches);
+
+/* ---- autotuning of the match launch -------------------------------------- */
+typedef struct cm_tune_result {
+    int32_t query_tile;  /* chosen queries per work item */
+    int32_t algo;        /* chosen cm_algo (TILE or WARP) */
+    int32_t K;           /* chosen K (the index's K unless K candidates were given) */
+    int32_t trials;      /* configurations timed */
+    float ms;            /* mean time of one match launch over the sample with the choice */
+    float agreement;     /* share of the sample's queries whose decision equals the largest K's */
+} cm_tune_result;
+/* Times the match launch on a sample of resident pairs under each work-item
+ * size (256 .. 4096 queries, where the tile kernel's shared memory fits) and
+ * thread mapping (tile; warp-per-query for the CUDA-core reranks), checks that
+ * all of them decide every query identically (CM_ERR_STATE otherwise), and
+ * keeps the fastest.  With n_K > 0 it then times each K of K_candidates and
+ * keeps the fastest K whose decisions agree with the largest candidate's on at
+ * least min_agreement of the sample's queries (K changes the method's result:
+ * Sec. 2.3.1 step (3)).  The choice is written to *out and becomes the index's
+ * parameters for plans made afterwards; plans that exist keep theirs.
+ * Synchronous (waits for stream); scratch comes from the index arena. */
+cm_status cm_autotune(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, const int32_t* K_candidates, int32_t n_K,
+                      float min_agreement, cm_stream stream, cm_tune_result* out);
 
 /* ---- matching without any device allocation ------------------------------ */
 /* The paper has no counterpart: this entry point serves callers that may not

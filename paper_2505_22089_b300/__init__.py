@@ -48,7 +48,7 @@ EXPORTS = [
     "cm_index_image_view", "cm_index_destroy", "cm_match_plan_create", "cm_match_plan_rows", "cm_match_plan_run",
     "cm_match_plan_compact", "cm_match_plan_destroy", "cm_match_pairs", "cm_sequence_create", "cm_sequence_launch",
     "cm_sequence_kernels", "cm_sequence_destroy", "cm_schedule_arena_bytes", "cm_pipeline_workspace_bytes", "cm_run_schedule",
-    "cm_verify_affine", "cm_affine_verify_cb", "cm_match_pair_noalloc",
+    "cm_verify_affine", "cm_affine_verify_cb", "cm_autotune", "cm_match_pair_noalloc",
 ]
 
 
@@ -104,6 +104,11 @@ class AffineVerifier(ctypes.Structure):
 
 VERIFY_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                              ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32))
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("query_tile", ctypes.c_int32), ("algo", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("trials", ctypes.c_int32), ("ms", ctypes.c_float), ("agreement", ctypes.c_float)]
 
 
 class ScheduleRow(ctypes.Structure):
@@ -167,6 +172,7 @@ def lib():
                                       ctypes.POINTER(PipelineStats)]),
             "cm_verify_affine": (i32, [vp, vp, i64, vp, ctypes.c_float, i32, u64, vp, vp, ctypes.POINTER(i64)]),
             "cm_affine_verify_cb": (i32, [vp, i32, i64, vp, i64, vp]),
+            "cm_autotune": (i32, [vp, vp, i64, vp, i32, ctypes.c_float, vp, ctypes.POINTER(TuneResult)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -332,7 +338,7 @@ class Index:
         device arena; otherwise one of `arena_bytes` (default: room for every
         image) is allocated."""
         import torch
-        self.p = p
+        self.p = Params.from_buffer_copy(p)   # the index's own copy (cm_autotune may change it)
         self.n_desc = np.ascontiguousarray(n_desc, dtype=np.int32)
         if arena is None:
             if arena_bytes is None:
@@ -353,7 +359,7 @@ class Index:
         uint8 tensor (used in place unless mem says otherwise) or a host array/tensor."""
         import torch
         self = cls.__new__(cls)
-        self.p = p
+        self.p = Params.from_buffer_copy(p)
         self.n_desc = np.ascontiguousarray(n_desc, dtype=np.int32)
         on_dev = isinstance(desc, torch.Tensor) and desc.is_cuda
         if mem is None:
@@ -402,6 +408,17 @@ class Index:
     def check(self, stream=None):
         """Raises CMError(CM_ERR_TIMEOUT) if a bounded device wait gave up."""
         check(lib().cm_index_check(self.h, _stream(stream)))
+
+    def autotune(self, pairs, Ks=None, min_agreement: float = 0.999, stream=None) -> dict:
+        """cm_autotune on a sample of resident pairs; the choice applies to plans made afterwards."""
+        pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        ks = np.ascontiguousarray(Ks if Ks is not None else [], dtype=np.int32)
+        r = TuneResult()
+        check(lib().cm_autotune(self.h, pr.ctypes.data, len(pr), ks.ctypes.data if len(ks) else None, len(ks),
+                                float(min_agreement), _stream(stream), ctypes.byref(r)))
+        self.p.query_tile, self.p.algo, self.p.K = r.query_tile, r.algo, r.K
+        return {"query_tile": r.query_tile, "algo": {v: k for k, v in ALGO.items()}[r.algo], "K": r.K,
+                "trials": r.trials, "ms": r.ms, "agreement": r.agreement}
 
     def image_view(self, image: int) -> dict:
         """Copies of a resident image's keys, codes and bucket tables (host numpy)."""
@@ -453,6 +470,7 @@ class MatchPlan:
         check(lib().cm_match_plan_create(index.h, self.pairs.ctypes.data, self.pairs.shape[0], _stream(stream),
                                          ctypes.byref(self.h)))
         self.rows = int(lib().cm_match_plan_rows(self.h))
+        self.K = int(index.p.K)   # the plan keeps the index's parameters of this moment
         index._plans.append(weakref.ref(self))
         nd = index.n_desc[self.pairs[:, 0]].astype(np.int64) if len(self.pairs) else np.zeros(0, np.int64)
         self.row_off = np.concatenate([[0], np.cumsum(nd)]).astype(np.int64)
@@ -465,7 +483,7 @@ class MatchPlan:
             out["d1sq"] = torch.empty(n, dtype=torch.int32, device="cuda")
             out["d2sq"] = torch.empty(n, dtype=torch.int32, device="cuda")
         if topk:
-            out["topk"] = torch.empty(n * self.index.p.K, dtype=torch.int32, device="cuda")
+            out["topk"] = torch.empty(n * self.K, dtype=torch.int32, device="cuda")
         if stats:
             out["stats"] = torch.zeros(4, dtype=torch.int32, device="cuda")
         return out

@@ -530,6 +530,8 @@ extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, in
         return fail(CM_ERR_BUDGET, "plan: arena full (%llu bytes for the pair table)", (unsigned long long)bytes);
     }
     pl->ix = ix;
+    pl->p = ix->p;
+    pl->S = S;
     ix->plans.insert(pl);
     pl->n_pairs = n_pairs;
     pl->rows = rows;
@@ -563,26 +565,27 @@ extern "C" cm_status cm_match_plan_run(cm_match_plan* pl, const cm_match_out* ou
     m.pairs = reinterpret_cast<const DevPair*>(ix->arena + pl->table_at);
     m.n_pairs = (int32_t)pl->n_pairs;
     m.n_items = pl->n_items;
-    m.S = query_tile(&ix->p);
-    m.L = ix->p.L;
-    m.m = ix->p.m;
-    m.K = ix->p.K;
-    m.ratio_num = ix->p.ratio_num;
-    m.ratio_den = ix->p.ratio_den;
-    m.rerank = ix->p.rerank;
+    const cm_params& pp = pl->p;
+    m.S = pl->S;
+    m.L = pp.L;
+    m.m = pp.m;
+    m.K = pp.K;
+    m.ratio_num = pp.ratio_num;
+    m.ratio_den = pp.ratio_den;
+    m.rerank = pp.rerank;
     m.counter = counter;
     m.out = *out;
-    m.algo = ix->p.algo == CM_ALGO_WARP ? CM_ALGO_WARP : CM_ALGO_TILE;   // auto: tile, if its tile fits
+    m.algo = pp.algo == CM_ALGO_WARP ? CM_ALGO_WARP : CM_ALGO_TILE;   // auto: tile, if its tile fits
     if (m.algo == CM_ALGO_TILE && match_smem_bytes(m.S, m.K) > kMatchSmemLimit) m.algo = CM_ALGO_WARP;
     m.err = ix->at<int>(ix->fx.err);
-    if (tc_rerank(&ix->p)) {
+    if (tc_rerank(&pp)) {
         // scan (top-K lists to the plan's hand-over area), then the tensor-core rerank
         m.algo = CM_ALGO_TILE;
-        const HandOver ho = hand_over(&ix->p, pl->rows);
+        const HandOver ho = hand_over(&pp, pl->rows);
         uint8_t* base = ix->arena + counter_at + kAlign;
         m.topk16 = reinterpret_cast<uint16_t*>(base + ho.idx);
         m.hnorm = reinterpret_cast<uint32_t*>(base + ho.norm);
-        m.hscale = ix->p.rerank == CM_RERANK_FP8 ? reinterpret_cast<float*>(base + ho.scale) : nullptr;
+        m.hscale = pp.rerank == CM_RERANK_FP8 ? reinterpret_cast<float*>(base + ho.scale) : nullptr;
         CM_CUDA(launch_match(m, ix->sms, s));
         CM_CUDA(launch_rerank_tc(m, ix->sms, s));
         return CM_OK;

@@ -263,6 +263,8 @@ inline uint64_t plan_bytes(const cm_params* p, int64_t n_pairs, int64_t rows) {
 
 struct cm_match_plan {
     cm_index* ix = nullptr;
+    cm_params p{};           // the index's parameters when the plan was made (K, query tile, algo)
+    int32_t S = 0;           // queries per work item
     uint64_t table_at = 0;   // arena offset: [n_pairs] DevPair, the work counter, the top-K hand-over
     int64_t n_pairs = 0;
     int64_t rows = 0;

@@ -25,7 +25,7 @@ def gpu_match(index: cm.Index, pairs, topk: bool = True):
     for k in ("d1sq", "d2sq"):
         res[k] = res[k].view(np.uint32)
     if topk:
-        res["topk"] = res["topk"][: plan.rows * index.p.K].reshape(-1, index.p.K)
+        res["topk"] = res["topk"][: plan.rows * plan.K].reshape(-1, plan.K)
     return plan, res
 
 

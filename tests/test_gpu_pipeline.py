@@ -196,3 +196,32 @@ def test_pipeline_callback_abort_and_recovery():
     assert e.value.status == cm.CM_ERR_STATE
     stats, _ = cm.run_schedule(index, sched, host, verify=None, workers=2)
     assert stats["pairs"] == len(wl.pairs)
+
+
+@pytest.mark.parametrize("rerank", ["int", "bf16"])
+def test_autotune_keeps_the_decisions(rerank):
+    wl = synth.strip30(n_images=8, n=3000)
+    desc = wl.generate()
+    p = cm.Params.make(rerank=rerank)
+    index = _index(wl, p, desc)
+    _, before = _direct(index, wl.pairs)
+    r = index.autotune(wl.pairs[:12])
+    assert r["trials"] >= 3 and r["query_tile"] % 64 == 0 and r["K"] == 8
+    if rerank == "bf16":
+        assert r["algo"] == "tile"
+    _, after = _direct(index, wl.pairs)   # a plan made after tuning uses the chosen tile and mapping
+    assert np.array_equal(before, after)
+
+
+def test_autotune_chooses_K_under_an_agreement_floor():
+    wl = synth.strip30(n_images=8, n=3000)
+    desc = wl.generate()
+    index = _index(wl, cm.Params.make(rerank="int"), desc)
+    r = index.autotune(wl.pairs[:12], Ks=[4, 8, 16], min_agreement=0.99)
+    assert r["K"] in (4, 8, 16) and r["agreement"] >= 0.99
+    assert index.p.K == r["K"]
+    plan, best = _direct(index, wl.pairs[:12])
+    assert plan.K == r["K"]
+    # a floor of 1.0 leaves only K values whose decisions equal the largest K's
+    r2 = index.autotune(wl.pairs[:12], Ks=[4, 8, 16], min_agreement=1.0)
+    assert r2["agreement"] == 1.0
