@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--verify-workers", type=int, default=-1,
                     help="CPU threads of the overlapped RANSAC run (-1: all host cores, 0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--algo", default="auto", choices=["auto", "tile", "warp"], help="match kernel thread mapping")
+    ap.add_argument("--algo", default="auto", choices=["auto", "tile", "warp", "tc"], help="match kernel thread mapping")
     ap.add_argument("--projection", default="tc", choices=["tc", "ffma"], help="hash projection: tensor cores or FP32 FFMA")
     ap.add_argument("--block-images", type=int, default=400, help="Size_blk: images per schedule chunk")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="HBM budget of the MBR schedule")

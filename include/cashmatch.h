@@ -59,7 +59,10 @@ typedef enum {
     CM_ALGO_AUTO = 0,    /* library choice */
     CM_ALGO_TILE = 1,    /* one lane per query; a CTA keeps a tile of queries' top-K in shared memory and
                             sweeps the tables with the queries sorted by bucket */
-    CM_ALGO_WARP = 2     /* one warp per query; top-K kept across the warp with ballots and shuffles */
+    CM_ALGO_WARP = 2,    /* one warp per query; top-K kept across the warp with ballots and shuffles */
+    CM_ALGO_TC = 3       /* a CTA per pair; each bucket's queries x database points block of Hamming
+                            distances on the tensor cores (code bits as E4M3 +-1: dot = 128 - 2 h, exact);
+                            then a separate rerank launch.  K in {4, 8, 16} */
 } cm_algo;
 
 /* How the projections onto the hyperplanes are computed (both decide the same
@@ -219,12 +222,14 @@ cm_status cm_index_image_view(const cm_index* ix, int32_t image, const void** ke
 void cm_index_destroy(cm_index* ix);
 
 /* ---- matching (Sec. 2.3.1 steps (1)-(4), one launch per block) ------------ */
-/* Arena bytes a plan of n_pairs pairs and `rows` query rows takes from its
- * index: the pair table and work counter, and for the BF16 / FP8 reranks the
- * top-K hand-over between the scan and the tensor-core rerank (index and
- * squared norm of each kept candidate, 6 K bytes per row; FP8 adds its scale,
- * 10 K bytes per row). */
-cm_status cm_plan_bytes(const cm_params* p, int64_t n_pairs, int64_t rows, uint64_t* bytes);
+/* Arena bytes a plan of n_pairs pairs and `rows` query rows (the largest
+ * query image having max_query_rows) takes from its index: the pair table and
+ * work counter; for the BF16 / FP8 reranks and the CM_ALGO_TC scan the top-K
+ * hand-over between the scan and the rerank launch (index and squared norm of
+ * each kept candidate, 6 K bytes per row; FP8 adds its scale, 10 K); for
+ * CM_ALGO_TC also per-table top-K lists of 160 concurrent pairs
+ * (160 * max_query_rows * L * K * 4 bytes). */
+cm_status cm_plan_bytes(const cm_params* p, int64_t n_pairs, int64_t rows, int32_t max_query_rows, uint64_t* bytes);
 /* Plans a batch of pairs (host list): validates ids and residency and uploads
  * the work table into the index arena (async, on stream).  The plan keeps the
  * index's parameters of that moment (K, work-item size, thread mapping).  A plan can be run

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libcashmatch.so")
 
 CM_OK, CM_ERR_INVALID, CM_ERR_BUDGET, CM_ERR_CUDA, CM_ERR_TIMEOUT, CM_ERR_NOMEM, CM_ERR_STATE = range(7)
 RERANK = {"fp32": 0, "bf16": 1, "fp8": 2, "int": 3}
-ALGO = {"auto": 0, "tile": 1, "warp": 2}
+ALGO = {"auto": 0, "tile": 1, "warp": 2, "tc": 3}
 PROJ = {"tc": 0, "ffma": 1}
 MEM_HOST, MEM_DEVICE, MEM_DEVICE_INPLACE = 0, 1, 2
 # Arena headroom the binding adds to cm_index_bytes for match-plan tables
@@ -34,9 +34,12 @@ TC_PLAN_ROWS_FACTOR = 16
 def default_headroom(p, n_desc) -> int:
     """Arena bytes the binding adds to cm_index_bytes by default."""
     extra = 0
-    if p.rerank in (RERANK["bf16"], RERANK["fp8"]):
+    nd = np.asarray(n_desc, dtype=np.int64)
+    if p.rerank in (RERANK["bf16"], RERANK["fp8"]) or p.algo == ALGO["tc"]:
         per_row = p.K * (10 if p.rerank == RERANK["fp8"] else 6)
-        extra = TC_PLAN_ROWS_FACTOR * int(np.asarray(n_desc, dtype=np.int64).sum()) * per_row
+        extra = TC_PLAN_ROWS_FACTOR * int(nd.sum()) * per_row
+    if p.algo == ALGO["tc"]:   # per-table lists of the tensor-core scan, for a few plans
+        extra += 4 * 160 * int(nd.max() if len(nd) else 0) * p.L * p.K * 4
     return PLAN_HEADROOM + extra
 
 # Every symbol include/cashmatch.h declares (checked by the CPU tests).
@@ -166,7 +169,7 @@ def lib():
             "cm_sequence_kernels": (i32, [vp]),
             "cm_sequence_destroy": (None, [vp]),
             "cm_schedule_arena_bytes": (i32, [vp, P, i32, vp, vp, i64, ctypes.POINTER(u64)]),
-            "cm_plan_bytes": (i32, [P, i64, i64, ctypes.POINTER(u64)]),
+            "cm_plan_bytes": (i32, [P, i64, i64, i32, ctypes.POINTER(u64)]),
             "cm_pipeline_workspace_bytes": (i32, [vp, vp, vp, i64, ctypes.POINTER(u64)]),
             "cm_run_schedule": (i32, [vp, vp, vp, i64, vp, vp, u64, vp, vp, i32, vp,
                                       ctypes.POINTER(PipelineStats)]),
@@ -276,18 +279,20 @@ def schedule_arena_bytes(sched: Schedule, p: Params, n_desc) -> int:
     return b.value
 
 
-def plan_bytes(p: Params, n_pairs: int, rows: int) -> int:
+def plan_bytes(p: Params, n_pairs: int, rows: int, max_query_rows: int) -> int:
     """cm_plan_bytes: arena bytes a plan takes from its index."""
     b = ctypes.c_uint64()
-    check(lib().cm_plan_bytes(ctypes.byref(p), int(n_pairs), int(rows), ctypes.byref(b)))
+    check(lib().cm_plan_bytes(ctypes.byref(p), int(n_pairs), int(rows), int(max_query_rows), ctypes.byref(b)))
     return b.value
 
 
 def pairs_plan_bytes(p: Params, n_desc, pairs) -> int:
     """Arena bytes of one plan over `pairs` (query rows = sum of N_i)."""
     pr = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
-    rows = int(np.asarray(n_desc, dtype=np.int64)[pr[:, 0]].sum()) if len(pr) else 0
-    return plan_bytes(p, len(pr), rows)
+    nd = np.asarray(n_desc, dtype=np.int64)
+    rows = int(nd[pr[:, 0]].sum()) if len(pr) else 0
+    max_ni = int(nd[pr[:, 0]].max()) if len(pr) else 0
+    return plan_bytes(p, len(pr), rows, max_ni)
 
 
 def verify_affine(kp_i, kp_j, matches, thresh_px: float = 3.0, max_iters: int = 1000, seed: int = 1):

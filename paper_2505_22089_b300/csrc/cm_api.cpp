@@ -71,7 +71,9 @@ extern "C" cm_status cm_params_check(const cm_params* p) {
     if (p->query_tile != 0 && (p->query_tile < 64 || p->query_tile > 8192 || p->query_tile % 64))
         return fail(CM_ERR_INVALID, "params: query_tile=%d must be 0 or a multiple of 64 in 64..8192",
                     p->query_tile);
-    if (p->algo < CM_ALGO_AUTO || p->algo > CM_ALGO_WARP) return fail(CM_ERR_INVALID, "params: algo %d", p->algo);
+    if (p->algo < CM_ALGO_AUTO || p->algo > CM_ALGO_TC) return fail(CM_ERR_INVALID, "params: algo %d", p->algo);
+    if (p->algo == CM_ALGO_TC && p->K < 4)
+        return fail(CM_ERR_INVALID, "params: the tensor-core Hamming scan needs K in {4, 8, 16}");
     if (p->projection != CM_PROJ_TC && p->projection != CM_PROJ_FFMA)
         return fail(CM_ERR_INVALID, "params: projection %d", p->projection);
     const int S = query_tile(p);
@@ -131,11 +133,13 @@ extern "C" cm_status cm_image_bytes(const cm_params* p, int32_t n_desc, uint64_t
     return CM_OK;
 }
 
-extern "C" cm_status cm_plan_bytes(const cm_params* p, int64_t n_pairs, int64_t rows, uint64_t* bytes) {
+extern "C" cm_status cm_plan_bytes(const cm_params* p, int64_t n_pairs, int64_t rows, int32_t max_query_rows,
+                                   uint64_t* bytes) {
     cm_status st = cm_params_check(p);
     if (st != CM_OK) return st;
-    if (!bytes || n_pairs < 0 || rows < 0) return fail(CM_ERR_INVALID, "cm_plan_bytes: bad argument");
-    *bytes = plan_bytes(p, n_pairs, rows);
+    if (!bytes || n_pairs < 0 || rows < 0 || max_query_rows < 0 || max_query_rows > 65535)
+        return fail(CM_ERR_INVALID, "cm_plan_bytes: bad argument");
+    *bytes = plan_bytes(p, n_pairs, rows, max_query_rows);
     return CM_OK;
 }
 
@@ -504,6 +508,7 @@ extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, in
     const int S = query_tile(&ix->p);
     std::vector<DevPair> tab((size_t)n_pairs);
     int64_t rows = 0, items = 0;
+    int32_t max_ni = 0;
     for (int64_t k = 0; k < n_pairs; ++k) {
         const int i = pairs[k].i, j = pairs[k].j;
         if (i < 0 || j < 0 || i >= ix->n_images || j >= ix->n_images)
@@ -520,11 +525,12 @@ extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, in
         d.nitems = (ix->n_desc[i] + S - 1) / S;
         rows += ix->n_desc[i];
         items += d.nitems;
+        max_ni = std::max(max_ni, ix->n_desc[i]);
     }
     if (items > INT32_MAX / 2) return fail(CM_ERR_INVALID, "plan: too many work items");
     cm_match_plan* pl = new (std::nothrow) cm_match_plan();
     if (!pl) return fail(CM_ERR_NOMEM, "plan: host allocation");
-    const uint64_t bytes = plan_bytes(&ix->p, n_pairs, rows);
+    const uint64_t bytes = plan_bytes(&ix->p, n_pairs, rows, max_ni);
     if (!ix->alloc.alloc(bytes, &pl->table_at)) {
         delete pl;
         return fail(CM_ERR_BUDGET, "plan: arena full (%llu bytes for the pair table)", (unsigned long long)bytes);
@@ -536,6 +542,7 @@ extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, in
     pl->n_pairs = n_pairs;
     pl->rows = rows;
     pl->n_items = (int32_t)items;
+    pl->max_ni = max_ni;
     if (n_pairs) {
         cm_status st = upload_table(ix, pl->table_at, tab.data(), tab.size() * sizeof(DevPair),
                                     reinterpret_cast<cudaStream_t>(stream));
@@ -578,16 +585,23 @@ extern "C" cm_status cm_match_plan_run(cm_match_plan* pl, const cm_match_out* ou
     m.algo = pp.algo == CM_ALGO_WARP ? CM_ALGO_WARP : CM_ALGO_TILE;   // auto: tile, if its tile fits
     if (m.algo == CM_ALGO_TILE && match_smem_bytes(m.S, m.K) > kMatchSmemLimit) m.algo = CM_ALGO_WARP;
     m.err = ix->at<int>(ix->fx.err);
-    if (tc_rerank(&pp)) {
-        // scan (top-K lists to the plan's hand-over area), then the tensor-core rerank
-        m.algo = CM_ALGO_TILE;
-        const HandOver ho = hand_over(&pp, pl->rows);
+    if (needs_hand_over(&pp)) {
+        // a scan leaves each query's top-K in the plan's hand-over area, then a rerank launch
+        const HandOver ho = hand_over(&pp, pl->rows, pl->max_ni);
         uint8_t* base = ix->arena + counter_at + kAlign;
         m.topk16 = reinterpret_cast<uint16_t*>(base + ho.idx);
         m.hnorm = reinterpret_cast<uint32_t*>(base + ho.norm);
         m.hscale = pp.rerank == CM_RERANK_FP8 ? reinterpret_cast<float*>(base + ho.scale) : nullptr;
-        CM_CUDA(launch_match(m, ix->sms, s));
-        CM_CUDA(launch_rerank_tc(m, ix->sms, s));
+        if (pp.algo == CM_ALGO_TC) {
+            m.algo = CM_ALGO_TC;
+            m.lists = reinterpret_cast<uint32_t*>(base + ho.lists);
+            m.max_ni = pl->max_ni;
+            CM_CUDA(launch_scan_tc(m, std::min(ix->sms, kMaxScanCtas), s));
+        } else {
+            m.algo = CM_ALGO_TILE;
+            CM_CUDA(launch_match(m, ix->sms, s));
+        }
+        CM_CUDA(tc_rerank(&pp) ? launch_rerank_tc(m, ix->sms, s) : launch_rerank_cc(m, ix->sms, s));
         return CM_OK;
     }
     CM_CUDA(m.algo == CM_ALGO_TILE ? launch_match(m, ix->sms, s) : launch_match_wq(m, ix->sms, s));

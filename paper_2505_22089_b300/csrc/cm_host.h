@@ -243,22 +243,29 @@ struct cm_index {
 // Arena bytes of a plan: its pair table, the work counter and, for the
 // tensor-core reranks, the [rows][K] top-K hand-over from scan to rerank
 // (index, squared norm and, for FP8, scale of every kept candidate).
-// Hand-over areas after the counter: indices u16, norms u32, scales f32 (FP8), [rows][K] each.
+// Hand-over areas after the counter: indices u16, norms u32, scales f32 (FP8), [rows][K] each,
+// for the tensor-core reranks and for the tensor-core Hamming scan; the scan adds per-CTA
+// scratch for per-table top-K lists: [kMaxScanCtas][max query rows][L][K] u32.
+constexpr int kMaxScanCtas = 160;   // >= the SM count; the scan's grid is capped to it
 struct HandOver {
-    uint64_t idx, norm, scale, total;
+    uint64_t idx, norm, scale, lists, total;
 };
-inline HandOver hand_over(const cm_params* p, int64_t rows) {
+inline bool needs_hand_over(const cm_params* p) { return tc_rerank(p) || p->algo == CM_ALGO_TC; }
+inline HandOver hand_over(const cm_params* p, int64_t rows, int32_t max_ni) {
     HandOver h{};
-    if (!tc_rerank(p)) return h;
+    if (!needs_hand_over(p)) return h;
     const uint64_t e = (uint64_t)rows * (uint64_t)p->K;
     h.idx = 0;
     h.norm = align_up(e * 2);
     h.scale = h.norm + align_up(e * 4);
-    h.total = h.scale + (p->rerank == CM_RERANK_FP8 ? align_up(e * 4) : 0);
+    h.lists = h.scale + (p->rerank == CM_RERANK_FP8 ? align_up(e * 4) : 0);
+    h.total = h.lists;
+    if (p->algo == CM_ALGO_TC)
+        h.total += align_up((uint64_t)kMaxScanCtas * (uint64_t)max_ni * (uint64_t)p->L * (uint64_t)p->K * 4);
     return h;
 }
-inline uint64_t plan_bytes(const cm_params* p, int64_t n_pairs, int64_t rows) {
-    return align_up((uint64_t)n_pairs * sizeof(DevPair)) + kAlign + hand_over(p, rows).total;
+inline uint64_t plan_bytes(const cm_params* p, int64_t n_pairs, int64_t rows, int32_t max_ni) {
+    return align_up((uint64_t)n_pairs * sizeof(DevPair)) + kAlign + hand_over(p, rows, max_ni).total;
 }
 
 struct cm_match_plan {
@@ -269,6 +276,7 @@ struct cm_match_plan {
     int64_t n_pairs = 0;
     int64_t rows = 0;
     int32_t n_items = 0;
+    int32_t max_ni = 0;      // largest query image of the plan
 };
 
 

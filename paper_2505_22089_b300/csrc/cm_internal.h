@@ -78,6 +78,8 @@ struct MatchLaunch {
     uint16_t* topk16;          // database indices (0xFFFF empty)
     uint32_t* hnorm;           // their squared norms
     float* hscale;             // their FP8 row scales (FP8 form)
+    uint32_t* lists;           // tensor-core Hamming scan: per-CTA [max_ni][L][K] per-table top-K keys
+    int32_t max_ni;            // largest query image of the launch
     cm_match_out out;
 };
 
@@ -102,5 +104,8 @@ int hash_npg(int P_pad);
 // the rerank of a plan's top-K lists.
 cudaError_t launch_xcopy(const HashLaunch& h, cudaStream_t s);
 cudaError_t launch_rerank_tc(const MatchLaunch& m, int sm_count, cudaStream_t s);
+// Tensor-core Hamming scan (cm_scan_tc.cu) and the CUDA-core rerank of a hand-over (cm_rerank_cc.cu).
+cudaError_t launch_scan_tc(const MatchLaunch& m, int grid, cudaStream_t s);
+cudaError_t launch_rerank_cc(const MatchLaunch& m, int sm_count, cudaStream_t s);
 
 }  // namespace cm

@@ -430,13 +430,15 @@ extern "C" cm_status cm_schedule_arena_bytes(const cm_schedule* s, const cm_para
         }
         peak = std::max(peak, cur);
         int64_t rows = 0;
+        int32_t max_ni = 0;
         for (int64_t k = 0; k < row.n_pairs; ++k) {
             const int64_t id = row.pairs[k];
             if (id < 0 || id >= n_pairs || pairs[id].i < 0 || pairs[id].i >= n_images)
                 return fail(CM_ERR_INVALID, "cm_schedule_arena_bytes: pair %lld", (long long)id);
             rows += n_desc[pairs[id].i];
+            max_ni = std::max(max_ni, n_desc[pairs[id].i]);
         }
-        plan = std::max(plan, plan_bytes(p, row.n_pairs, rows));
+        plan = std::max(plan, plan_bytes(p, row.n_pairs, rows, max_ni));
         for (int k = 0; k < row.n_free; ++k) {
             const int i = row.free_ids[k];
             if (i >= 0 && i < n_images && res[i]) {
@@ -539,7 +541,7 @@ extern "C" cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const c
     for (int w = 0; w < n_workers; ++w) threads.emplace_back([&P] { P.worker(); });
     // hashing: (bias +) projection + buckets (+ the rerank row copies); matching: scan (+ tensor-core rerank)
     const int hash_kernels = (ix->p.projection == CM_PROJ_TC ? 3 : 2) + (tc_rerank(&ix->p) ? 1 : 0);
-    const int match_kernels = tc_rerank(&ix->p) ? 2 : 1;
+    const int match_kernels = needs_hand_over(&ix->p) ? 2 : 1;
 
     for (int32_t r = 0; r < R; ++r) {
         cm_schedule_row row{};

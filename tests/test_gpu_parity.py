@@ -50,12 +50,12 @@ def test_pair2k_query_tiles_with_ragged_tail(tile, algo):
     _run(synth.pair2k(), cm.Params.make(query_tile=tile, algo=algo))
 
 
-@pytest.mark.parametrize("algo", ["tile", "warp"])
+@pytest.mark.parametrize("algo", ["tile", "warp", "tc"])
 def test_pair2k_integer_rerank(algo):
     _run(synth.pair2k(), cm.Params.make(rerank="int", algo=algo))
 
 
-@pytest.mark.parametrize("algo", ["tile", "warp"])
+@pytest.mark.parametrize("algo", ["tile", "warp", "tc"])
 def test_strip30_full_block(algo):
     # 30 images x 8,000 descriptors, 120 ordered pairs: one MBR block
     _run(synth.strip30(), cm.Params.make(algo=algo), threads=16)
@@ -69,7 +69,7 @@ def test_projection_forms(projection, kw):
     _run(synth.pair2k(n=3000, shared=1000), cm.Params.make(projection=projection, **kw))
 
 
-@pytest.mark.parametrize("algo", ["tile", "warp"])
+@pytest.mark.parametrize("algo", ["tile", "warp", "tc"])
 def test_uneven_sizes_including_tiny_images(algo):
     wl = synth.grid500(gx=5, gy=4, nmin=1, nmax=5000)
     wl.images["n"][[0, 7]] = [1, 63]
@@ -79,13 +79,15 @@ def test_uneven_sizes_including_tiny_images(algo):
 @pytest.mark.parametrize("kw", [dict(K=2), dict(K=4), dict(K=16), dict(m=4), dict(m=0, K=16), dict(L=1),
                                 dict(L=8), dict(L=8, m=6), dict(ratio=(0, 1)), dict(ratio=(1, 2)),
                                 dict(ratio=(1, 1)), dict(seed=12345)])
-@pytest.mark.parametrize("algo", ["tile", "warp"])
+@pytest.mark.parametrize("algo", ["tile", "warp", "tc"])
 def test_parameter_variants(kw, algo):
+    if algo == "tc" and kw.get("K") == 2:
+        pytest.skip("the tensor-core scan keeps K >= 4")
     wl = synth.pair2k(n=1500, shared=600)
     _run(wl, cm.Params.make(algo=algo, **kw))
 
 
-@pytest.mark.parametrize("algo", ["tile", "warp"])
+@pytest.mark.parametrize("algo", ["tile", "warp", "tc"])
 def test_one_bucket_full_rerank_is_exhaustive_nn(algo):
     # m = 0 and K >= N_J: every database point is reranked, so the GPU result
     # equals exhaustive L2 nearest neighbours with the ratio test.
@@ -224,3 +226,30 @@ def test_fp8_tensor_core_rerank(K):
         assert np.array_equal(res["d1sq"][r0:r1][both], o["d1sq"][both])
     assert same / total >= 0.995, same / total
     print("fp8 K=%d decision agreement %.5f, top-2 re-score swaps %d" % (K, same / total, res["stats"][2]))
+
+
+def test_tensor_core_scan_pair2k_defaults():
+    res, rows, excl, n_diff = _run(synth.pair2k(), cm.Params.make(algo="tc"))
+    assert rows + excl == 2000
+
+
+@pytest.mark.parametrize("rerank", ["bf16", "fp32"])
+def test_tensor_core_scan_big_buckets(rerank):
+    # m = 2: four buckets of ~1,000 points per table, so a bucket spans several
+    # 128-row query tiles and 128-column database chunks
+    _run(synth.pair2k(n=4000, shared=1500), cm.Params.make(algo="tc", m=2, rerank=rerank))
+
+
+@pytest.mark.parametrize("K", [4, 8, 16])
+def test_tensor_core_scan_equals_tile_scan(K):
+    # the two scans rank the same candidates by the same exact keys
+    wl = synth.strip30(n_images=6, n=3000)
+    desc = wl.generate()
+    outs = []
+    for algo in ("tile", "tc"):
+        p = cm.Params.make(algo=algo, K=K, rerank="int")
+        index = cm.Index.build(p, wl.n_desc, torch.from_numpy(desc).cuda())
+        plan, res = gpu_match(index, wl.pairs)
+        outs.append(res)
+    for key in ("best_j", "d1sq", "d2sq", "topk"):
+        assert np.array_equal(outs[0][key], outs[1][key]), key
