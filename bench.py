@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--plain-pairs", type=int, default=200, help="pairs timed in the plain per-pair form")
     ap.add_argument("--oracle-pairs", type=int, default=12, help="pairs in the CPU-oracle sample")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--nn-pairs", type=int, default=2, help="pairs of the CPU leg also matched exhaustively")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default=None, help="GXxGY: a smaller grid of the same per-image shape (profiling)")
     return ap.parse_args()
@@ -125,6 +126,32 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# DRAM traffic of the dominant kernel, from ncu (dram__bytes_read.sum + dram__bytes_write.sum
+# summed over the 13 k_match launches of one grid5000 step, divided by 13).  It is reported only
+# for the configuration it was taken on and only while the kernel's sources are unchanged
+# (their SHA-256 below); otherwise the roofline's "traffic" is null.
+KMATCH_TRAFFIC = {"workload": "grid5000", "rerank": "bf16", "K": 8, "bytes_per_launch": None, "sources_sha256": None}
+KMATCH_SOURCES = ["paper_2505_22089_b300/csrc/cm_match.cu", "paper_2505_22089_b300/csrc/cm_internal.h",
+                  "paper_2505_22089_b300/csrc/cm_ratio.cuh"]
+
+
+def kmatch_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KMATCH_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def kmatch_traffic(args):
+    t = KMATCH_TRAFFIC
+    if (t["bytes_per_launch"] is None or args.grid or args.workload != t["workload"] or args.rerank != t["rerank"]
+            or args.K != t["K"] or kmatch_sources_sha256() != t["sources_sha256"]):
+        return None
+    return t["bytes_per_launch"]
 
 
 def peaks():
@@ -298,6 +325,59 @@ def pipeline_e2e(args, wl, host, kp, sums, stream, world, dev):
     return out, ver
 
 
+def schedule_comparison(wl, p, budget, size_blk):
+    """Data movement of three ways to feed the GPU the same pair list (Sec. 2.2):
+    one pair at a time (both images loaded and freed per pair), a load/free list
+    (pairs in band order, least recently used image freed when the budget is
+    full), and the MBR block rows of cm_schedule_blocks.  Counted on the host:
+    image loads, H2D bytes, match launches and the largest resident set."""
+    import paper_2505_22089_b300 as cm
+    nd = wl.n_desc.astype(np.int64)
+    ib = np.array([cm.image_bytes(p, int(n)) for n in nd], dtype=np.int64)
+    pairs = wl.pairs
+    per_pair = {"loads": int(2 * len(pairs)), "h2d_bytes": int(128 * (nd[pairs[:, 0]] + nd[pairs[:, 1]]).sum()),
+                "launches": int(len(pairs)), "peak_resident_bytes": int((ib[pairs[:, 0]] + ib[pairs[:, 1]]).max())}
+    # load/free list: band order, LRU eviction under the budget
+    order = np.lexsort((np.maximum(pairs[:, 0], pairs[:, 1]), np.minimum(pairs[:, 0], pairs[:, 1])))
+    resident, last_use, used, loads, h2d, peak = set(), {}, 0, 0, 0, 0
+    for t, k in enumerate(order):
+        for im in (int(pairs[k, 0]), int(pairs[k, 1])):
+            if im not in resident:
+                while used + ib[im] > budget and resident:
+                    victim = min((x for x in resident if x not in (int(pairs[k, 0]), int(pairs[k, 1]))),
+                                 key=lambda x: last_use[x], default=None)
+                    if victim is None:
+                        break
+                    resident.discard(victim)
+                    used -= ib[victim]
+                resident.add(im)
+                used += ib[im]
+                loads += 1
+                h2d += 128 * int(nd[im])
+            last_use[im] = t
+        peak = max(peak, used)
+    load_free = {"loads": loads, "h2d_bytes": h2d, "launches": int(len(pairs)), "peak_resident_bytes": int(peak)}
+    sched = cm.schedule_blocks(pairs, wl.n_desc, p, int(budget), size_blk)
+    res, used, peak, loads, h2d = set(), 0, 0, 0, 0
+    for r in sched.rows:
+        for im in r["load"]:
+            if im not in res:
+                res.add(im)
+                used += ib[im]
+                loads += 1
+                h2d += 128 * int(nd[im])
+        peak = max(peak, used)
+        for im in r["free"]:
+            if im in res:
+                res.discard(im)
+                used -= ib[im]
+    mbr = {"loads": loads, "h2d_bytes": h2d, "launches": sum(1 for r in sched.rows if r["pairs"]),
+           "peak_resident_bytes": int(peak), "gps_iterations": sched.iterations}
+    sched.close()
+    return {"budget_bytes": int(budget), "size_blk": size_blk, "per_pair": per_pair, "load_free_lru": load_free,
+            "mbr_blocks": mbr}
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2505_22089_b300 as cm
@@ -344,7 +424,7 @@ def run_ours(args, rank, world, local):
     evals = head["evals_per_step"]
     achieved = 4.0 * evals / head["launches"] / (head["match_launch_ms"] / 1e3)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": popc_peak / 1e12, "unit": "Tpopc/s",
-                "frac": achieved / popc_peak, "traffic": None,
+                "frac": achieved / popc_peak, "traffic": kmatch_traffic(args),
                 "peak_kind": "derived: %d POPC/clk/SM (measured) x %d SMs x %.0f MHz (%s max clock)"
                              % (POPC_PER_CLK_PER_SM, SM_COUNT, sm_mhz, pk_kind),
                 "kernel": "k_match", "evals_per_step": evals, "match_launch_ms": head["match_launch_ms"],
@@ -385,6 +465,7 @@ def run_ours(args, rank, world, local):
         "forms": forms_out,
         "plain_fp32_per_pair": plain,
         "pipeline_verified": verified,
+        "schedules": schedule_comparison(wl, p, int(args.budget_gb * 2 ** 30), args.block_images),
         "gpu_launches": args.steps * head["graph_kernels"],
         "roofline": roofline,
         "clocks": head["clocks"],
@@ -451,11 +532,49 @@ def cpu_baseline_and_agreement(args, wl, desc, sums, pairs, rows, gpu_rows):
         union += len(gm | om)
         ng += len(gm)
         no += len(om)
+    ceiling = exhaustive_nn_quality(wl, desc, pairs, sel[: args.nn_pairs], gpu_rows) if args.nn_pairs > 0 else None
     return {"cpu_baseline": {"value": len(sel) / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                              "sample": "%d of %d pairs, each: hash both images (FP64) + match; centring sums "
                                        "given" % (len(sel), len(pairs))},
             "pairs_checked": int(len(sel)), "match_set_jaccard": inter / union if union else 1.0,
-            "per_query_agreement": same / total if total else 1.0, "gpu_matches": ng, "oracle_matches": no}
+            "per_query_agreement": same / total if total else 1.0, "gpu_matches": ng, "oracle_matches": no,
+            "exhaustive_nn": ceiling}
+
+
+def exhaustive_nn_quality(wl, desc, pairs, sel, gpu_rows):
+    """Quality ceiling: exhaustive nearest neighbours of every query over all of
+    J with the same exact ratio test (d^2 from an FP64 matrix product of the
+    uint8 rows, exact for integers), against the cascade-hashing matches on
+    the same pairs: recall = shared / exhaustive, precision = shared / cascade."""
+    off = wl.row_off
+    num, den = 4, 5
+    shared = n_ex = n_gpu = 0
+    t0 = time.perf_counter()
+    for k in sel:
+        i, j = (int(x) for x in pairs[k])
+        X = desc[off[i]:off[i + 1]].astype(np.float64)
+        Y = desc[off[j]:off[j + 1]].astype(np.float64)
+        ny = (Y * Y).sum(1)
+        ex = np.full(len(X), -1, dtype=np.int64)
+        for q0 in range(0, len(X), 2048):
+            Xq = X[q0:q0 + 2048]
+            d2 = (Xq * Xq).sum(1)[:, None] + ny[None, :] - 2.0 * (Xq @ Y.T)
+            top = np.argpartition(d2, 1, axis=1)[:, :2]
+            a = np.take_along_axis(d2, top, 1)
+            order = np.argsort(a, axis=1, kind="stable")
+            top = np.take_along_axis(top, order, 1)
+            a = np.take_along_axis(a, order, 1)
+            ok = den * den * a[:, 0] < num * num * a[:, 1]
+            ex[q0:q0 + len(Xq)] = np.where(ok, top[:, 0], -1)
+        g = gpu_rows[int(k)]
+        shared += int(((g == ex) & (g >= 0)).sum())
+        n_ex += int((ex >= 0).sum())
+        n_gpu += int((g >= 0).sum())
+    return {"pairs": int(len(sel)), "exhaustive_matches": n_ex, "cascade_matches": n_gpu,
+            "recall": shared / n_ex if n_ex else 1.0, "precision": shared / n_gpu if n_gpu else 1.0,
+            "seconds": round(time.perf_counter() - t0, 1),
+            "note": "exhaustive L2 NN over all database points, exact ratio test 4/5; ties in d^2 resolved by "
+                    "argpartition order (rare)"}
 
 
 def run_reference(args, rank, world):
