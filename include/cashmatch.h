@@ -253,6 +253,13 @@ cm_status cm_match_plan_run(cm_match_plan* pl, const cm_match_out* out, cm_strea
  * Entries past `capacity` are dropped (counts stay exact).  Async. */
 cm_status cm_match_plan_compact(cm_match_plan* pl, const int32_t* d_best_j, uint32_t* d_counts, uint64_t* d_offsets,
                                 uint64_t* d_total, uint32_t* d_matches, uint64_t capacity, cm_stream stream);
+/* Two-way (mutual) consistency of a run's decisions, a matching variant next
+ * to the one-directional ratio test of Sec. 2.3.1 step (4): for each pair (I, J)
+ * of the plan whose reverse (J, I) is also in the plan, a match q -> j is kept
+ * only if (J, I) matched j back to q; pairs without a reverse keep their
+ * decisions.  d_best_in: a cm_match_plan_run best_j output; d_best_out: a
+ * distinct device array of the same rows.  Async. */
+cm_status cm_match_plan_mutual(cm_match_plan* pl, const int32_t* d_best_in, int32_t* d_best_out, cm_stream stream);
 void cm_match_plan_destroy(cm_match_plan* pl);
 /* Convenience: plan, run on stream, wait for the stream, destroy the plan. */
 cm_status cm_match_pairs(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, const cm_match_out* out,

@@ -49,7 +49,7 @@ EXPORTS = [
     "cm_schedule_get_row", "cm_free_schedule", "cm_gps_order", "cm_index_create", "cm_index_set_mean",
     "cm_index_mean_device", "cm_index_col_sums", "cm_index_check", "cm_index_load", "cm_index_rehash", "cm_index_evict", "cm_build_index",
     "cm_index_image_view", "cm_index_destroy", "cm_match_plan_create", "cm_match_plan_rows", "cm_match_plan_run",
-    "cm_match_plan_compact", "cm_match_plan_destroy", "cm_match_pairs", "cm_sequence_create", "cm_sequence_launch",
+    "cm_match_plan_compact", "cm_match_plan_mutual", "cm_match_plan_destroy", "cm_match_pairs", "cm_sequence_create", "cm_sequence_launch",
     "cm_sequence_kernels", "cm_sequence_destroy", "cm_schedule_arena_bytes", "cm_pipeline_workspace_bytes", "cm_run_schedule",
     "cm_verify_affine", "cm_affine_verify_cb", "cm_autotune", "cm_match_pair_noalloc",
 ]
@@ -162,6 +162,7 @@ def lib():
             "cm_match_plan_run": (i32, [vp, ctypes.POINTER(MatchOut), vp]),
             "cm_match_plan_destroy": (None, [vp]),
             "cm_match_plan_compact": (i32, [vp, vp, vp, vp, vp, vp, u64, vp]),
+            "cm_match_plan_mutual": (i32, [vp, vp, vp, vp]),
             "cm_match_pairs": (i32, [vp, vp, i64, ctypes.POINTER(MatchOut), vp]),
             "cm_match_pair_noalloc": (i32, [P, vp, i32, vp, i32, vp, u64, vp, vp, vp, vp]),
             "cm_sequence_create": (i32, [vp, i32, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]),
@@ -512,6 +513,13 @@ class MatchPlan:
         check(lib().cm_match_plan_compact(self.h, _ptr(best_j), _ptr(counts), _ptr(offsets), _ptr(total),
                                           _ptr(matches), cap, _stream(stream)))
         return counts, offsets, total, matches
+
+    def mutual(self, best_j, stream=None):
+        """cm_match_plan_mutual: decisions kept only where the reverse pair agrees (new CUDA tensor)."""
+        import torch
+        out = torch.empty_like(best_j)
+        check(lib().cm_match_plan_mutual(self.h, _ptr(best_j), _ptr(out), _stream(stream)))
+        return out
 
     def close(self):
         if getattr(self, "h", None):

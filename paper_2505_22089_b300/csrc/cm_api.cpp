@@ -528,6 +528,15 @@ extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, in
         max_ni = std::max(max_ni, ix->n_desc[i]);
     }
     if (items > INT32_MAX / 2) return fail(CM_ERR_INVALID, "plan: too many work items");
+    {   // the reverse of each pair within the plan (first occurrence), for cm_match_plan_mutual
+        std::map<std::pair<int, int>, int64_t> first;
+        for (int64_t k = 0; k < n_pairs; ++k) first.emplace(std::make_pair(tab[k].i, tab[k].j), k);
+        for (int64_t k = 0; k < n_pairs; ++k) {
+            auto it = first.find(std::make_pair(tab[k].j, tab[k].i));
+            tab[k].rev = it == first.end() ? -1 : (int32_t)it->second;
+            tab[k].pad = 0;
+        }
+    }
     cm_match_plan* pl = new (std::nothrow) cm_match_plan();
     if (!pl) return fail(CM_ERR_NOMEM, "plan: host allocation");
     const uint64_t bytes = plan_bytes(&ix->p, n_pairs, rows, max_ni);
@@ -618,6 +627,17 @@ extern "C" cm_status cm_match_plan_compact(cm_match_plan* pl, const int32_t* d_b
                            ix->at<DevImage>(ix->fx.imgs), d_best_j, d_counts,
                            reinterpret_cast<unsigned long long*>(d_offsets), reinterpret_cast<unsigned long long*>(d_total),
                            d_matches, (unsigned long long)capacity, reinterpret_cast<cudaStream_t>(stream)));
+    return CM_OK;
+}
+
+extern "C" cm_status cm_match_plan_mutual(cm_match_plan* pl, const int32_t* d_best_in, int32_t* d_best_out,
+                                          cm_stream stream) {
+    if (!pl || !d_best_in || !d_best_out || d_best_in == d_best_out)
+        return fail(CM_ERR_INVALID, "mutual: bad argument (in and out must differ)");
+    if (!pl->ix) return fail(CM_ERR_STATE, "mutual: the plan's index was destroyed");
+    cm_index* ix = pl->ix;
+    CM_CUDA(launch_mutual(reinterpret_cast<const DevPair*>(ix->arena + pl->table_at), (int)pl->n_pairs,
+                          ix->at<DevImage>(ix->fx.imgs), d_best_in, d_best_out, reinterpret_cast<cudaStream_t>(stream)));
     return CM_OK;
 }
 

@@ -105,7 +105,31 @@ __global__ void __launch_bounds__(kCompactThreads) k_scatter(const DevPair* __re
     }
 }
 
+// Two-way consistency: a match q -> j of pair (I, J) stays only if the reverse
+// pair (J, I) matched j back to q.  One CTA per pair; a pair without a reverse
+// keeps its decisions.
+__global__ void __launch_bounds__(kCompactThreads) k_mutual(const DevPair* __restrict__ pairs, const DevImage* imgs,
+                                                            const int32_t* __restrict__ in, int32_t* __restrict__ out) {
+    const DevPair P = pairs[blockIdx.x];
+    const int n = imgs[P.i].n;
+    const int nj = imgs[P.j].n;
+    const int64_t back0 = P.rev >= 0 ? pairs[P.rev].row_off : 0;
+    for (int q = threadIdx.x; q < n; q += kCompactThreads) {
+        const int32_t j = in[P.row_off + q];
+        int32_t keep = j;
+        if (P.rev >= 0 && j >= 0) keep = (j < nj && in[back0 + j] == q) ? j : -1;
+        out[P.row_off + q] = keep;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_mutual(const DevPair* pairs, int n_pairs, const DevImage* imgs, const int32_t* best_in,
+                          int32_t* best_out, cudaStream_t s) {
+    if (n_pairs <= 0) return cudaSuccess;
+    k_mutual<<<n_pairs, kCompactThreads, 0, s>>>(pairs, imgs, best_in, best_out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_compact(const DevPair* pairs, int n_pairs, const DevImage* imgs, const int32_t* best,
                            uint32_t* counts, unsigned long long* offsets, unsigned long long* total, uint32_t* out,

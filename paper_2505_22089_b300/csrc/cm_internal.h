@@ -44,6 +44,8 @@ struct DevPair {
     int64_t row_off;       // first output row of this pair
     int32_t item0;         // first work item of this pair
     int32_t nitems;        // work items (query tiles) of this pair
+    int32_t rev;           // index of the pair (j, i) in the same plan, -1 if absent
+    int32_t pad;
 };
 
 struct HashLaunch {
@@ -99,6 +101,8 @@ size_t match_smem_bytes(int S, int K);
 cudaError_t launch_compact(const DevPair* pairs, int n_pairs, const DevImage* imgs, const int32_t* best,
                            uint32_t* counts, unsigned long long* offsets, unsigned long long* total, uint32_t* out,
                            unsigned long long capacity, cudaStream_t s);                 // cm_compact.cu
+cudaError_t launch_mutual(const DevPair* pairs, int n_pairs, const DevImage* imgs, const int32_t* best_in,
+                          int32_t* best_out, cudaStream_t s);                                // cm_compact.cu
 int hash_npg(int P_pad);
 // Tensor-core rerank (cm_rerank_tc.cu): row copies written after hashing, and
 // the rerank of a plan's top-K lists.
