@@ -532,49 +532,110 @@ def cpu_baseline_and_agreement(args, wl, desc, sums, pairs, rows, gpu_rows):
         union += len(gm | om)
         ng += len(gm)
         no += len(om)
-    ceiling = exhaustive_nn_quality(wl, desc, pairs, sel[: args.nn_pairs], gpu_rows) if args.nn_pairs > 0 else None
+    ceiling = sweep = None
+    if args.nn_pairs > 0:
+        t1 = time.perf_counter()
+        nn_sel = sel[: args.nn_pairs]
+        exact = {int(k): exhaustive_nn(wl, desc, pairs[k]) for k in nn_sel}
+        ceiling = exhaustive_nn_quality(wl, desc, pairs, nn_sel, gpu_rows, exact)
+        sweep = quality_sweep(wl, desc, sums, pairs, nn_sel, exact, gpu_rows, args.K)
+        ceiling["seconds"] = round(time.perf_counter() - t1, 1)
     return {"cpu_baseline": {"value": len(sel) / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                              "sample": "%d of %d pairs, each: hash both images (FP64) + match; centring sums "
                                        "given" % (len(sel), len(pairs))},
             "pairs_checked": int(len(sel)), "match_set_jaccard": inter / union if union else 1.0,
             "per_query_agreement": same / total if total else 1.0, "gpu_matches": ng, "oracle_matches": no,
-            "exhaustive_nn": ceiling}
+            "exhaustive_nn": ceiling, "quality_sweep": sweep}
 
 
-def exhaustive_nn_quality(wl, desc, pairs, sel, gpu_rows):
-    """Quality ceiling: exhaustive nearest neighbours of every query over all of
-    J with the same exact ratio test (d^2 from an FP64 matrix product of the
-    uint8 rows, exact for integers), against the cascade-hashing matches on
-    the same pairs: recall = shared / exhaustive, precision = shared / cascade."""
+def exhaustive_nn(wl, desc, pair):
+    """Exhaustive nearest neighbours of every query of pair (i, j) over all of J
+    with the exact ratio test 4/5 (d^2 from an FP64 matrix product of the uint8
+    rows, exact for integers).  Returns best_j per query (-1: no match)."""
     off = wl.row_off
     num, den = 4, 5
+    i, j = (int(x) for x in pair)
+    X = desc[off[i]:off[i + 1]].astype(np.float64)
+    Y = desc[off[j]:off[j + 1]].astype(np.float64)
+    ny = (Y * Y).sum(1)
+    ex = np.full(len(X), -1, dtype=np.int64)
+    for q0 in range(0, len(X), 2048):
+        Xq = X[q0:q0 + 2048]
+        d2 = (Xq * Xq).sum(1)[:, None] + ny[None, :] - 2.0 * (Xq @ Y.T)
+        top = np.argpartition(d2, 1, axis=1)[:, :2]
+        a = np.take_along_axis(d2, top, 1)
+        order = np.argsort(a, axis=1, kind="stable")
+        top = np.take_along_axis(top, order, 1)
+        a = np.take_along_axis(a, order, 1)
+        ok = den * den * a[:, 0] < num * num * a[:, 1]
+        ex[q0:q0 + len(Xq)] = np.where(ok, top[:, 0], -1)
+    return ex
+
+
+def recall_precision(g, ex):
+    shared = int(((g == ex) & (g >= 0)).sum())
+    n_ex, n_g = int((ex >= 0).sum()), int((g >= 0).sum())
+    return shared, n_ex, n_g
+
+
+def exhaustive_nn_quality(wl, desc, pairs, sel, gpu_rows, exact):
+    """Quality ceiling: the cascade-hashing matches of sampled pairs against
+    exhaustive nearest neighbours with the same exact ratio test:
+    recall = shared / exhaustive, precision = shared / cascade."""
     shared = n_ex = n_gpu = 0
-    t0 = time.perf_counter()
     for k in sel:
-        i, j = (int(x) for x in pairs[k])
-        X = desc[off[i]:off[i + 1]].astype(np.float64)
-        Y = desc[off[j]:off[j + 1]].astype(np.float64)
-        ny = (Y * Y).sum(1)
-        ex = np.full(len(X), -1, dtype=np.int64)
-        for q0 in range(0, len(X), 2048):
-            Xq = X[q0:q0 + 2048]
-            d2 = (Xq * Xq).sum(1)[:, None] + ny[None, :] - 2.0 * (Xq @ Y.T)
-            top = np.argpartition(d2, 1, axis=1)[:, :2]
-            a = np.take_along_axis(d2, top, 1)
-            order = np.argsort(a, axis=1, kind="stable")
-            top = np.take_along_axis(top, order, 1)
-            a = np.take_along_axis(a, order, 1)
-            ok = den * den * a[:, 0] < num * num * a[:, 1]
-            ex[q0:q0 + len(Xq)] = np.where(ok, top[:, 0], -1)
-        g = gpu_rows[int(k)]
-        shared += int(((g == ex) & (g >= 0)).sum())
-        n_ex += int((ex >= 0).sum())
-        n_gpu += int((g >= 0).sum())
+        s, e, g = recall_precision(gpu_rows[int(k)], exact[int(k)])
+        shared += s
+        n_ex += e
+        n_gpu += g
     return {"pairs": int(len(sel)), "exhaustive_matches": n_ex, "cascade_matches": n_gpu,
             "recall": shared / n_ex if n_ex else 1.0, "precision": shared / n_gpu if n_gpu else 1.0,
-            "seconds": round(time.perf_counter() - t0, 1),
-            "note": "exhaustive L2 NN over all database points, exact ratio test 4/5; ties in d^2 resolved by "
-                    "argpartition order (rare)"}
+            "note": "exhaustive L2 NN over all database points, exact ratio test 4/5"}
+
+
+def quality_sweep(wl, desc, sums, pairs, sel, exact, gpu_rows, main_K):
+    """Recall / precision against exhaustive NN, and the candidate evaluations
+    of the lookup, for L in {4, 6, 8} tables and K in {4, 8, 16} kept
+    candidates, on the sampled pairs: an index over just their images, centred
+    on the whole workload's mean like the main run (so L=6 reproduces the
+    main run's matches at the main run's K, which is checked)."""
+    import paper_2505_22089_b300 as cm
+    off = wl.row_off
+    imgs = sorted(set(int(x) for k in sel for x in pairs[k]))
+    remap = {im: n for n, im in enumerate(imgs)}
+    sub_nd = np.array([wl.n_desc[im] for im in imgs], dtype=np.int32)
+    sub_pairs = np.array([[remap[int(pairs[k][0])], remap[int(pairs[k][1])]] for k in sel], dtype=np.int32)
+    views = [np.ascontiguousarray(desc[off[im]:off[im + 1]]) for im in imgs]
+    out = []
+    import torch
+    for L in (4, 6, 8):
+        for K in (4, 8, 16):
+            p = cm.Params.make(L=L, K=K)
+            index = cm.Index(p, sub_nd)
+            index.set_mean(sums, wl.total_desc)
+            index.load(list(range(len(imgs))), views, cm.MEM_HOST)
+            plan = cm.MatchPlan(index, sub_pairs)
+            o = plan.alloc_out(d12=False)
+            plan.run(o)
+            torch.cuda.synchronize()
+            bj = o["best_j"].cpu().numpy()
+            shared = n_ex = n_g = 0
+            same_as_main = True
+            for q, k in enumerate(sel):
+                mine = bj[plan.row_off[q]:plan.row_off[q + 1]]
+                s, e, g = recall_precision(mine, exact[int(k)])
+                shared, n_ex, n_g = shared + s, n_ex + e, n_g + g
+                same_as_main &= bool(np.array_equal(mine, gpu_rows[int(k)]))
+            pt = {"L": L, "K": K, "recall": round(shared / max(n_ex, 1), 4),
+                  "precision": round(shared / max(n_g, 1), 4), "matches": n_g,
+                  "evals": bucket_evaluations(index, wl, sub_pairs)}
+            if (L, K) == (6, main_K):
+                pt["equals_main_run"] = same_as_main
+            out.append(pt)
+            plan.close()
+            index.close()
+    return {"pairs": int(len(sel)), "points": out,
+            "note": "fp32 rerank; evals = sum over pairs, tables, buckets of n_I * n_J"}
 
 
 def run_reference(args, rank, world):
