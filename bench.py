@@ -13,7 +13,8 @@ with the descriptors already resident in HBM (headline rerank form; the other
 forms are timed the same way under "forms").  `e2e` runs the public pipeline
 call with the descriptors in pinned host memory: H2D, matching and the D2H of
 the match lists are inside its timed region.  "pipeline_verified" repeats it
-with affine RANSAC on the host cores overlapped with the GPU rows.
+with outlier removal on the host cores overlapped with the GPU rows: affine
+RANSAC alone, and the SAO local constraint ahead of RANSAC.
 
 The workloads are synthetic stand-ins for the paper's UAV datasets (see
 synth/).  `--impl reference` times the FP64 CPU oracle on the host cores on a
@@ -314,12 +315,21 @@ def pipeline_e2e(args, wl, host, kp, sums, stream, world, dev):
            "form": "cm_run_schedule, host descriptors (pinned) in, per-pair match lists (pinned host) out"}
     ver = None
     if kp is not None and args.verify_workers > 0:
+        # outlier removal on the host workers, overlapped with the GPU rows:
+        # RANSAC alone, then the SAO local constraint ahead of RANSAC (Sec. 2.3.3)
         kl = [kp[off[i]:off[i + 1]] for i in range(wl.n_images)]
-        st, inl = cm.run_schedule(index, sched, hl, verify="affine", keypoints=kl, thresh_px=4.0,
-                                  workers=args.verify_workers, stream=stream)
-        ver = {k: (round(v, 2) if isinstance(v, float) else v) for k, v in st.items()}
-        ver["inlier_share"] = float(inl.sum() / max(1, st["matches"]))
-        ver["overlap"] = "GPU rows overlap CPU verification when wall_ms < gpu_ms + verify_ms / workers"
+        ver = {"overlap": "GPU rows overlap CPU verification when wall_ms < gpu_ms + verify_ms / workers"}
+        for mode, sao_k in (("ransac", 0), ("sao_ransac", 8)):
+            kept = np.zeros(len(wl.pairs), dtype=np.int64)
+            st, inl = cm.run_schedule(index, sched, hl, verify="affine", keypoints=kl, thresh_px=4.0,
+                                      workers=args.verify_workers, stream=stream, sao_k=sao_k, sao_kept=kept)
+            v = {k: (round(x, 2) if isinstance(x, float) else x) for k, x in st.items()}
+            v["inliers"] = int(inl.sum())
+            v["inlier_share"] = float(inl.sum() / max(1, st["matches"]))
+            if sao_k:
+                v["sao_kept"] = int(kept.sum())
+                v["sao"] = {"k": sao_k, "max_score": 0.875}
+            ver[mode] = v
     index.close()
     sched.close()
     return out, ver

@@ -371,13 +371,39 @@ cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const cm_pair* pai
 cm_status cm_verify_affine(const float* kp_i, const float* kp_j, int64_t n_matches, const uint32_t* matches,
                            float thresh_px, int32_t max_iters, uint64_t seed, float* A, uint8_t* inlier_mask,
                            int64_t* n_inliers);
-/* A ready-made cm_verify_fn running cm_verify_affine; user = cm_affine_verifier*. */
+/* Spatial-angular-order local geometric constraint (Sec. 2.3.3, Fig. 4): a
+ * dissimilarity score per initial match of one pair, computed before RANSAC
+ * so that the global fit sees fewer outliers.  For match m = (p_m, q_m): its
+ * k_nn nearest other matches around p_m in the query image and, found
+ * independently, around q_m in the database image (squared Euclidean
+ * distance, ties by match index; the Euclidean k-NN set that the Delaunay
+ * graph of the matched keypoints yields); each list in angular order around
+ * its centre (from the horizontal axis, [0, 2*pi), a zero vector at angle 0,
+ * ties by match index); Score = d_ced / N with d_ced the cyclic unit-cost
+ * edit distance of the two label sequences and N = min(k_nn, n_matches - 1)
+ * (Score 0 when N = 0), in float.  A match is kept when Score <= max_score.
+ *  - kp_i / kp_j: host float [n][2] keypoints of the query / database image.
+ *  - matches: n_matches entries query << 16 | database index (as in cm_verify_fn).
+ *  - k_nn: 1..32 (8 is the usual choice); max_score >= 0 (0.875 keeps a match
+ *    unless its two orders need one edit per neighbour at k_nn = 8).
+ *  - score[n_matches], keep[n_matches] (0/1), *n_kept: outputs, any may be NULL.
+ * Host only, thread-safe, deterministic.  CM_ERR_INVALID on a bad argument. */
+cm_status cm_sao_filter(const float* kp_i, const float* kp_j, int64_t n_matches, const uint32_t* matches,
+                        int32_t k_nn, float max_score, float* score, uint8_t* keep, int64_t* n_kept);
+
+/* A ready-made cm_verify_fn running cm_verify_affine; user = cm_affine_verifier*.
+ * With sao_k > 0 the pair's matches first pass cm_sao_filter(sao_k,
+ * sao_max_score) and RANSAC fits the kept ones (the local-then-global
+ * outlier removal of Sec. 2.3.3). */
 typedef struct cm_affine_verifier {
     const float* const* keypoints;  /* per image: host float [n][2] */
     float thresh_px;
     int32_t max_iters;
     uint64_t seed;                  /* pair k uses seed ^ k */
     int64_t* inliers;               /* [n_pairs of the caller's list]: inlier count written per pair */
+    int32_t sao_k;                  /* 0: no local constraint; 1..32: its k */
+    float sao_max_score;
+    int64_t* sao_kept;              /* optional [n_pairs]: matches kept by the local constraint per pair */
 } cm_affine_verifier;
 int32_t cm_affine_verify_cb(void* user, int32_t row, int64_t pair_id, const cm_pair* pair, int64_t n_matches,
                             const uint32_t* matches);

@@ -51,7 +51,7 @@ EXPORTS = [
     "cm_index_image_view", "cm_index_destroy", "cm_match_plan_create", "cm_match_plan_rows", "cm_match_plan_run",
     "cm_match_plan_compact", "cm_match_plan_mutual", "cm_match_plan_destroy", "cm_match_pairs", "cm_sequence_create", "cm_sequence_launch",
     "cm_sequence_kernels", "cm_sequence_destroy", "cm_schedule_arena_bytes", "cm_pipeline_workspace_bytes", "cm_run_schedule",
-    "cm_verify_affine", "cm_affine_verify_cb", "cm_autotune", "cm_match_pair_noalloc",
+    "cm_verify_affine", "cm_affine_verify_cb", "cm_sao_filter", "cm_autotune", "cm_match_pair_noalloc",
 ]
 
 
@@ -102,7 +102,8 @@ class PipelineStats(ctypes.Structure):
 
 class AffineVerifier(ctypes.Structure):
     _fields_ = [("keypoints", ctypes.c_void_p), ("thresh_px", ctypes.c_float), ("max_iters", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("inliers", ctypes.c_void_p)]
+                ("seed", ctypes.c_uint64), ("inliers", ctypes.c_void_p), ("sao_k", ctypes.c_int32),
+                ("sao_max_score", ctypes.c_float), ("sao_kept", ctypes.c_void_p)]
 
 
 VERIFY_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
@@ -176,6 +177,7 @@ def lib():
                                       ctypes.POINTER(PipelineStats)]),
             "cm_verify_affine": (i32, [vp, vp, i64, vp, ctypes.c_float, i32, u64, vp, vp, ctypes.POINTER(i64)]),
             "cm_affine_verify_cb": (i32, [vp, i32, i64, vp, i64, vp]),
+            "cm_sao_filter": (i32, [vp, vp, i64, vp, i32, ctypes.c_float, vp, vp, ctypes.POINTER(i64)]),
             "cm_autotune": (i32, [vp, vp, i64, vp, i32, ctypes.c_float, vp, ctypes.POINTER(TuneResult)]),
         }
         for name, (res, args) in sig.items():
@@ -308,6 +310,19 @@ def verify_affine(kp_i, kp_j, matches, thresh_px: float = 3.0, max_iters: int = 
                                  float(thresh_px), int(max_iters), int(seed), A.ctypes.data, mask.ctypes.data,
                                  ctypes.byref(n)))
     return A.reshape(2, 3), mask[: len(mt)].astype(bool), n.value
+
+
+def sao_filter(kp_i, kp_j, matches, k: int = 8, max_score: float = 0.875):
+    """cm_sao_filter on host arrays: returns (scores float32, keep mask, kept count)."""
+    ki = np.ascontiguousarray(kp_i, dtype=np.float32)
+    kj = np.ascontiguousarray(kp_j, dtype=np.float32)
+    mt = np.ascontiguousarray(matches, dtype=np.uint32)
+    score = np.zeros(max(len(mt), 1), dtype=np.float32)
+    keep = np.zeros(max(len(mt), 1), dtype=np.uint8)
+    n = ctypes.c_int64()
+    check(lib().cm_sao_filter(ki.ctypes.data, kj.ctypes.data, len(mt), mt.ctypes.data if len(mt) else None, int(k),
+                              float(max_score), score.ctypes.data, keep.ctypes.data, ctypes.byref(n)))
+    return score[: len(mt)], keep[: len(mt)].astype(bool), n.value
 
 
 def _cudart():
@@ -586,11 +601,14 @@ def compact_out(plan: "MatchPlan", capacity: int | None = None) -> dict:
 
 
 def run_schedule(index: Index, sched: Schedule, desc_host, verify=None, keypoints=None, thresh_px: float = 3.0,
-                 max_iters: int = 500, seed: int = 7, workers: int = 4, stream=None):
+                 max_iters: int = 500, seed: int = 7, workers: int = 4, stream=None, sao_k: int = 0,
+                 sao_max_score: float = 0.875, sao_kept=None):
     """cm_run_schedule.  desc_host: per image a host uint8 [n][128] array or
     pinned CPU tensor.  verify: None (count matches only), "affine" (the
-    library's RANSAC callback over `keypoints`, per image float [n][2]), or a
-    Python callable f(row, pair_id, (i, j), matches: np.ndarray uint32) -> int.
+    library's RANSAC callback over `keypoints`, per image float [n][2], after
+    the SAO local constraint when sao_k > 0; sao_kept: optional int64 array,
+    one entry per pair, receiving the matches SAO kept), or a Python callable
+    f(row, pair_id, (i, j), matches: np.ndarray uint32) -> int.
     Returns (stats dict, inliers per pair or None)."""
     import torch
     pairs = sched.pairs
@@ -607,8 +625,11 @@ def run_schedule(index: Index, sched: Schedule, desc_host, verify=None, keypoint
         kps = [np.ascontiguousarray(k, dtype=np.float32) for k in keypoints]
         kp_ptrs = (ctypes.c_void_p * len(kps))(*[k.ctypes.data for k in kps])
         inliers = np.full(len(pairs), -1, dtype=np.int64)
+        if sao_kept is not None:
+            assert sao_kept.dtype == np.int64 and sao_kept.shape == (len(pairs),) and sao_kept.flags.c_contiguous
         v = AffineVerifier(ctypes.cast(kp_ptrs, ctypes.c_void_p), float(thresh_px), int(max_iters), int(seed),
-                           inliers.ctypes.data)
+                           inliers.ctypes.data, int(sao_k), float(sao_max_score),
+                           sao_kept.ctypes.data if sao_kept is not None else None)
         keep += [kps, kp_ptrs, v]
         fn = ctypes.cast(lib().cm_affine_verify_cb, ctypes.c_void_p)
         user = ctypes.cast(ctypes.pointer(v), ctypes.c_void_p)

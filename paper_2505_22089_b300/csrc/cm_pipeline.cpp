@@ -259,9 +259,23 @@ extern "C" cm_status cm_verify_affine(const float* kp_i, const float* kp_j, int6
 extern "C" int32_t cm_affine_verify_cb(void* user, int32_t, int64_t pair_id, const cm_pair* pair, int64_t n_matches,
                                        const uint32_t* matches) {
     auto* v = static_cast<cm_affine_verifier*>(user);
+    const float *ki = v->keypoints[pair->i], *kj = v->keypoints[pair->j];
+    std::vector<uint32_t> kept;
+    if (v->sao_k > 0) {   // local constraint first, RANSAC on the survivors
+        std::vector<uint8_t> keep((size_t)n_matches);
+        int64_t nk = 0;
+        if (cm_sao_filter(ki, kj, n_matches, matches, v->sao_k, v->sao_max_score, nullptr, keep.data(), &nk) != CM_OK)
+            return 1;
+        kept.reserve((size_t)nk);
+        for (int64_t m = 0; m < n_matches; ++m)
+            if (keep[m]) kept.push_back(matches[m]);
+        if (v->sao_kept) v->sao_kept[pair_id] = nk;
+        matches = kept.data();
+        n_matches = nk;
+    }
     int64_t n = 0;
-    if (cm_verify_affine(v->keypoints[pair->i], v->keypoints[pair->j], n_matches, matches, v->thresh_px, v->max_iters,
-                         v->seed ^ (uint64_t)pair_id, nullptr, nullptr, &n) != CM_OK)
+    if (cm_verify_affine(ki, kj, n_matches, matches, v->thresh_px, v->max_iters, v->seed ^ (uint64_t)pair_id, nullptr,
+                         nullptr, &n) != CM_OK)
         return 1;
     if (v->inliers) v->inliers[pair_id] = n;
     return 0;

@@ -188,6 +188,28 @@ def test_pipeline_affine_verification_finds_the_shared_tracks():
     assert stats["verify_ms"] > 0
 
 
+def test_pipeline_sao_then_affine_equals_the_host_calls():
+    """The verifier with the SAO local constraint: per pair, the kept count is
+    cm_sao_filter's on the pair's initial matches and the inlier count is
+    cm_verify_affine's on the kept ones (same seed per pair)."""
+    wl, desc, p, sched, host, kps = _grid_case()
+    index = _pipeline_index(wl, p, desc)
+    kept = np.full(len(wl.pairs), -1, dtype=np.int64)
+    seed = 7
+    stats, inliers = cm.run_schedule(index, sched, host, verify="affine", keypoints=kps, thresh_px=4.0, workers=4,
+                                     seed=seed, sao_k=8, sao_max_score=0.875, sao_kept=kept)
+    direct = _index(wl, p, desc)
+    plan, best = _direct(direct, wl.pairs)
+    lists = _lists(plan, best)
+    for k, (i, j) in enumerate(wl.pairs):
+        _, keep, nk = cm.sao_filter(kps[i], kps[j], lists[k], 8, 0.875)
+        assert kept[k] == nk, k
+        _, _, n_in = cm.verify_affine(kps[i], kps[j], lists[k][keep], thresh_px=4.0, max_iters=500,
+                                      seed=seed ^ k)
+        assert inliers[k] == n_in, k
+    assert 0 < kept.sum() <= stats["matches"]
+
+
 def test_pipeline_callback_abort_and_recovery():
     wl, desc, p, sched, host, _ = _grid_case()
     index = _pipeline_index(wl, p, desc)
