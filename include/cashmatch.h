@@ -408,6 +408,35 @@ typedef struct cm_affine_verifier {
 int32_t cm_affine_verify_cb(void* user, int32_t row, int64_t pair_id, const cm_pair* pair, int64_t n_matches,
                             const uint32_t* matches);
 
+/* ---- VLAD image encoding (Sec. 2.1, the retrieval front end) ------------- */
+/* Device workspace of cm_vlad_encode for n_images images of n_rows rows in all. */
+cm_status cm_vlad_workspace_bytes(int32_t n_images, int64_t n_rows, uint64_t* bytes);
+/* VLAD vector of every image, against a codebook on the descriptors' integer
+ * grid (e.g. k-means centroids rounded to integers; the paper trains the
+ * codebook with Lloyd's k-means, outside this call):
+ *  1. each descriptor goes to its nearest codeword by exact squared Euclidean
+ *     distance (ties to the smaller codeword index) - a 128 x C x 128 BF16
+ *     tensor-core contraction per tile of 128 descriptors, exact on integers;
+ *  2. per codeword c, r_c = sum over the image's descriptors assigned to c of
+ *     (x - c), exact integers, concatenated codeword-major (C x 128);
+ *  3. signed square root of every component, then L2 normalisation of the
+ *     vector (FP64 sum of squares); an all-zero vector stays zero.
+ *  - desc: device uint8 [n_rows][128], all images' rows concatenated.
+ *  - img_off: host int64 [n_images + 1], img_off[0] = 0, ascending; image i
+ *    owns rows img_off[i] .. img_off[i+1]-1 (an empty image gives zeros).
+ *  - codebook: device uint8 [n_codewords][128], 1 <= n_codewords <= 256.
+ *  - d_work / work_bytes: device workspace of cm_vlad_workspace_bytes, 256-byte aligned.
+ *  - assign (optional): device uint16 [n_rows], the codeword of each row.
+ *  - vlad: device float [n_images][n_codewords * 128].
+ * Asynchronous on `stream`; cm_vlad_status(d_work, stream) waits for it and
+ * reports CM_ERR_TIMEOUT if a bounded device wait gave up.  Errors:
+ * CM_ERR_INVALID (bad argument), CM_ERR_BUDGET (workspace too small), CM_ERR_CUDA. */
+cm_status cm_vlad_encode(const uint8_t* desc, const int64_t* img_off, int32_t n_images, const uint8_t* codebook,
+                         int32_t n_codewords, void* d_work, uint64_t work_bytes, uint16_t* assign, float* vlad,
+                         cm_stream stream);
+/* Synchronises `stream` and reads the device status of the last cm_vlad_encode on d_work. */
+cm_status cm_vlad_status(const void* d_work, cm_stream stream);
+
 /* ---- autotuning of the match launch -------------------------------------- */
 typedef struct cm_tune_result {
     int32_t query_tile;  /* chosen queries per work item */

@@ -27,8 +27,9 @@ def assign(desc: np.ndarray, codebook: np.ndarray) -> np.ndarray:
     X = np.asarray(desc, dtype=np.int64)
     Cb = np.asarray(codebook, dtype=np.int64)
     out = np.empty(len(X), dtype=np.int64)
-    for r0 in range(0, len(X), 4096):
-        Xr = X[r0:r0 + 4096]
+    step = max(1, (1 << 23) // max(1, Cb.size))   # rows per block: ~8 M differences at a time
+    for r0 in range(0, len(X), step):
+        Xr = X[r0:r0 + step]
         d2 = ((Xr[:, None, :] - Cb[None, :, :]) ** 2).sum(-1)   # exact integers
         out[r0:r0 + len(Xr)] = np.argmin(d2, axis=1)            # first minimum: the smaller index
     return out

@@ -51,7 +51,8 @@ EXPORTS = [
     "cm_index_image_view", "cm_index_destroy", "cm_match_plan_create", "cm_match_plan_rows", "cm_match_plan_run",
     "cm_match_plan_compact", "cm_match_plan_mutual", "cm_match_plan_destroy", "cm_match_pairs", "cm_sequence_create", "cm_sequence_launch",
     "cm_sequence_kernels", "cm_sequence_destroy", "cm_schedule_arena_bytes", "cm_pipeline_workspace_bytes", "cm_run_schedule",
-    "cm_verify_affine", "cm_affine_verify_cb", "cm_sao_filter", "cm_autotune", "cm_match_pair_noalloc",
+    "cm_verify_affine", "cm_affine_verify_cb", "cm_sao_filter", "cm_vlad_workspace_bytes", "cm_vlad_encode",
+    "cm_vlad_status", "cm_autotune", "cm_match_pair_noalloc",
 ]
 
 
@@ -178,6 +179,9 @@ def lib():
             "cm_verify_affine": (i32, [vp, vp, i64, vp, ctypes.c_float, i32, u64, vp, vp, ctypes.POINTER(i64)]),
             "cm_affine_verify_cb": (i32, [vp, i32, i64, vp, i64, vp]),
             "cm_sao_filter": (i32, [vp, vp, i64, vp, i32, ctypes.c_float, vp, vp, ctypes.POINTER(i64)]),
+            "cm_vlad_workspace_bytes": (i32, [i32, i64, ctypes.POINTER(u64)]),
+            "cm_vlad_encode": (i32, [vp, vp, i32, vp, i32, vp, u64, vp, vp, vp]),
+            "cm_vlad_status": (i32, [vp, vp]),
             "cm_autotune": (i32, [vp, vp, i64, vp, i32, ctypes.c_float, vp, ctypes.POINTER(TuneResult)]),
         }
         for name, (res, args) in sig.items():
@@ -323,6 +327,28 @@ def sao_filter(kp_i, kp_j, matches, k: int = 8, max_score: float = 0.875):
     check(lib().cm_sao_filter(ki.ctypes.data, kj.ctypes.data, len(mt), mt.ctypes.data if len(mt) else None, int(k),
                               float(max_score), score.ctypes.data, keep.ctypes.data, ctypes.byref(n)))
     return score[: len(mt)], keep[: len(mt)].astype(bool), n.value
+
+
+def vlad_encode(desc, n_desc, codebook, stream=None, want_assign: bool = False, check_status: bool = True):
+    """cm_vlad_encode.  desc: CUDA uint8 [n][128] (all images' rows), n_desc:
+    rows per image, codebook: CUDA uint8 [C][128].  Returns (vlad float32
+    [n_images][C * 128], assignments uint16 as int32 tensor or None)."""
+    import torch
+    nd = np.ascontiguousarray(n_desc, dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(nd)]).astype(np.int64)
+    C = int(codebook.shape[0])
+    ws = ctypes.c_uint64()
+    check(lib().cm_vlad_workspace_bytes(len(nd), int(off[-1]), ctypes.byref(ws)))
+    work = torch.empty(int(ws.value) + 256, dtype=torch.uint8, device=desc.device)
+    wbase = (work.data_ptr() + 255) // 256 * 256
+    out = torch.empty((len(nd), C * 128), dtype=torch.float32, device=desc.device)
+    asg = torch.empty(int(off[-1]), dtype=torch.int16, device=desc.device) if want_assign else None
+    check(lib().cm_vlad_encode(_ptr(desc), off.ctypes.data, len(nd), _ptr(codebook), C, ctypes.c_void_p(wbase),
+                               int(ws.value), _ptr(asg), _ptr(out), _stream(stream)))
+    if check_status:
+        check(lib().cm_vlad_status(ctypes.c_void_p(wbase), _stream(stream)))
+    a = asg.to(torch.int32) & 0xFFFF if asg is not None else None
+    return out, a
 
 
 def _cudart():

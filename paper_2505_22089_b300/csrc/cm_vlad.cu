@@ -1,0 +1,275 @@
+// VLAD image encoding (Sec. 2.1): the retrieval front end that turns each
+// image's descriptors into one vector, from which the view graph's pairs are
+// retrieved.
+//
+// k_vlad_assign: nearest codeword of every descriptor.  With x and the
+// codewords c on the integer grid 0..255 (exact in BF16), the dot products
+// x.c of a tile of 128 descriptors against all C codewords are one
+// 128 x C x 128 tcgen05 contraction; every partial sum is an integer below
+// 2^24, so the FP32 accumulator is exact and so is |c|^2 - 2 x.c (its
+// magnitude stays below 2^24).  The argmin over c of that value (ties to the
+// smaller c) is the exact nearest codeword.  The codebook is converted once
+// per CTA and stays in shared memory; each CTA converts its tiles' rows,
+// one thread issues the 8 MMAs, the 4 warps read their lanes back.
+//
+// k_vlad_accum: one CTA per image sums x per codeword in shared memory
+// (integer atomics, exact), forms the residual sums r_c = sum x - n_c * c,
+// takes the signed square root of every component and L2-normalises the
+// vector (FP64 sum of squares).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cm_host.h"
+#include "cm_tc.cuh"
+
+namespace cm {
+
+namespace {
+
+constexpr int kVaThreads = 128;
+constexpr int kVaRows = 128;            // descriptors per tile (M)
+constexpr int kVaMaxC = 256;            // codewords (N <= 256)
+constexpr int kVaPolls = 1 << 24;       // bound of every mbarrier wait
+constexpr size_t kVaMinSmem = 100 * 1024;   // at most 2 CTAs per SM: their TMEM (<= 2 x 256 columns) always fits
+constexpr int kAcThreads = 256;
+
+__device__ __forceinline__ uint32_t u8x2_to_bf16x2(uint32_t w, int b0) {
+    const float f0 = __uint_as_float(0x4B000000u | ((w >> (8 * b0)) & 0xFFu)) - 8388608.f;
+    const float f1 = __uint_as_float(0x4B000000u | ((w >> (8 * (b0 + 1))) & 0xFFu)) - 8388608.f;
+    // an integer 0..255 has at most 8 significant bits: its FP32 upper half is its exact BF16
+    return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+
+// One uint8 row (8 x 16 bytes, or zeros) into row r of a K-major BF16 operand
+// tile of `rows` rows; returns the row's squared norm.
+__device__ __forceinline__ uint32_t stage_row(const uint8_t* src, bool have, unsigned char* tile, int r, int rows) {
+    uint32_t nn = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (have) v = __ldg(reinterpret_cast<const uint4*>(src) + c);
+        nn = __dp4a(v.x, v.x, nn);
+        nn = __dp4a(v.y, v.y, nn);
+        nn = __dp4a(v.z, v.z, nn);
+        nn = __dp4a(v.w, v.w, nn);
+        uint4 lo, hi;
+        lo.x = u8x2_to_bf16x2(v.x, 0); lo.y = u8x2_to_bf16x2(v.x, 2);
+        lo.z = u8x2_to_bf16x2(v.y, 0); lo.w = u8x2_to_bf16x2(v.y, 2);
+        hi.x = u8x2_to_bf16x2(v.z, 0); hi.y = u8x2_to_bf16x2(v.z, 2);
+        hi.z = u8x2_to_bf16x2(v.w, 0); hi.w = u8x2_to_bf16x2(v.w, 2);
+        *reinterpret_cast<uint4*>(tile + tc::chunk_off(r, 2 * c, rows)) = lo;
+        *reinterpret_cast<uint4*>(tile + tc::chunk_off(r, 2 * c + 1, rows)) = hi;
+    }
+    return nn;
+}
+
+__global__ void __launch_bounds__(kVaThreads, 1)
+k_vlad_assign(const uint8_t* __restrict__ desc, int64_t n_rows, const uint8_t* __restrict__ codebook, int C, int NC,
+              int tcols, uint16_t* __restrict__ assign, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* Bt = smem;                                   // NC x 256 B
+    unsigned char* At = Bt + (size_t)NC * 256;                  // 128 x 256 B
+    float* cn = reinterpret_cast<float*>(At + kVaRows * 256);   // [NC] |c|^2
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(cn + kVaMaxC);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t kLboA = (kVaRows / 8) * 128, kLboB = (uint32_t)(NC / 8) * 128;
+
+    for (int r = tid; r < NC; r += kVaThreads) {
+        const bool have = r < C;
+        const uint32_t nn = stage_row(codebook + (size_t)(have ? r : 0) * kDim, have, Bt, r, NC);
+        cn[r] = (float)nn;   // exact: below 2^24
+    }
+    if (tid == 0) tc::mbar_init(mbar, 1);
+    if (warp == 0) tc::tmem_alloc(tslot, tcols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = tc::idesc_f16(kVaRows, NC, 1);
+    const int64_t n_tiles = (n_rows + kVaRows - 1) / kVaRows;
+    uint32_t parity = 0;
+
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t row = tile * kVaRows + tid;
+        const bool have = row < n_rows;
+        stage_row(desc + (size_t)(have ? row : 0) * kDim, have, At, tid, kVaRows);
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after();
+            const uint32_t a0 = tc::smem_addr(At), b0 = tc::smem_addr(Bt);
+#pragma unroll
+            for (int ks = 0; ks < kDim / 16; ++ks)
+                tc::mma_f16(tmem, tc::smem_desc(a0 + ks * 2 * kLboA, kLboA, 128),
+                            tc::smem_desc(b0 + ks * 2 * kLboB, kLboB, 128), idesc, ks != 0);
+            tc::commit(mbar);
+        }
+        const bool ok = tc::mbar_wait(mbar, parity, kVaPolls);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            // the accumulator never completed: report, give the MMA a last bounded wait, stop
+            if (tid == 0) atomicExch(err, 1);
+            tc::mbar_wait(mbar, parity ^ 1u, kVaPolls);
+            break;
+        }
+        tc::fence_after();
+        // this thread's lane = row; argmin over c of |c|^2 - 2 x.c, ties to the smaller c
+        const uint32_t lane = tmem + ((uint32_t)(32 * warp) << 16);
+        float best = 0.f;
+        int bc = -1;
+        for (int c0 = 0; c0 < NC; c0 += 16) {
+            uint32_t v[16];
+            tc::tmem_ld16(lane + c0, v);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float d = cn[c0 + j] - 2.f * __uint_as_float(v[j]);
+                if (c0 + j < C && (bc < 0 || d < best)) {
+                    best = d;
+                    bc = c0 + j;
+                }
+            }
+        }
+        if (have) assign[row] = (uint16_t)bc;
+        tc::fence_before();
+        __syncthreads();   // TMEM and the A tile are reused by the next tile
+    }
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, tcols);
+}
+
+__global__ void __launch_bounds__(kAcThreads)
+k_vlad_accum(const uint8_t* __restrict__ desc, const int64_t* __restrict__ img_off, const uint8_t* __restrict__ codebook,
+             int C, const uint16_t* __restrict__ assign, float* __restrict__ vlad, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    int32_t* acc = reinterpret_cast<int32_t*>(smem);   // [C][128]
+    int32_t* cnt = acc + C * kDim;                      // [C]
+    double* red = reinterpret_cast<double*>(cnt + ((C + 1) & ~1));   // [kAcThreads / 32]
+    const int tid = threadIdx.x, img = blockIdx.x;
+    const int64_t r0 = img_off[img], nr = img_off[img + 1] - r0;
+    for (int e = tid; e < C * kDim; e += kAcThreads) acc[e] = 0;
+    for (int c = tid; c < C; c += kAcThreads) cnt[c] = 0;
+    __syncthreads();
+    // 8 threads per row, 16 bytes each
+    for (int64_t t = tid; t < nr * 8; t += kAcThreads) {
+        const int64_t r = t >> 3;
+        const int ch = (int)(t & 7);
+        const int c = assign[r0 + r];
+        if (c >= C) {   // cannot happen for assignments written by k_vlad_assign
+            atomicExch(err, 2);
+            continue;
+        }
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(desc + (size_t)(r0 + r) * kDim) + ch);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        int32_t* a = acc + c * kDim + ch * 16;
+#pragma unroll
+        for (int b = 0; b < 16; ++b) atomicAdd(a + b, (int32_t)((w[b >> 2] >> (8 * (b & 3))) & 0xFFu));
+        if (ch == 0) atomicAdd(cnt + c, 1);
+    }
+    __syncthreads();
+    // residuals, signed square roots (kept in place as floats), sum of squares
+    float* s = reinterpret_cast<float*>(acc);
+    double ss = 0.0;
+    for (int e = tid; e < C * kDim; e += kAcThreads) {
+        const int c = e >> 7;
+        const int32_t r = acc[e] - cnt[c] * (int32_t)codebook[e];
+        const float q = sqrtf((float)(r < 0 ? -r : r));
+        const float v = r < 0 ? -q : q;
+        s[e] = v;
+        ss += (double)v * (double)v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
+    if ((tid & 31) == 0) red[tid >> 5] = ss;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < kAcThreads / 32; ++w) tot += red[w];
+    const float inv = tot > 0.0 ? (float)(1.0 / sqrt(tot)) : 0.f;
+    float* out = vlad + (size_t)img * C * kDim;
+    for (int e = tid; e < C * kDim; e += kAcThreads) out[e] = s[e] * inv;
+}
+
+// Workspace: the error flag first (a fixed place, read by cm_vlad_status),
+// then the device copy of the image offsets, then the assignments when the
+// caller does not take them.
+struct VladWork {
+    uint64_t err, off, assign, total;
+};
+
+VladWork vlad_layout(int32_t n_images, int64_t n_rows) {
+    VladWork w{};
+    w.err = 0;
+    w.off = align_up(4);
+    w.assign = align_up(w.off + 8 * (uint64_t)(n_images + 1));
+    w.total = align_up(w.assign + 2 * (uint64_t)n_rows);
+    return w;
+}
+
+}  // namespace
+
+}  // namespace cm
+
+using namespace cm;
+
+extern "C" cm_status cm_vlad_workspace_bytes(int32_t n_images, int64_t n_rows, uint64_t* bytes) {
+    if (n_images < 0 || n_rows < 0 || !bytes) return host_fail(CM_ERR_INVALID, "cm_vlad_workspace_bytes: bad argument");
+    *bytes = vlad_layout(n_images, n_rows).total;
+    return CM_OK;
+}
+
+extern "C" cm_status cm_vlad_encode(const uint8_t* desc, const int64_t* img_off, int32_t n_images,
+                                    const uint8_t* codebook, int32_t n_codewords, void* d_work, uint64_t work_bytes,
+                                    uint16_t* assign, float* vlad, cm_stream stream) {
+    if (n_images < 0 || !img_off || n_codewords < 1 || n_codewords > kVaMaxC || !codebook || !d_work ||
+        (n_images > 0 && !vlad))
+        return host_fail(CM_ERR_INVALID, "cm_vlad_encode: bad argument");
+    if (img_off[0] != 0) return host_fail(CM_ERR_INVALID, "cm_vlad_encode: img_off[0] must be 0");
+    for (int32_t i = 0; i < n_images; ++i)
+        if (img_off[i + 1] < img_off[i]) return host_fail(CM_ERR_INVALID, "cm_vlad_encode: img_off not ascending");
+    const int64_t n_rows = img_off[n_images];
+    if (n_rows > 0 && !desc) return host_fail(CM_ERR_INVALID, "cm_vlad_encode: desc is NULL");
+    const VladWork w = vlad_layout(n_images, n_rows);
+    if (work_bytes < w.total || (reinterpret_cast<uintptr_t>(d_work) & (kAlign - 1)))
+        return host_fail(CM_ERR_BUDGET, "cm_vlad_encode: workspace smaller than cm_vlad_workspace_bytes or not 256-byte aligned");
+    if (n_images == 0) return CM_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* base = static_cast<unsigned char*>(d_work);
+    int64_t* off = reinterpret_cast<int64_t*>(base + w.off);
+    int* err = reinterpret_cast<int*>(base + w.err);
+    uint16_t* asg = assign ? assign : reinterpret_cast<uint16_t*>(base + w.assign);
+    CM_CUDA(cudaMemcpyAsync(off, img_off, 8 * (size_t)(n_images + 1), cudaMemcpyHostToDevice, s));
+    CM_CUDA(cudaMemsetAsync(err, 0, 4, s));
+    int dev = 0, sms = 148;
+    CM_CUDA(cudaGetDevice(&dev));
+    CM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (n_rows > 0) {
+        const int NC = (n_codewords + 15) / 16 * 16;
+        int tcols = 32;
+        while (tcols < NC) tcols <<= 1;
+        size_t smem = (size_t)NC * 256 + kVaRows * 256 + kVaMaxC * 4 + 64;
+        if (smem < kVaMinSmem) smem = kVaMinSmem;
+        CM_CUDA(cudaFuncSetAttribute(k_vlad_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int64_t n_tiles = (n_rows + kVaRows - 1) / kVaRows;
+        const int grid = (int)std::min<int64_t>(n_tiles, 2 * (int64_t)sms);
+        k_vlad_assign<<<grid, kVaThreads, smem, s>>>(desc, n_rows, codebook, n_codewords, NC, tcols, asg, err);
+        CM_CUDA(cudaGetLastError());
+    }
+    const size_t smem2 = (size_t)n_codewords * kDim * 4 + ((n_codewords + 1) & ~1) * 4 + (kAcThreads / 32) * 8;
+    CM_CUDA(cudaFuncSetAttribute(k_vlad_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+    k_vlad_accum<<<n_images, kAcThreads, smem2, s>>>(desc, off, codebook, n_codewords, asg, vlad, err);
+    CM_CUDA(cudaGetLastError());
+    return CM_OK;
+}
+
+extern "C" cm_status cm_vlad_status(const void* d_work, cm_stream stream) {
+    if (!d_work || (reinterpret_cast<uintptr_t>(d_work) & (kAlign - 1)))
+        return host_fail(CM_ERR_INVALID, "cm_vlad_status: bad workspace");
+    int flag = 0;
+    CM_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    CM_CUDA(cudaMemcpy(&flag, d_work, 4, cudaMemcpyDeviceToHost));
+    if (flag == 1) return host_fail(CM_ERR_TIMEOUT, "cm_vlad_encode: a bounded device wait gave up");
+    if (flag != 0) return host_fail(CM_ERR_STATE, "cm_vlad_encode: a codeword index out of range was met");
+    return CM_OK;
+}
