@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--workload", default="grid5000", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--rerank", default="bf16", choices=["fp32", "int", "bf16", "fp8"], help="headline form")
     ap.add_argument("--forms", default="all", choices=["all", "one"], help="also time the other rerank forms")
+    ap.add_argument("--vlad-codewords", type=int, default=128,
+                    help="codebook size of the VLAD encoding timed beside the matching (0: skip)")
     ap.add_argument("--K", type=int, default=8)
     ap.add_argument("--tune-pairs", type=int, default=120,
                     help="pairs of the first block row the autotuner times (0: no tuning)")
@@ -288,6 +290,50 @@ def device_forms(args, wl, desc_dev, rows, stream, dev, world, forms):
     return res
 
 
+def vlad_encoding(args, wl, desc_dev, host, stream, world, dev):
+    """VLAD encoding of every image of the workload (the retrieval front end,
+    Sec. 2.1) with the descriptors resident: cm_vlad_encode timed with CUDA
+    events over the steps, its two kernels' bounds stated, and the FP64 oracle
+    timed on one image for the CPU figure."""
+    import torch
+    import paper_2505_22089_b300 as cm
+    from oracle import vlad as ovlad
+    C = args.vlad_codewords
+    rng = np.random.default_rng(77)
+    cb_host = host[np.sort(rng.choice(len(host), C, replace=False))].copy()   # stand-in for k-means centroids
+    cb = torch.from_numpy(cb_host).to(dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            v, _ = cm.vlad_encode(desc_dev, wl.n_desc, cb, stream=stream, check_status=False)
+        stream.synchronize()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(args.steps):
+            v, _ = cm.vlad_encode(desc_dev, wl.n_desc, cb, stream=stream, check_status=False)
+        stop.record(stream)
+        stop.synchronize()
+    ms = _sync_ms(start.elapsed_time(stop) / args.steps, world, dev)
+    n = int(wl.total_desc)
+    NC = (C + 15) // 16 * 16
+    flops = 2.0 * 128 * NC * n
+    hbm = 2 * (128 + 2) * n + 4 * C * 128 * wl.n_images      # both kernels read the rows and the assignments
+    norms = v.norm(dim=1).cpu().numpy()
+    t0 = time.perf_counter()
+    i0 = int(np.argmax(wl.n_desc > 0))
+    off = wl.row_off
+    ovlad.encode(host[off[i0]:off[i0 + 1]], [wl.n_desc[i0]], cb_host)
+    cpu_s = time.perf_counter() - t0
+    return {"codewords": C, "images": wl.n_images, "descriptors": n, "ms_per_step": ms,
+            "images_per_s": wl.n_images * world / (ms / 1e3), "descriptors_per_s": n * world / (ms / 1e3),
+            "tensor_tflops_if_assign_alone": flops / (ms / 1e3) / 1e12,
+            "hbm_gbs_if_streaming_alone": hbm / (ms / 1e3) / 1e9,
+            "algorithmic": {"assign_flop": flops, "hbm_bytes": hbm},
+            "unit_norm": bool(np.allclose(norms[wl.n_desc > 0], 1.0, atol=1e-5)),
+            "cpu_oracle_images_per_s": 1.0 / cpu_s, "cpu_oracle_sample": "1 image of %d rows, FP64 numpy"
+                                                                        % int(wl.n_desc[i0]),
+            "codebook": "C rows sampled from the workload (seeded), a stand-in for k-means centroids"}
+
+
 def pipeline_e2e(args, wl, host, kp, sums, stream, world, dev):
     """End to end through the public pipeline call (cm_run_schedule): per block
     row, H2D of the row's new images from pinned host memory, hashing, one fused
@@ -420,6 +466,7 @@ def run_ours(args, rank, world, local):
                              if args.forms == "all" else [])
     desc_dev = host.to(dev, non_blocking=False)
     fr = device_forms(args, wl, desc_dev, rows, stream, dev, world, forms)
+    vl = vlad_encoding(args, wl, desc_dev, host.numpy(), stream, world, dev) if args.vlad_codewords > 0 else None
     head = fr[args.rerank]
     gpu_rows, sums = head.pop("_gpu_rows"), head.pop("_sums")
     del desc_dev
@@ -478,6 +525,7 @@ def run_ours(args, rank, world, local):
         "schedules": schedule_comparison(wl, p, int(args.budget_gb * 2 ** 30), args.block_images),
         "gpu_launches": args.steps * head["graph_kernels"],
         "roofline": roofline,
+        "vlad": vl,
         "clocks": head["clocks"],
     }
     if cpu is not None:

@@ -31,40 +31,46 @@ constexpr int kVaThreads = 128;
 constexpr int kVaRows = 128;            // descriptors per tile (M)
 constexpr int kVaMaxC = 256;            // codewords (N <= 256)
 constexpr int kVaPolls = 1 << 24;       // bound of every mbarrier wait
-constexpr size_t kVaMinSmem = 100 * 1024;   // at most 2 CTAs per SM: their TMEM (<= 2 x 256 columns) always fits
-constexpr int kAcThreads = 256;
+constexpr int kAcThreads = 512;
 
+// Bytes b0 and b0+1 of w as two BF16 values.  The byte is placed under the
+// exponent of 2^23 by one byte permute (2^23 + b as FP32) and 2^23 subtracted;
+// an integer 0..255 has at most 8 significant bits, so the FP32 upper half is
+// its exact BF16.
 __device__ __forceinline__ uint32_t u8x2_to_bf16x2(uint32_t w, int b0) {
-    const float f0 = __uint_as_float(0x4B000000u | ((w >> (8 * b0)) & 0xFFu)) - 8388608.f;
-    const float f1 = __uint_as_float(0x4B000000u | ((w >> (8 * (b0 + 1))) & 0xFFu)) - 8388608.f;
-    // an integer 0..255 has at most 8 significant bits: its FP32 upper half is its exact BF16
+    const float f0 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540 + b0)) - 8388608.f;
+    const float f1 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7541 + b0)) - 8388608.f;
     return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
 }
 
-// One uint8 row (8 x 16 bytes, or zeros) into row r of a K-major BF16 operand
-// tile of `rows` rows; returns the row's squared norm.
-__device__ __forceinline__ uint32_t stage_row(const uint8_t* src, bool have, unsigned char* tile, int r, int rows) {
+// One uint8 row (8 x 16 bytes, or zeros) from global memory.
+__device__ __forceinline__ void load_row(const uint8_t* src, bool have, uint4 (&v)[8]) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = have ? __ldg(reinterpret_cast<const uint4*>(src) + c) : make_uint4(0, 0, 0, 0);
+}
+
+// The row into row r of a K-major BF16 operand tile of `rows` rows; returns
+// its squared norm.
+__device__ __forceinline__ uint32_t stage_row(const uint4 (&v)[8], unsigned char* tile, int r, int rows) {
     uint32_t nn = 0;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (have) v = __ldg(reinterpret_cast<const uint4*>(src) + c);
-        nn = __dp4a(v.x, v.x, nn);
-        nn = __dp4a(v.y, v.y, nn);
-        nn = __dp4a(v.z, v.z, nn);
-        nn = __dp4a(v.w, v.w, nn);
+        nn = __dp4a(v[c].x, v[c].x, nn);
+        nn = __dp4a(v[c].y, v[c].y, nn);
+        nn = __dp4a(v[c].z, v[c].z, nn);
+        nn = __dp4a(v[c].w, v[c].w, nn);
         uint4 lo, hi;
-        lo.x = u8x2_to_bf16x2(v.x, 0); lo.y = u8x2_to_bf16x2(v.x, 2);
-        lo.z = u8x2_to_bf16x2(v.y, 0); lo.w = u8x2_to_bf16x2(v.y, 2);
-        hi.x = u8x2_to_bf16x2(v.z, 0); hi.y = u8x2_to_bf16x2(v.z, 2);
-        hi.z = u8x2_to_bf16x2(v.w, 0); hi.w = u8x2_to_bf16x2(v.w, 2);
+        lo.x = u8x2_to_bf16x2(v[c].x, 0); lo.y = u8x2_to_bf16x2(v[c].x, 2);
+        lo.z = u8x2_to_bf16x2(v[c].y, 0); lo.w = u8x2_to_bf16x2(v[c].y, 2);
+        hi.x = u8x2_to_bf16x2(v[c].z, 0); hi.y = u8x2_to_bf16x2(v[c].z, 2);
+        hi.z = u8x2_to_bf16x2(v[c].w, 0); hi.w = u8x2_to_bf16x2(v[c].w, 2);
         *reinterpret_cast<uint4*>(tile + tc::chunk_off(r, 2 * c, rows)) = lo;
         *reinterpret_cast<uint4*>(tile + tc::chunk_off(r, 2 * c + 1, rows)) = hi;
     }
     return nn;
 }
 
-__global__ void __launch_bounds__(kVaThreads, 1)
+__global__ void __launch_bounds__(kVaThreads, 3)
 k_vlad_assign(const uint8_t* __restrict__ desc, int64_t n_rows, const uint8_t* __restrict__ codebook, int C, int NC,
               int tcols, uint16_t* __restrict__ assign, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -77,9 +83,10 @@ k_vlad_assign(const uint8_t* __restrict__ desc, int64_t n_rows, const uint8_t* _
     const uint32_t kLboA = (kVaRows / 8) * 128, kLboB = (uint32_t)(NC / 8) * 128;
 
     for (int r = tid; r < NC; r += kVaThreads) {
-        const bool have = r < C;
-        const uint32_t nn = stage_row(codebook + (size_t)(have ? r : 0) * kDim, have, Bt, r, NC);
-        cn[r] = (float)nn;   // exact: below 2^24
+        uint4 v[8];
+        load_row(codebook + (size_t)(r < C ? r : 0) * kDim, r < C, v);
+        const uint32_t nn = stage_row(v, Bt, r, NC);
+        cn[r] = r < C ? (float)nn : __uint_as_float(0x7F800000u);   // exact below 2^24; padding: +inf
     }
     if (tid == 0) tc::mbar_init(mbar, 1);
     if (warp == 0) tc::tmem_alloc(tslot, tcols);
@@ -91,10 +98,21 @@ k_vlad_assign(const uint8_t* __restrict__ desc, int64_t n_rows, const uint8_t* _
     const int64_t n_tiles = (n_rows + kVaRows - 1) / kVaRows;
     uint32_t parity = 0;
 
+    // the next tile's row is loaded while this tile's MMA and epilogue run
+    uint4 raw[8];
+    {
+        const int64_t row = (int64_t)blockIdx.x * kVaRows + tid;
+        load_row(desc + (size_t)(row < n_rows ? row : 0) * kDim, blockIdx.x < n_tiles && row < n_rows, raw);
+    }
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t row = tile * kVaRows + tid;
         const bool have = row < n_rows;
-        stage_row(desc + (size_t)(have ? row : 0) * kDim, have, At, tid, kVaRows);
+        stage_row(raw, At, tid, kVaRows);
+        {
+            const int64_t nrow = (tile + gridDim.x) * kVaRows + tid;
+            const bool nhave = tile + gridDim.x < n_tiles && nrow < n_rows;
+            load_row(desc + (size_t)(nhave ? nrow : 0) * kDim, nhave, raw);
+        }
         tc::fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
@@ -116,20 +134,19 @@ k_vlad_assign(const uint8_t* __restrict__ desc, int64_t n_rows, const uint8_t* _
         }
         tc::fence_after();
         // this thread's lane = row; argmin over c of |c|^2 - 2 x.c, ties to the smaller c
+        // (padded codewords carry |c|^2 = +inf and never win)
         const uint32_t lane = tmem + ((uint32_t)(32 * warp) << 16);
-        float best = 0.f;
-        int bc = -1;
+        float best = __uint_as_float(0x7F800000u);
+        int bc = 0;
         for (int c0 = 0; c0 < NC; c0 += 16) {
             uint32_t v[16];
             tc::tmem_ld16(lane + c0, v);
             tc::tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const float d = cn[c0 + j] - 2.f * __uint_as_float(v[j]);
-                if (c0 + j < C && (bc < 0 || d < best)) {
-                    best = d;
-                    bc = c0 + j;
-                }
+                const float d = fmaf(-2.f, __uint_as_float(v[j]), cn[c0 + j]);   // exact: integers below 2^24
+                bc = d < best ? c0 + j : bc;
+                best = fminf(best, d);
             }
         }
         if (have) assign[row] = (uint16_t)bc;
@@ -152,21 +169,31 @@ k_vlad_accum(const uint8_t* __restrict__ desc, const int64_t* __restrict__ img_o
     for (int e = tid; e < C * kDim; e += kAcThreads) acc[e] = 0;
     for (int c = tid; c < C; c += kAcThreads) cnt[c] = 0;
     __syncthreads();
-    // 8 threads per row, 16 bytes each
-    for (int64_t t = tid; t < nr * 8; t += kAcThreads) {
-        const int64_t r = t >> 3;
-        const int ch = (int)(t & 7);
-        const int c = assign[r0 + r];
-        if (c >= C) {   // cannot happen for assignments written by k_vlad_assign
-            atomicExch(err, 2);
-            continue;
-        }
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(desc + (size_t)(r0 + r) * kDim) + ch);
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-        int32_t* a = acc + c * kDim + ch * 16;
+    // A warp takes 32 consecutive rows: lane l loads the l-th word of each
+    // (32 independent coalesced loads in flight) and the row's codeword; then
+    // per row, lane l gathers bytes l, l+32, l+64, l+96 by shuffles and adds
+    // them, so each atomic instruction touches 32 consecutive words.
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int64_t g = (int64_t)warp * 32; g < nr; g += kAcThreads) {
+        const int rows = nr - g < 32 ? (int)(nr - g) : 32;
+        uint32_t w[32];
 #pragma unroll
-        for (int b = 0; b < 16; ++b) atomicAdd(a + b, (int32_t)((w[b >> 2] >> (8 * (b & 3))) & 0xFFu));
-        if (ch == 0) atomicAdd(cnt + c, 1);
+        for (int k = 0; k < 32; ++k)
+            w[k] = k < rows ? __ldg(reinterpret_cast<const uint32_t*>(desc + (size_t)(r0 + g + k) * kDim) + lane) : 0u;
+        const int cl = lane < rows ? assign[r0 + g + lane] : 0;
+        if (lane < rows && cl >= C) atomicExch(err, 2);   // cannot happen for k_vlad_assign's output
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const int c = __shfl_sync(0xFFFFFFFFu, cl, k);
+            if (k >= rows || c >= C) continue;   // uniform over the warp
+            int32_t* a = acc + c * kDim + lane;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t word = __shfl_sync(0xFFFFFFFFu, w[k], (lane >> 2) + 8 * q);
+                atomicAdd(a + 32 * q, (int32_t)((word >> (8 * (lane & 3))) & 0xFFu));
+            }
+            if (lane == 0) atomicAdd(cnt + c, 1);
+        }
     }
     __syncthreads();
     // residuals, signed square roots (kept in place as floats), sum of squares
@@ -248,11 +275,13 @@ extern "C" cm_status cm_vlad_encode(const uint8_t* desc, const int64_t* img_off,
         const int NC = (n_codewords + 15) / 16 * 16;
         int tcols = 32;
         while (tcols < NC) tcols <<= 1;
+        // at most 512 / tcols CTAs per SM, so that their TMEM allocations always fit together
+        const size_t per_sm = 228 * 1024, max_ctas = 512 / tcols;
         size_t smem = (size_t)NC * 256 + kVaRows * 256 + kVaMaxC * 4 + 64;
-        if (smem < kVaMinSmem) smem = kVaMinSmem;
+        smem = std::max(smem, per_sm / (max_ctas + 1) + 1024);
         CM_CUDA(cudaFuncSetAttribute(k_vlad_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int64_t n_tiles = (n_rows + kVaRows - 1) / kVaRows;
-        const int grid = (int)std::min<int64_t>(n_tiles, 2 * (int64_t)sms);
+        const int grid = (int)std::min<int64_t>(n_tiles, (int64_t)std::min<size_t>(max_ctas, per_sm / smem) * sms);
         k_vlad_assign<<<grid, kVaThreads, smem, s>>>(desc, n_rows, codebook, n_codewords, NC, tcols, asg, err);
         CM_CUDA(cudaGetLastError());
     }
