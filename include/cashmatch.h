@@ -428,14 +428,42 @@ cm_status cm_vlad_workspace_bytes(int32_t n_images, int64_t n_rows, uint64_t* by
  *  - d_work / work_bytes: device workspace of cm_vlad_workspace_bytes, 256-byte aligned.
  *  - assign (optional): device uint16 [n_rows], the codeword of each row.
  *  - vlad: device float [n_images][n_codewords * 128].
- * Asynchronous on `stream`; cm_vlad_status(d_work, stream) waits for it and
+ * Asynchronous on `stream`; cm_workspace_status(d_work, stream) waits for it and
  * reports CM_ERR_TIMEOUT if a bounded device wait gave up.  Errors:
  * CM_ERR_INVALID (bad argument), CM_ERR_BUDGET (workspace too small), CM_ERR_CUDA. */
 cm_status cm_vlad_encode(const uint8_t* desc, const int64_t* img_off, int32_t n_images, const uint8_t* codebook,
                          int32_t n_codewords, void* d_work, uint64_t work_bytes, uint16_t* assign, float* vlad,
                          cm_stream stream);
-/* Synchronises `stream` and reads the device status of the last cm_vlad_encode on d_work. */
-cm_status cm_vlad_status(const void* d_work, cm_stream stream);
+/* Synchronises `stream` and reads the device status of the last call that used
+ * the workspace d_work (cm_vlad_encode, cm_nn_pairs): CM_ERR_TIMEOUT if a
+ * bounded device wait gave up, CM_ERR_STATE if a device-side bounds check
+ * failed, else CM_OK. */
+cm_status cm_workspace_status(const void* d_work, cm_stream stream);
+
+/* ---- exhaustive nearest neighbours (quality ceiling) --------------------- */
+/* Device workspace of cm_nn_pairs. */
+cm_status cm_nn_workspace_bytes(int32_t n_images, int64_t n_pairs, uint64_t* bytes);
+/* Exhaustive nearest neighbours with the exact ratio test for each pair: for
+ * every query x of image i, q1 and q2 = the two smallest (d^2, j) over ALL
+ * rows y of image j (d^2 exact squared Euclidean distance on the uint8 rows,
+ * ties to the smaller j), and best_j = j1 when den^2 d1^2 < num^2 d2^2 (no
+ * match with fewer than 2 rows in j).  These are the matches cascade hashing
+ * gives with every database point a candidate (Sec. 2.3.1 with K = N_J): the
+ * ceiling its recall is measured against.  d^2 = |x|^2 + |y|^2 - 2 x.y with
+ * x.y from BF16 tensor-core products, exact on integers.
+ *  - desc: device uint8 [rows][128], all images concatenated; img_off: host
+ *    int64 [n_images + 1], img_off[0] = 0, ascending, <= 65535 rows per image.
+ *  - pairs: host, n_pairs entries; output rows: pair k owns rows
+ *    row_off[k] .. row_off[k] + n_i - 1, row_off the prefix sum of the query
+ *    counts (the layout of a match plan).
+ *  - best_j (required), d1sq, d2sq (optional): device outputs per row;
+ *    0xFFFFFFFF where q1 / q2 do not exist.
+ *  - d_work / work_bytes: cm_nn_workspace_bytes, 256-byte aligned.
+ * Asynchronous on `stream`; cm_workspace_status reports device-side failures.
+ * Errors: CM_ERR_INVALID, CM_ERR_BUDGET (workspace), CM_ERR_CUDA. */
+cm_status cm_nn_pairs(const uint8_t* desc, const int64_t* img_off, int32_t n_images, const cm_pair* pairs,
+                      int64_t n_pairs, int32_t ratio_num, int32_t ratio_den, void* d_work, uint64_t work_bytes,
+                      int32_t* best_j, uint32_t* d1sq, uint32_t* d2sq, cm_stream stream);
 
 /* ---- autotuning of the match launch -------------------------------------- */
 typedef struct cm_tune_result {

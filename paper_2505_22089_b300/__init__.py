@@ -52,7 +52,7 @@ EXPORTS = [
     "cm_match_plan_compact", "cm_match_plan_mutual", "cm_match_plan_destroy", "cm_match_pairs", "cm_sequence_create", "cm_sequence_launch",
     "cm_sequence_kernels", "cm_sequence_destroy", "cm_schedule_arena_bytes", "cm_pipeline_workspace_bytes", "cm_run_schedule",
     "cm_verify_affine", "cm_affine_verify_cb", "cm_sao_filter", "cm_vlad_workspace_bytes", "cm_vlad_encode",
-    "cm_vlad_status", "cm_autotune", "cm_match_pair_noalloc",
+    "cm_workspace_status", "cm_nn_workspace_bytes", "cm_nn_pairs", "cm_autotune", "cm_match_pair_noalloc",
 ]
 
 
@@ -181,7 +181,9 @@ def lib():
             "cm_sao_filter": (i32, [vp, vp, i64, vp, i32, ctypes.c_float, vp, vp, ctypes.POINTER(i64)]),
             "cm_vlad_workspace_bytes": (i32, [i32, i64, ctypes.POINTER(u64)]),
             "cm_vlad_encode": (i32, [vp, vp, i32, vp, i32, vp, u64, vp, vp, vp]),
-            "cm_vlad_status": (i32, [vp, vp]),
+            "cm_workspace_status": (i32, [vp, vp]),
+            "cm_nn_workspace_bytes": (i32, [i32, i64, ctypes.POINTER(u64)]),
+            "cm_nn_pairs": (i32, [vp, vp, i32, vp, i64, i32, i32, vp, u64, vp, vp, vp, vp]),
             "cm_autotune": (i32, [vp, vp, i64, vp, i32, ctypes.c_float, vp, ctypes.POINTER(TuneResult)]),
         }
         for name, (res, args) in sig.items():
@@ -346,9 +348,36 @@ def vlad_encode(desc, n_desc, codebook, stream=None, want_assign: bool = False, 
     check(lib().cm_vlad_encode(_ptr(desc), off.ctypes.data, len(nd), _ptr(codebook), C, ctypes.c_void_p(wbase),
                                int(ws.value), _ptr(asg), _ptr(out), _stream(stream)))
     if check_status:
-        check(lib().cm_vlad_status(ctypes.c_void_p(wbase), _stream(stream)))
+        check(lib().cm_workspace_status(ctypes.c_void_p(wbase), _stream(stream)))
     a = asg.to(torch.int32) & 0xFFFF if asg is not None else None
     return out, a
+
+
+def nn_pairs(desc, n_desc, pairs, ratio=(4, 5), stream=None, check_status: bool = True):
+    """cm_nn_pairs: exhaustive nearest neighbours with the exact ratio test.
+    desc: CUDA uint8 [n][128] (all images), n_desc: rows per image, pairs:
+    [n_pairs][2].  Returns (best_j, d1sq, d2sq) CUDA tensors (int32; the
+    squared distances as int64 with 0xFFFFFFFF for a missing q1 / q2) and the
+    per-pair row offsets."""
+    import torch
+    nd = np.ascontiguousarray(n_desc, dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(nd)]).astype(np.int64)
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    rows = np.concatenate([[0], np.cumsum(nd[pr[:, 0]])]).astype(np.int64) if len(pr) else np.zeros(1, np.int64)
+    ws = ctypes.c_uint64()
+    check(lib().cm_nn_workspace_bytes(len(nd), len(pr), ctypes.byref(ws)))
+    work = torch.empty(int(ws.value) + 256, dtype=torch.uint8, device=desc.device)
+    wbase = (work.data_ptr() + 255) // 256 * 256
+    n = int(rows[-1])
+    best = torch.empty(max(n, 1), dtype=torch.int32, device=desc.device)
+    d1 = torch.empty(max(n, 1), dtype=torch.int32, device=desc.device)
+    d2 = torch.empty(max(n, 1), dtype=torch.int32, device=desc.device)
+    check(lib().cm_nn_pairs(_ptr(desc), off.ctypes.data, len(nd), pr.ctypes.data if len(pr) else None, len(pr),
+                            int(ratio[0]), int(ratio[1]), ctypes.c_void_p(wbase), int(ws.value), _ptr(best), _ptr(d1),
+                            _ptr(d2), _stream(stream)))
+    if check_status:
+        check(lib().cm_workspace_status(ctypes.c_void_p(wbase), _stream(stream)))
+    return best[:n], d1[:n].to(torch.int64) & 0xFFFFFFFF, d2[:n].to(torch.int64) & 0xFFFFFFFF, rows
 
 
 def _cudart():

@@ -21,6 +21,7 @@
 #include <cstdint>
 
 #include "cm_host.h"
+#include "cm_stage.cuh"
 #include "cm_tc.cuh"
 
 namespace cm {
@@ -33,42 +34,7 @@ constexpr int kVaMaxC = 256;            // codewords (N <= 256)
 constexpr int kVaPolls = 1 << 24;       // bound of every mbarrier wait
 constexpr int kAcThreads = 512;
 
-// Bytes b0 and b0+1 of w as two BF16 values.  The byte is placed under the
-// exponent of 2^23 by one byte permute (2^23 + b as FP32) and 2^23 subtracted;
-// an integer 0..255 has at most 8 significant bits, so the FP32 upper half is
-// its exact BF16.
-__device__ __forceinline__ uint32_t u8x2_to_bf16x2(uint32_t w, int b0) {
-    const float f0 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540 + b0)) - 8388608.f;
-    const float f1 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7541 + b0)) - 8388608.f;
-    return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
-}
-
-// One uint8 row (8 x 16 bytes, or zeros) from global memory.
-__device__ __forceinline__ void load_row(const uint8_t* src, bool have, uint4 (&v)[8]) {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) v[c] = have ? __ldg(reinterpret_cast<const uint4*>(src) + c) : make_uint4(0, 0, 0, 0);
-}
-
-// The row into row r of a K-major BF16 operand tile of `rows` rows; returns
-// its squared norm.
-__device__ __forceinline__ uint32_t stage_row(const uint4 (&v)[8], unsigned char* tile, int r, int rows) {
-    uint32_t nn = 0;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        nn = __dp4a(v[c].x, v[c].x, nn);
-        nn = __dp4a(v[c].y, v[c].y, nn);
-        nn = __dp4a(v[c].z, v[c].z, nn);
-        nn = __dp4a(v[c].w, v[c].w, nn);
-        uint4 lo, hi;
-        lo.x = u8x2_to_bf16x2(v[c].x, 0); lo.y = u8x2_to_bf16x2(v[c].x, 2);
-        lo.z = u8x2_to_bf16x2(v[c].y, 0); lo.w = u8x2_to_bf16x2(v[c].y, 2);
-        hi.x = u8x2_to_bf16x2(v[c].z, 0); hi.y = u8x2_to_bf16x2(v[c].z, 2);
-        hi.z = u8x2_to_bf16x2(v[c].w, 0); hi.w = u8x2_to_bf16x2(v[c].w, 2);
-        *reinterpret_cast<uint4*>(tile + tc::chunk_off(r, 2 * c, rows)) = lo;
-        *reinterpret_cast<uint4*>(tile + tc::chunk_off(r, 2 * c + 1, rows)) = hi;
-    }
-    return nn;
-}
+using stage::load_row;
 
 __global__ void __launch_bounds__(kVaThreads, 3)
 k_vlad_assign(const uint8_t* __restrict__ desc, int64_t n_rows, const uint8_t* __restrict__ codebook, int C, int NC,
@@ -80,12 +46,11 @@ k_vlad_assign(const uint8_t* __restrict__ desc, int64_t n_rows, const uint8_t* _
     uint64_t* mbar = reinterpret_cast<uint64_t*>(cn + kVaMaxC);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t kLboA = (kVaRows / 8) * 128, kLboB = (uint32_t)(NC / 8) * 128;
 
     for (int r = tid; r < NC; r += kVaThreads) {
         uint4 v[8];
         load_row(codebook + (size_t)(r < C ? r : 0) * kDim, r < C, v);
-        const uint32_t nn = stage_row(v, Bt, r, NC);
+        const uint32_t nn = stage::store_row(v, Bt, r, NC);
         cn[r] = r < C ? (float)nn : __uint_as_float(0x7F800000u);   // exact below 2^24; padding: +inf
     }
     if (tid == 0) tc::mbar_init(mbar, 1);
@@ -94,7 +59,6 @@ k_vlad_assign(const uint8_t* __restrict__ desc, int64_t n_rows, const uint8_t* _
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t idesc = tc::idesc_f16(kVaRows, NC, 1);
     const int64_t n_tiles = (n_rows + kVaRows - 1) / kVaRows;
     uint32_t parity = 0;
 
@@ -107,7 +71,7 @@ k_vlad_assign(const uint8_t* __restrict__ desc, int64_t n_rows, const uint8_t* _
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t row = tile * kVaRows + tid;
         const bool have = row < n_rows;
-        stage_row(raw, At, tid, kVaRows);
+        stage::store_row(raw, At, tid, kVaRows);
         {
             const int64_t nrow = (tile + gridDim.x) * kVaRows + tid;
             const bool nhave = tile + gridDim.x < n_tiles && nrow < n_rows;
@@ -117,11 +81,7 @@ k_vlad_assign(const uint8_t* __restrict__ desc, int64_t n_rows, const uint8_t* _
         __syncthreads();
         if (tid == 0) {
             tc::fence_after();
-            const uint32_t a0 = tc::smem_addr(At), b0 = tc::smem_addr(Bt);
-#pragma unroll
-            for (int ks = 0; ks < kDim / 16; ++ks)
-                tc::mma_f16(tmem, tc::smem_desc(a0 + ks * 2 * kLboA, kLboA, 128),
-                            tc::smem_desc(b0 + ks * 2 * kLboB, kLboB, 128), idesc, ks != 0);
+            stage::mma_128xN(tmem, At, Bt, NC);
             tc::commit(mbar);
         }
         const bool ok = tc::mbar_wait(mbar, parity, kVaPolls);
@@ -218,7 +178,7 @@ k_vlad_accum(const uint8_t* __restrict__ desc, const int64_t* __restrict__ img_o
     for (int e = tid; e < C * kDim; e += kAcThreads) out[e] = s[e] * inv;
 }
 
-// Workspace: the error flag first (a fixed place, read by cm_vlad_status),
+// Workspace: the error flag first (a fixed place, read by cm_workspace_status),
 // then the device copy of the image offsets, then the assignments when the
 // caller does not take them.
 struct VladWork {
@@ -292,13 +252,13 @@ extern "C" cm_status cm_vlad_encode(const uint8_t* desc, const int64_t* img_off,
     return CM_OK;
 }
 
-extern "C" cm_status cm_vlad_status(const void* d_work, cm_stream stream) {
+extern "C" cm_status cm_workspace_status(const void* d_work, cm_stream stream) {
     if (!d_work || (reinterpret_cast<uintptr_t>(d_work) & (kAlign - 1)))
-        return host_fail(CM_ERR_INVALID, "cm_vlad_status: bad workspace");
+        return host_fail(CM_ERR_INVALID, "cm_workspace_status: bad workspace");
     int flag = 0;
     CM_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
     CM_CUDA(cudaMemcpy(&flag, d_work, 4, cudaMemcpyDeviceToHost));
-    if (flag == 1) return host_fail(CM_ERR_TIMEOUT, "cm_vlad_encode: a bounded device wait gave up");
-    if (flag != 0) return host_fail(CM_ERR_STATE, "cm_vlad_encode: a codeword index out of range was met");
+    if (flag == 1) return host_fail(CM_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (flag != 0) return host_fail(CM_ERR_STATE, "a device-side bounds check failed");
     return CM_OK;
 }
