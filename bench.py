@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--plain-pairs", type=int, default=200, help="pairs timed in the plain per-pair form")
     ap.add_argument("--oracle-pairs", type=int, default=12, help="pairs in the CPU-oracle sample")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--nn-pairs", type=int, default=2, help="pairs of the CPU leg also matched exhaustively")
+    ap.add_argument("--nn-pairs", type=int, default=64,
+                    help="sampled pairs matched exhaustively on the tensor cores (recall ceiling, L/K sweep); 0: skip")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default=None, help="GXxGY: a smaller grid of the same per-image shape (profiling)")
     return ap.parse_args()
@@ -466,9 +467,13 @@ def run_ours(args, rank, world, local):
                              if args.forms == "all" else [])
     desc_dev = host.to(dev, non_blocking=False)
     fr = device_forms(args, wl, desc_dev, rows, stream, dev, world, forms)
-    vl = vlad_encoding(args, wl, desc_dev, host.numpy(), stream, world, dev) if args.vlad_codewords > 0 else None
     head = fr[args.rerank]
     gpu_rows, sums = head.pop("_gpu_rows"), head.pop("_sums")
+    vl = vlad_encoding(args, wl, desc_dev, host.numpy(), stream, world, dev) if args.vlad_codewords > 0 else None
+    ceiling = sweep = None
+    if args.nn_pairs > 0:
+        ceiling, sweep = exhaustive_leg(args, wl, desc_dev, host.numpy(), sums, pairs, gpu_rows, stream, world, dev,
+                                        float(peaks()[0].get("bf16_tflops", 1800.0)))
     del desc_dev
     torch.cuda.empty_cache()
     ms = head["ms_per_step"]
@@ -526,6 +531,8 @@ def run_ours(args, rank, world, local):
         "gpu_launches": args.steps * head["graph_kernels"],
         "roofline": roofline,
         "vlad": vl,
+        "exhaustive_nn": ceiling,
+        "quality_sweep": sweep,
         "clocks": head["clocks"],
     }
     if cpu is not None:
@@ -590,44 +597,11 @@ def cpu_baseline_and_agreement(args, wl, desc, sums, pairs, rows, gpu_rows):
         union += len(gm | om)
         ng += len(gm)
         no += len(om)
-    ceiling = sweep = None
-    if args.nn_pairs > 0:
-        t1 = time.perf_counter()
-        nn_sel = sel[: args.nn_pairs]
-        exact = {int(k): exhaustive_nn(wl, desc, pairs[k]) for k in nn_sel}
-        ceiling = exhaustive_nn_quality(wl, desc, pairs, nn_sel, gpu_rows, exact)
-        sweep = quality_sweep(wl, desc, sums, pairs, nn_sel, exact, gpu_rows, args.K)
-        ceiling["seconds"] = round(time.perf_counter() - t1, 1)
     return {"cpu_baseline": {"value": len(sel) / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                              "sample": "%d of %d pairs, each: hash both images (FP64) + match; centring sums "
                                        "given" % (len(sel), len(pairs))},
             "pairs_checked": int(len(sel)), "match_set_jaccard": inter / union if union else 1.0,
-            "per_query_agreement": same / total if total else 1.0, "gpu_matches": ng, "oracle_matches": no,
-            "exhaustive_nn": ceiling, "quality_sweep": sweep}
-
-
-def exhaustive_nn(wl, desc, pair):
-    """Exhaustive nearest neighbours of every query of pair (i, j) over all of J
-    with the exact ratio test 4/5 (d^2 from an FP64 matrix product of the uint8
-    rows, exact for integers).  Returns best_j per query (-1: no match)."""
-    off = wl.row_off
-    num, den = 4, 5
-    i, j = (int(x) for x in pair)
-    X = desc[off[i]:off[i + 1]].astype(np.float64)
-    Y = desc[off[j]:off[j + 1]].astype(np.float64)
-    ny = (Y * Y).sum(1)
-    ex = np.full(len(X), -1, dtype=np.int64)
-    for q0 in range(0, len(X), 2048):
-        Xq = X[q0:q0 + 2048]
-        d2 = (Xq * Xq).sum(1)[:, None] + ny[None, :] - 2.0 * (Xq @ Y.T)
-        top = np.argpartition(d2, 1, axis=1)[:, :2]
-        a = np.take_along_axis(d2, top, 1)
-        order = np.argsort(a, axis=1, kind="stable")
-        top = np.take_along_axis(top, order, 1)
-        a = np.take_along_axis(a, order, 1)
-        ok = den * den * a[:, 0] < num * num * a[:, 1]
-        ex[q0:q0 + len(Xq)] = np.where(ok, top[:, 0], -1)
-    return ex
+            "per_query_agreement": same / total if total else 1.0, "gpu_matches": ng, "oracle_matches": no}
 
 
 def recall_precision(g, ex):
@@ -636,19 +610,42 @@ def recall_precision(g, ex):
     return shared, n_ex, n_g
 
 
-def exhaustive_nn_quality(wl, desc, pairs, sel, gpu_rows, exact):
-    """Quality ceiling: the cascade-hashing matches of sampled pairs against
-    exhaustive nearest neighbours with the same exact ratio test:
-    recall = shared / exhaustive, precision = shared / cascade."""
-    shared = n_ex = n_gpu = 0
+def exhaustive_leg(args, wl, desc_dev, host, sums, pairs, gpu_rows, stream, world, dev, peak_tflops):
+    """Quality ceiling and its cost: exhaustive nearest neighbours (cm_nn_pairs,
+    tensor cores, exact) on a seeded sample of pairs, timed with CUDA events;
+    the main run's cascade-hashing matches against them (recall = shared /
+    exhaustive, precision = shared / cascade); then the L / K sweep."""
+    import torch
+    import paper_2505_22089_b300 as cm
+    rng = np.random.default_rng(123)
+    sel = np.sort(rng.choice(len(pairs), min(args.nn_pairs, len(pairs)), replace=False))
+    sp = pairs[sel]
+    with torch.cuda.stream(stream):
+        best, _, _, rows = cm.nn_pairs(desc_dev, wl.n_desc, sp, stream=stream)   # warm-up, status checked
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(2):
+            best, _, _, rows = cm.nn_pairs(desc_dev, wl.n_desc, sp, stream=stream, check_status=False)
+        stop.record(stream)
+        stop.synchronize()
+    ms = start.elapsed_time(stop) / 2
+    bj = best.cpu().numpy()
+    exact = {int(k): bj[rows[q]:rows[q + 1]] for q, k in enumerate(sel)}
+    shared = n_ex = n_g = 0
     for k in sel:
-        s, e, g = recall_precision(gpu_rows[int(k)], exact[int(k)])
-        shared += s
-        n_ex += e
-        n_gpu += g
-    return {"pairs": int(len(sel)), "exhaustive_matches": n_ex, "cascade_matches": n_gpu,
-            "recall": shared / n_ex if n_ex else 1.0, "precision": shared / n_gpu if n_gpu else 1.0,
-            "note": "exhaustive L2 NN over all database points, exact ratio test 4/5"}
+        s_, e_, g_ = recall_precision(gpu_rows[int(k)], exact[int(k)])
+        shared, n_ex, n_g = shared + s_, n_ex + e_, n_g + g_
+    nd = wl.n_desc.astype(np.int64)
+    flop = 2.0 * 128 * float((nd[sp[:, 0]] * nd[sp[:, 1]]).sum())
+    tf = flop / (ms / 1e3) / 1e12
+    ceiling = {"pairs": int(len(sel)), "exhaustive_matches": n_ex, "cascade_matches": n_g,
+               "recall": shared / n_ex if n_ex else 1.0, "precision": shared / n_g if n_g else 1.0,
+               "exhaustive_ms": ms, "exhaustive_pairs_per_s": len(sel) * world / (ms / 1e3),
+               "exhaustive_tflops": tf, "exhaustive_frac_of_bf16_peak": tf / peak_tflops,
+               "note": "cm_nn_pairs: every database row a candidate, exact d^2 from BF16 tensor-core products, "
+                       "exact ratio test 4/5; FLOP = 2 x 128 x n_i x n_j per pair"}
+    sweep = quality_sweep(wl, host, sums, pairs, sel, exact, gpu_rows, args.K)
+    return ceiling, sweep
 
 
 def quality_sweep(wl, desc, sums, pairs, sel, exact, gpu_rows, main_K):
