@@ -382,57 +382,70 @@ def pipeline_e2e(args, wl, host, kp, sums, stream, world, dev):
     return out, ver
 
 
-def schedule_comparison(wl, p, budget, size_blk):
-    """Data movement of three ways to feed the GPU the same pair list (Sec. 2.2):
-    one pair at a time (both images loaded and freed per pair), a load/free list
-    (pairs in band order, least recently used image freed when the budget is
-    full), and the MBR block rows of cm_schedule_blocks.  Counted on the host:
-    image loads, H2D bytes, match launches and the largest resident set."""
+def strategy_rows(wl, p, budget, size_blk):
+    """Row lists of the five strategies for one workload under one budget
+    (MBR from cm_schedule_blocks, the others from the strategies module)."""
     import paper_2505_22089_b300 as cm
-    nd = wl.n_desc.astype(np.int64)
-    ib = np.array([cm.image_bytes(p, int(n)) for n in nd], dtype=np.int64)
-    pairs = wl.pairs
-    per_pair = {"loads": int(2 * len(pairs)), "h2d_bytes": int(128 * (nd[pairs[:, 0]] + nd[pairs[:, 1]]).sum()),
-                "launches": int(len(pairs)), "peak_resident_bytes": int((ib[pairs[:, 0]] + ib[pairs[:, 1]]).max())}
-    # load/free list: band order, LRU eviction under the budget
-    order = np.lexsort((np.maximum(pairs[:, 0], pairs[:, 1]), np.minimum(pairs[:, 0], pairs[:, 1])))
-    resident, last_use, used, loads, h2d, peak = set(), {}, 0, 0, 0, 0
-    for t, k in enumerate(order):
-        for im in (int(pairs[k, 0]), int(pairs[k, 1])):
-            if im not in resident:
-                while used + ib[im] > budget and resident:
-                    victim = min((x for x in resident if x not in (int(pairs[k, 0]), int(pairs[k, 1]))),
-                                 key=lambda x: last_use[x], default=None)
-                    if victim is None:
-                        break
-                    resident.discard(victim)
-                    used -= ib[victim]
-                resident.add(im)
-                used += ib[im]
-                loads += 1
-                h2d += 128 * int(nd[im])
-            last_use[im] = t
-        peak = max(peak, used)
-    load_free = {"loads": loads, "h2d_bytes": h2d, "launches": int(len(pairs)), "peak_resident_bytes": int(peak)}
-    sched = cm.schedule_blocks(pairs, wl.n_desc, p, int(budget), size_blk)
-    res, used, peak, loads, h2d = set(), 0, 0, 0, 0
-    for r in sched.rows:
-        for im in r["load"]:
-            if im not in res:
-                res.add(im)
-                used += ib[im]
-                loads += 1
-                h2d += 128 * int(nd[im])
-        peak = max(peak, used)
-        for im in r["free"]:
-            if im in res:
-                res.discard(im)
-                used -= ib[im]
-    mbr = {"loads": loads, "h2d_bytes": h2d, "launches": sum(1 for r in sched.rows if r["pairs"]),
-           "peak_resident_bytes": int(peak), "gps_iterations": sched.iterations}
+    from paper_2505_22089_b300 import strategies as st
+    ib = np.array([cm.image_bytes(p, int(n)) for n in wl.n_desc], dtype=np.int64)
+    order = st.connection_order(wl.pairs, wl.n_images, cm.gps_order)
+    sched = cm.schedule_blocks(wl.pairs, wl.n_desc, p, int(budget), size_blk)
+    mbr = [{"load": r["load"], "free": r["free"], "pairs": r["pairs"], "iteration": r["iteration"]}
+           for r in sched.rows]
     sched.close()
-    return {"budget_bytes": int(budget), "size_blk": size_blk, "per_pair": per_pair, "load_free_lru": load_free,
-            "mbr_blocks": mbr}
+    part = max(1, int(budget // 2 // ib.max()))
+    return ib, {"per_pair": st.per_pair(wl.pairs), "pair_blocks": st.pair_blocks(wl.pairs, ib, budget),
+                "load_free_list": st.load_free_list(wl.pairs, ib, budget, order),
+                "graph_partition": st.graph_partition(wl.pairs, ib, budget, order, part), "mbr_blocks": mbr}
+
+
+def schedule_comparison(args, wl, p, stream, world, dev):
+    """Data schedules compared (Sec. 2.2 against the strategies of Sec. 4):
+    one pair at a time, blocks of pairs in input order, a load/free list in
+    connection order (one pair per row), graph partitions, and the MBR block
+    rows.  (1) Counted on the host for the bench workload under its budget:
+    image loads, H2D bytes, launches, peak resident bytes.  (2) Measured end to
+    end through cm_run_schedule on the 200-image grid under a quarter of its
+    bytes: wall time, GPU time (GPU busy = GPU / wall), H2D bytes, pairs/s."""
+    import paper_2505_22089_b300 as cm
+    from paper_2505_22089_b300 import strategies as st
+    budget = int(args.budget_gb * 2 ** 30)
+    ib, strat = strategy_rows(wl, p, budget, args.block_images)
+    counts = {}
+    for name, rows in strat.items():
+        r = st.residency(rows, ib)
+        r["h2d_bytes"] = int(128 * sum(int(wl.n_desc[x]) for row in rows for x in row["load"]))
+        counts[name] = r
+    # measured on a smaller grid with a tight budget, so that every strategy has to choose
+    sw = synth.scaled(args.workload, gx=20, gy=10) if args.workload == "grid5000" else wl
+    host = sw.generate()
+    off = sw.row_off
+    hl = [host[off[i]:off[i + 1]] for i in range(sw.n_images)]
+    sums = host.astype(np.uint64).sum(0)
+    ib2 = np.array([cm.image_bytes(p, int(n)) for n in sw.n_desc], dtype=np.int64)
+    budget2 = int(ib2.sum() // 4)
+    _, strat2 = strategy_rows(sw, p, budget2, args.block_images)
+    measured = {}
+    for name, rows in strat2.items():
+        sched = cm.schedule_from_rows(rows, sw.pairs, sw.n_images)
+        index = cm.Index(p, sw.n_desc, arena_bytes=cm.schedule_arena_bytes(sched, p, sw.n_desc))
+        index.set_mean(sums, int(sw.total_desc), stream)
+        cm.run_schedule(index, sched, hl, verify=None, workers=1, stream=stream)   # warm-up
+        stt, _ = cm.run_schedule(index, sched, hl, verify=None, workers=1, stream=stream)
+        rr = st.residency(rows, ib2)
+        measured[name] = {"pairs_per_s": len(sw.pairs) / (stt["wall_ms"] / 1e3), "wall_ms": round(stt["wall_ms"], 2),
+                          "gpu_ms": round(stt["gpu_ms"], 2), "gpu_busy": stt["gpu_ms"] / stt["wall_ms"],
+                          "h2d_bytes": int(stt["h2d_bytes"]), "rows": stt["rows"], "kernels": int(stt["kernels"]),
+                          "peak_resident_bytes": rr["peak_resident_bytes"],
+                          "memory_use": rr["peak_resident_bytes"] / budget2, "matches": int(stt["matches"])}
+        index.close()
+        sched.close()
+    return {"budget_bytes": budget, "size_blk": args.block_images, "counted": counts,
+            "measured": {"workload": "%s %dx%d grid, %d images, %d pairs" % (args.workload, 20, 10, sw.n_images,
+                                                                              len(sw.pairs)),
+                         "budget_bytes": budget2, "strategies": measured,
+                         "note": "cm_run_schedule from pinned host rows, no verification; gpu_busy = GPU time "
+                                 "of the rows / wall time"}}
 
 
 def run_ours(args, rank, world, local):
@@ -527,7 +540,7 @@ def run_ours(args, rank, world, local):
         "forms": forms_out,
         "plain_fp32_per_pair": plain,
         "pipeline_verified": verified,
-        "schedules": schedule_comparison(wl, p, int(args.budget_gb * 2 ** 30), args.block_images),
+        "schedules": schedule_comparison(args, wl, p, stream, world, dev) if world == 1 else None,
         "gpu_launches": args.steps * head["graph_kernels"],
         "roofline": roofline,
         "vlad": vl,

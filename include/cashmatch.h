@@ -167,6 +167,15 @@ cm_status cm_index_bytes(const cm_params* p, int32_t n_images, const int32_t* n_
 cm_status cm_schedule_blocks(const cm_pair* pairs, int64_t n_pairs, int32_t n_images, const int32_t* n_desc,
                              const cm_params* p, uint64_t hbm_budget, int32_t max_images_per_block,
                              cm_schedule** out);
+/* A schedule from the caller's own rows, for strategies other than the MBR
+ * blocks (one pair at a time, load/free lists, graph partitions); it runs
+ * through cm_run_schedule like a block schedule.  The rows are copied and
+ * checked by replaying residency: a row loads only non-resident images and
+ * frees only resident ones; both images of each of its pairs are resident
+ * during the row; every index 0..n_pairs-1 of `pairs` appears in exactly one
+ * row.  Errors: CM_ERR_INVALID with the first violation in cm_last_error(). */
+cm_status cm_schedule_from_rows(int32_t n_rows, const cm_schedule_row* rows, const cm_pair* pairs, int64_t n_pairs,
+                                int32_t n_images, cm_schedule** out);
 int32_t cm_schedule_num_rows(const cm_schedule* s);
 int32_t cm_schedule_num_iterations(const cm_schedule* s);
 /* View of row r; pointers stay valid until cm_free_schedule. */

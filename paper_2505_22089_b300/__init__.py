@@ -51,7 +51,7 @@ EXPORTS = [
     "cm_index_image_view", "cm_index_destroy", "cm_match_plan_create", "cm_match_plan_rows", "cm_match_plan_run",
     "cm_match_plan_compact", "cm_match_plan_mutual", "cm_match_plan_destroy", "cm_match_pairs", "cm_sequence_create", "cm_sequence_launch",
     "cm_sequence_kernels", "cm_sequence_destroy", "cm_schedule_arena_bytes", "cm_pipeline_workspace_bytes", "cm_run_schedule",
-    "cm_verify_affine", "cm_affine_verify_cb", "cm_sao_filter", "cm_vlad_workspace_bytes", "cm_vlad_encode",
+    "cm_verify_affine", "cm_affine_verify_cb", "cm_sao_filter", "cm_schedule_from_rows", "cm_vlad_workspace_bytes", "cm_vlad_encode",
     "cm_workspace_status", "cm_nn_workspace_bytes", "cm_nn_pairs", "cm_autotune", "cm_match_pair_noalloc",
 ]
 
@@ -144,6 +144,7 @@ def lib():
             "cm_index_bytes": (i32, [P, i32, vp, i32, ctypes.POINTER(u64)]),
             "cm_schedule_blocks": (i32, [vp, i64, i32, vp, P, u64, i32, ctypes.POINTER(vp)]),
             "cm_schedule_num_rows": (i32, [vp]),
+            "cm_schedule_from_rows": (i32, [i32, vp, vp, i64, i32, ctypes.POINTER(vp)]),
             "cm_schedule_num_iterations": (i32, [vp]),
             "cm_schedule_get_row": (i32, [vp, i32, ctypes.POINTER(ScheduleRow)]),
             "cm_free_schedule": (None, [vp]),
@@ -276,6 +277,27 @@ def schedule_blocks(pairs, n_desc, p: Params, budget: int, max_images_per_block:
     h = ctypes.c_void_p()
     check(lib().cm_schedule_blocks(pr.ctypes.data, pr.shape[0], len(nd), nd.ctypes.data, ctypes.byref(p),
                                    int(budget), int(max_images_per_block), ctypes.byref(h)))
+    return Schedule(h, pr)
+
+
+def schedule_from_rows(rows, pairs, n_images: int) -> Schedule:
+    """cm_schedule_from_rows: rows = [{"load": [...], "free": [...], "pairs": [...],
+    "iteration": int (optional)}], pair ids into `pairs`."""
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    keep = []
+    crows = (ScheduleRow * max(len(rows), 1))()
+    for k, r in enumerate(rows):
+        ld = np.ascontiguousarray(r.get("load", []), dtype=np.int32)
+        fr = np.ascontiguousarray(r.get("free", []), dtype=np.int32)
+        ps = np.ascontiguousarray(r.get("pairs", []), dtype=np.int64)
+        keep += [ld, fr, ps]
+        crows[k] = ScheduleRow(int(r.get("iteration", 0)), len(ld), ld.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               len(fr), fr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(ps),
+                               ps.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    h = ctypes.c_void_p()
+    check(lib().cm_schedule_from_rows(len(rows), ctypes.cast(crows, ctypes.c_void_p), pr.ctypes.data if len(pr) else None,
+                                      len(pr), int(n_images), ctypes.byref(h)))
+    del keep
     return Schedule(h, pr)
 
 

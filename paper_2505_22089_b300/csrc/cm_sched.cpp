@@ -23,6 +23,7 @@
 #include <map>
 #include <set>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "cm_internal.h"
@@ -325,6 +326,65 @@ extern "C" cm_status cm_schedule_blocks(const cm_pair* pairs, int64_t n_pairs, i
     }
     s->iterations = it;
     *out = s;
+    return CM_OK;
+}
+
+// A schedule from the caller's rows (another strategy than the MBR blocks),
+// checked by replaying its residency: a row may load only images that are
+// not resident and free only resident ones, both images of each of its pairs
+// must be resident while it runs, and every pair index appears in exactly one
+// row.  Images still resident after the last row are allowed (cm_run_schedule
+// releases them).
+extern "C" cm_status cm_schedule_from_rows(int32_t n_rows, const cm_schedule_row* rows, const cm_pair* pairs,
+                                           int64_t n_pairs, int32_t n_images, cm_schedule** out) {
+    if (!out || n_rows < 0 || (n_rows && !rows) || n_pairs < 0 || (n_pairs && !pairs) || n_images < 0)
+        return sfail(CM_ERR_INVALID, "schedule_from_rows: bad argument");
+    *out = nullptr;
+    std::vector<char> res((size_t)n_images, 0), seen((size_t)n_pairs, 0);
+    auto s = std::make_unique<cm_schedule>();
+    s->rows.resize((size_t)n_rows);
+    int32_t iters = 0;
+    for (int32_t r = 0; r < n_rows; ++r) {
+        const cm_schedule_row& R = rows[r];
+        if (R.n_load < 0 || R.n_free < 0 || R.n_pairs < 0 || (R.n_load && !R.load) || (R.n_free && !R.free_ids) ||
+            (R.n_pairs && !R.pairs))
+            return sfail(CM_ERR_INVALID, "schedule_from_rows: row %d is malformed", r);
+        for (int k = 0; k < R.n_load; ++k) {
+            const int32_t i = R.load[k];
+            if (i < 0 || i >= n_images) return sfail(CM_ERR_INVALID, "schedule_from_rows: row %d loads image %d", r, i);
+            if (res[i]) return sfail(CM_ERR_INVALID, "schedule_from_rows: row %d loads resident image %d", r, i);
+            res[i] = 1;
+        }
+        for (int64_t k = 0; k < R.n_pairs; ++k) {
+            const int64_t id = R.pairs[k];
+            if (id < 0 || id >= n_pairs || seen[id])
+                return sfail(CM_ERR_INVALID, "schedule_from_rows: row %d: pair %lld out of range or repeated", r,
+                             (long long)id);
+            seen[id] = 1;
+            const cm_pair pr = pairs[id];
+            if (pr.i < 0 || pr.j < 0 || pr.i >= n_images || pr.j >= n_images || pr.i == pr.j)
+                return sfail(CM_ERR_INVALID, "schedule_from_rows: pair %lld is invalid", (long long)id);
+            if (!res[pr.i] || !res[pr.j])
+                return sfail(CM_ERR_INVALID, "schedule_from_rows: row %d matches pair %lld without its images resident",
+                             r, (long long)id);
+        }
+        for (int k = 0; k < R.n_free; ++k) {
+            const int32_t i = R.free_ids[k];
+            if (i < 0 || i >= n_images || !res[i])
+                return sfail(CM_ERR_INVALID, "schedule_from_rows: row %d frees image %d that is not resident", r, i);
+            res[i] = 0;
+        }
+        auto& D = s->rows[r];
+        D.iteration = R.iteration;
+        D.load.assign(R.load, R.load + R.n_load);
+        D.free_ids.assign(R.free_ids, R.free_ids + R.n_free);
+        D.pairs.assign(R.pairs, R.pairs + R.n_pairs);
+        iters = std::max(iters, R.iteration + 1);
+    }
+    for (int64_t k = 0; k < n_pairs; ++k)
+        if (!seen[k]) return sfail(CM_ERR_INVALID, "schedule_from_rows: pair %lld is in no row", (long long)k);
+    s->iterations = iters;
+    *out = s.release();
     return CM_OK;
 }
 
