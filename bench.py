@@ -136,7 +136,8 @@ class ClockSampler:
 # summed over the 13 k_match launches of one grid5000 step, divided by 13).  It is reported only
 # for the configuration it was taken on and only while the kernel's sources are unchanged
 # (their SHA-256 below); otherwise the roofline's "traffic" is null.
-KMATCH_TRAFFIC = {"workload": "grid5000", "rerank": "bf16", "K": 8, "bytes_per_launch": None, "sources_sha256": None}
+KMATCH_TRAFFIC = {"workload": "grid5000", "rerank": "bf16", "K": 8, "bytes_per_launch": 9137427790,
+                  "sources_sha256": "7a7fe629d21c8148528e3e6e6a7c01b6bae13dbdf7a2d002971b24032af85a3a"}
 KMATCH_SOURCES = ["paper_2505_22089_b300/csrc/cm_match.cu", "paper_2505_22089_b300/csrc/cm_internal.h",
                   "paper_2505_22089_b300/csrc/cm_ratio.cuh"]
 
