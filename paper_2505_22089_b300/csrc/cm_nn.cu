@@ -9,9 +9,9 @@
 // chunks of up to 256 rows, each staged as the B operand and multiplied on
 // the tensor cores (128 x N x 128, BF16, FP32 accumulate: every partial sum
 // of x.y is an integer below 2^24, so exact).  The 4 warps read their lanes
-// back and keep, per query, the two smallest (d^2, j) with
-// d^2 = |x|^2 + |y|^2 - 2 x.y, exact as an FP32 integer; the last chunk is
-// followed by the exact integer ratio test.  Two CTAs per SM overlap one's
+// back and keep, per query, the smallest (d^2, j) and the second smallest
+// d^2, with d^2 = |x|^2 + |y|^2 - 2 x.y exact as an FP32 integer; the last
+// chunk is followed by the exact integer ratio test.  Two CTAs per SM overlap one's
 // staging with the other's MMA and epilogue.
 #include <cuda_runtime.h>
 
@@ -76,7 +76,7 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
         stage::load_row(desc + (size_t)(oi + (qv ? q : 0)) * kDim, qv, v);
         const float nq = (float)stage::store_row(v, At, tid, kNnRows);
         float e1 = kInf, e2 = kInf;
-        int j1 = -1, j2 = -1;
+        int j1 = -1;
 
         for (int c0 = 0; c0 < nj; c0 += kNnChunk) {
             const int nc = min(kNnChunk, nj - c0);
@@ -104,20 +104,20 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
                 break;
             }
             tc::fence_after();
+            // q1 keeps its index, q2 only its value (the outputs need no j2);
+            // columns in ascending j, so a tie keeps the smaller j as q1
             for (int cc = 0; cc < N; cc += 16) {
                 uint32_t acc[16];
                 tc::tmem_ld16(lane_base + cc, acc);
                 tc::tmem_wait_ld();
+                const int jb = c0 + cc;
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     // exact: |x|^2 + |y|^2 < 2^24 and the result is a squared distance
                     const float d = fmaf(-2.f, __uint_as_float(acc[u]), nq + nb[cc + u]);
-                    const int j = c0 + cc + u;
-                    const bool lt1 = d < e1, lt2 = d < e2;   // columns in ascending j: ties keep the smaller j
-                    e2 = lt1 ? e1 : (lt2 ? d : e2);
-                    j2 = lt1 ? j1 : (lt2 ? j : j2);
-                    e1 = lt1 ? d : e1;
-                    j1 = lt1 ? j : j1;
+                    j1 = d < e1 ? jb + u : j1;
+                    e2 = fminf(e2, fmaxf(e1, d));
+                    e1 = fminf(e1, d);
                 }
             }
             tc::fence_before();
@@ -125,8 +125,9 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
         }
         if (!failed && qv) {
             const int64_t row = P.row_off + q;
-            const uint32_t u1 = j1 >= 0 ? (uint32_t)e1 : 0xFFFFFFFFu, u2 = j2 >= 0 ? (uint32_t)e2 : 0xFFFFFFFFu;
-            const bool pass = j2 >= 0 && (int64_t)ratio_den * ratio_den * u1 < (int64_t)ratio_num * ratio_num * u2;
+            const bool has2 = nj >= 2;   // e2 is finite exactly when J has two rows
+            const uint32_t u1 = j1 >= 0 ? (uint32_t)e1 : 0xFFFFFFFFu, u2 = has2 ? (uint32_t)e2 : 0xFFFFFFFFu;
+            const bool pass = has2 && (int64_t)ratio_den * ratio_den * u1 < (int64_t)ratio_num * ratio_num * u2;
             best_j[row] = pass ? j1 : -1;
             if (d1sq) d1sq[row] = u1;
             if (d2sq) d2sq[row] = u2;
