@@ -449,6 +449,14 @@ cm_status cm_vlad_encode(const uint8_t* desc, const int64_t* img_off, int32_t n_
  * failed, else CM_OK. */
 cm_status cm_workspace_status(const void* d_work, cm_stream stream);
 
+/* Diagnostic: runs the bounded-wait path every kernel uses, on the device,
+ * without a fault.  One CTA holds tensor memory, waits on an mbarrier that
+ * nothing completes, gives up after `polls` (1..2^24) polls, records the
+ * timeout and frees its tensor memory.  Returns CM_ERR_TIMEOUT (the status a
+ * launch whose wait ran out reports); the context stays usable.  Blocks until
+ * done.  CM_ERR_INVALID for polls out of range. */
+cm_status cm_selftest_wait(int32_t polls, cm_stream stream);
+
 /* ---- exhaustive nearest neighbours (quality ceiling) --------------------- */
 /* Device workspace of cm_nn_pairs. */
 cm_status cm_nn_workspace_bytes(int32_t n_images, int64_t n_pairs, uint64_t* bytes);

@@ -52,7 +52,7 @@ EXPORTS = [
     "cm_match_plan_compact", "cm_match_plan_mutual", "cm_match_plan_destroy", "cm_match_pairs", "cm_sequence_create", "cm_sequence_launch",
     "cm_sequence_kernels", "cm_sequence_destroy", "cm_schedule_arena_bytes", "cm_pipeline_workspace_bytes", "cm_run_schedule",
     "cm_verify_affine", "cm_affine_verify_cb", "cm_sao_filter", "cm_schedule_from_rows", "cm_vlad_workspace_bytes", "cm_vlad_encode",
-    "cm_workspace_status", "cm_nn_workspace_bytes", "cm_nn_pairs", "cm_autotune", "cm_match_pair_noalloc",
+    "cm_workspace_status", "cm_nn_workspace_bytes", "cm_nn_pairs", "cm_selftest_wait", "cm_autotune", "cm_match_pair_noalloc",
 ]
 
 
@@ -183,6 +183,7 @@ def lib():
             "cm_vlad_workspace_bytes": (i32, [i32, i64, ctypes.POINTER(u64)]),
             "cm_vlad_encode": (i32, [vp, vp, i32, vp, i32, vp, u64, vp, vp, vp]),
             "cm_workspace_status": (i32, [vp, vp]),
+            "cm_selftest_wait": (i32, [i32, vp]),
             "cm_nn_workspace_bytes": (i32, [i32, i64, ctypes.POINTER(u64)]),
             "cm_nn_pairs": (i32, [vp, vp, i32, vp, i64, i32, i32, vp, u64, vp, vp, vp, vp]),
             "cm_autotune": (i32, [vp, vp, i64, vp, i32, ctypes.c_float, vp, ctypes.POINTER(TuneResult)]),

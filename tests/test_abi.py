@@ -108,3 +108,17 @@ def test_image_bytes_layout():
     assert b - b0 >= 264 * 20000
     assert b - b0 < 264 * 20000 + 4096
     assert cm.image_bytes(cm.Params.make(rerank="int"), 20000) == b
+
+
+def test_host_argument_checks_of_the_later_entry_points():
+    lib = cm.lib()
+    # rejected before any device work, so these run without a GPU
+    assert lib.cm_selftest_wait(0, None) == cm.CM_ERR_INVALID
+    assert lib.cm_selftest_wait((1 << 24) + 1, None) == cm.CM_ERR_INVALID
+    off = np.array([1, 5], dtype=np.int64)
+    assert lib.cm_vlad_encode(None, off.ctypes.data, 1, None, 4, None, 0, None, None, None) == cm.CM_ERR_INVALID
+    assert lib.cm_nn_pairs(None, off.ctypes.data, 1, None, 0, 5, 4, None, 0, None, None, None, None) == cm.CM_ERR_INVALID
+    b = cm.ctypes.c_uint64()
+    assert lib.cm_vlad_workspace_bytes(3, 100, cm.ctypes.byref(b)) == cm.CM_OK and b.value % 256 == 0
+    assert lib.cm_nn_workspace_bytes(3, 7, cm.ctypes.byref(b)) == cm.CM_OK and b.value % 256 == 0
+    assert lib.cm_nn_workspace_bytes(-1, 7, cm.ctypes.byref(b)) == cm.CM_ERR_INVALID
