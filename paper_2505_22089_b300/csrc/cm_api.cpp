@@ -196,6 +196,7 @@ extern "C" cm_status cm_index_create(const cm_params* p, int32_t n_images, const
     for (int i = 0; i < n_images; ++i) ix->h_imgs[i].n = n_desc[i];
     ix->slot_at.assign(n_images, 0);
     ix->resident.assign(n_images, 0);
+    ix->pending.assign(n_images, 0);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&ix->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -262,8 +263,13 @@ extern "C" cm_status cm_index_mean_device(cm_index* ix, const uint8_t* d_desc, u
 
 // Allocate slots, copy descriptors, refresh the device image table and the
 // load-batch table.  Returns the batch's hash-tile count.
-static cm_status stage_images(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc,
-                              int32_t mem, cudaStream_t s, int* n_tiles_out, int* n_tiles128_out) {
+// Loading an image has three phases: placing its slot in the arena, copying
+// its descriptors there, and publishing it (device table entry, cleared
+// histograms, resident flag) before it is hashed.  cm_index_load runs them
+// in a row on one stream; the pipeline runs the first two early, on a copy
+// stream, for the next block row (index_prefetch / index_publish).
+static cm_status check_loadable(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc,
+                                int32_t mem) {
     if (count < 0 || (count && (!ids || !desc))) return fail(CM_ERR_INVALID, "load: bad argument");
     if (mem != CM_MEM_HOST && mem != CM_MEM_DEVICE && mem != CM_MEM_DEVICE_INPLACE)
         return fail(CM_ERR_INVALID, "load: bad memory kind %d", mem);
@@ -271,28 +277,56 @@ static cm_status stage_images(cm_index* ix, int32_t count, const int32_t* ids, c
     for (int k = 0; k < count; ++k) {
         const int i = ids[k];
         if (i < 0 || i >= ix->n_images) return fail(CM_ERR_INVALID, "load: image id %d out of range", i);
-        if (ix->resident[i] || seen[i]) return fail(CM_ERR_STATE, "load: image %d is already resident", i);
+        if (ix->resident[i] || ix->pending[i] || seen[i])
+            return fail(CM_ERR_STATE, "load: image %d is already resident", i);
         if (!desc[k] && ix->n_desc[i]) return fail(CM_ERR_INVALID, "load: NULL descriptors for image %d", i);
         seen[i] = 1;
     }
-    const bool inplace = mem == CM_MEM_DEVICE_INPLACE;
+    return CM_OK;
+}
+
+// Places the slots of ids (all or none); false when the arena has no room.
+static bool place_slots(cm_index* ix, int32_t count, const int32_t* ids, bool inplace) {
+    for (int k = 0; k < count; ++k) {
+        const int i = ids[k];
+        uint64_t at = 0;
+        if (!ix->alloc.alloc(slot_layout(&ix->p, ix->n_desc[i], inplace).total, &at)) {
+            for (int r = 0; r < k; ++r) {   // roll back this call's slots
+                ix->alloc.release(ix->slot_at[ids[r]]);
+                ix->pending[ids[r]] = 0;
+            }
+            return false;
+        }
+        ix->slot_at[i] = at;
+        ix->pending[i] = 1;
+    }
+    return true;
+}
+
+static cm_status copy_descs(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc, int32_t mem,
+                            cudaStream_t s) {
+    if (mem == CM_MEM_DEVICE_INPLACE) return CM_OK;
+    const cudaMemcpyKind kind = mem == CM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    for (int k = 0; k < count; ++k) {
+        const int i = ids[k];
+        const int64_t n = ix->n_desc[i];
+        if (n) CM_CUDA(cudaMemcpyAsync(ix->arena + ix->slot_at[i] + slot_layout(&ix->p, n, false).desc, desc[k],
+                                       (size_t)n * kDim, kind, s));
+    }
+    return CM_OK;
+}
+
+// Fills the device-table entries of placed images, marks them resident and
+// uploads the tables of the batch that hash_batch processes next.
+static cm_status publish(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc, bool inplace,
+                         cudaStream_t s, int* n_tiles_out, int* n_tiles128_out) {
     ++ix->generation;
     std::vector<int32_t> batch(count), tiles(count + 1, 0), tiles128(count + 1, 0);
-    int k_done = 0;
-    for (int k = 0; k < count; ++k, ++k_done) {
+    for (int k = 0; k < count; ++k) {
         const int i = ids[k];
         const int64_t n = ix->n_desc[i];
         const SlotLayout L = slot_layout(&ix->p, n, inplace);
-        uint64_t at = 0;
-        if (!ix->alloc.alloc(L.total, &at)) {
-            for (int r = 0; r < k_done; ++r) {  // roll back this call's slots
-                ix->alloc.release(ix->slot_at[ids[r]]);
-                ix->resident[ids[r]] = 0;
-            }
-            return fail(CM_ERR_BUDGET, "load: arena full while placing image %d (%llu bytes)", i,
-                        (unsigned long long)L.total);
-        }
-        uint8_t* base = ix->arena + at;
+        uint8_t* base = ix->arena + ix->slot_at[i];
         DevImage& e = ix->h_imgs[i];
         e.n = (int32_t)n;
         e.desc = inplace ? desc[k] : base + L.desc;
@@ -306,15 +340,11 @@ static cm_status stage_images(cm_index* ix, int32_t count, const int32_t* ids, c
         e.norm = reinterpret_cast<uint32_t*>(base + L.norm);
         e.xq = L.xq ? base + L.xq : nullptr;
         e.xscale = L.xscale ? reinterpret_cast<float*>(base + L.xscale) : nullptr;
-        ix->slot_at[i] = at;
+        ix->pending[i] = 0;
         ix->resident[i] = 1;
         batch[k] = i;
         tiles[k + 1] = tiles[k] + (int)((n + kHashTile - 1) / kHashTile);
         tiles128[k + 1] = tiles128[k] + (int)((n + 127) / 128);
-        if (!inplace && n) {
-            const cudaMemcpyKind kind = mem == CM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-            CM_CUDA(cudaMemcpyAsync(base + L.desc, desc[k], (size_t)n * kDim, kind, s));
-        }
         CM_CUDA(cudaMemsetAsync(e.hist, 0, (size_t)ix->p.L * ix->B * 4, s));
     }
     cm_status st = upload_table(ix, ix->fx.imgs, ix->h_imgs.data(), ix->h_imgs.size() * sizeof(DevImage), s);
@@ -325,6 +355,24 @@ static cm_status stage_images(cm_index* ix, int32_t count, const int32_t* ids, c
     *n_tiles_out = tiles[count];
     *n_tiles128_out = tiles128[count];
     return CM_OK;
+}
+
+static cm_status stage_images(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc,
+                              int32_t mem, cudaStream_t s, int* n_tiles_out, int* n_tiles128_out) {
+    cm_status st = check_loadable(ix, count, ids, desc, mem);
+    if (st != CM_OK) return st;
+    const bool inplace = mem == CM_MEM_DEVICE_INPLACE;
+    if (!place_slots(ix, count, ids, inplace)) {
+        uint64_t need = 0;
+        for (int k = 0; k < count; ++k) need += slot_layout(&ix->p, ix->n_desc[ids[k]], inplace).total;
+        return fail(CM_ERR_BUDGET, "load: arena full while placing %d images (%llu bytes)", count,
+                    (unsigned long long)need);
+    }
+    if ((st = copy_descs(ix, count, ids, desc, mem, s)) != CM_OK) {
+        index_cancel_prefetch(ix, count, ids);
+        return st;
+    }
+    return publish(ix, count, ids, desc, inplace, s, n_tiles_out, n_tiles128_out);
 }
 
 // The resident-set table used by cm_index_rehash.
@@ -395,6 +443,48 @@ extern "C" cm_status cm_index_load(cm_index* ix, int32_t count, const int32_t* i
     if (st != CM_OK) return st;
     return hash_batch(ix, ix->hash_launch(false, count, n_tiles, n_tiles128), s);
 }
+
+namespace cm {
+
+cm_status index_prefetch(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc,
+                         cudaStream_t copy_stream, bool* placed) {
+    *placed = false;
+    cm_status st = check_loadable(ix, count, ids, desc, CM_MEM_HOST);
+    if (st != CM_OK) return st;
+    if (!place_slots(ix, count, ids, false)) return CM_OK;   // no room yet: the caller loads later
+    if ((st = copy_descs(ix, count, ids, desc, CM_MEM_HOST, copy_stream)) != CM_OK) {
+        index_cancel_prefetch(ix, count, ids);
+        return st;
+    }
+    *placed = true;
+    return CM_OK;
+}
+
+cm_status index_publish(cm_index* ix, int32_t count, const int32_t* ids, cudaStream_t s) {
+    for (int k = 0; k < count; ++k)
+        if (ids[k] < 0 || ids[k] >= ix->n_images || !ix->pending[ids[k]])
+            return fail(CM_ERR_STATE, "publish: image %d was not prefetched", ids[k]);
+    int n_tiles = 0, n_tiles128 = 0;
+    cm_status st = publish(ix, count, ids, nullptr, false, s, &n_tiles, &n_tiles128);
+    if (st != CM_OK) return st;
+    int rb = 0, rt = 0;
+    uint64_t rows = 0;
+    st = refresh_resident(ix, s, &rb, &rt, &rows);
+    if (st != CM_OK) return st;
+    return hash_batch(ix, ix->hash_launch(false, count, n_tiles, n_tiles128), s);
+}
+
+void index_cancel_prefetch(cm_index* ix, int32_t count, const int32_t* ids) {
+    for (int k = 0; k < count; ++k) {
+        const int i = ids[k];
+        if (i >= 0 && i < ix->n_images && ix->pending[i]) {
+            ix->alloc.release(ix->slot_at[i]);
+            ix->pending[i] = 0;
+        }
+    }
+}
+
+}  // namespace cm
 
 extern "C" cm_status cm_index_rehash(cm_index* ix, cm_stream stream) {
     if (!ix) return fail(CM_ERR_INVALID, "cm_index_rehash: NULL index");

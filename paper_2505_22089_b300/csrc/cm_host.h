@@ -210,11 +210,28 @@ struct cm_index {
     std::vector<DevImage> h_imgs;
     std::vector<uint64_t> slot_at;     // arena offset of each image's slot (valid if resident)
     std::vector<char> resident;
+    std::vector<char> pending;         // slot placed and descriptors on their way, not yet published
     bool mean_set = false;
     bool sums_on_host = false;         // the mean came from cm_index_set_mean
     uint64_t host_sums[kDim] = {};
     uint64_t n_total = 0;              // rows behind the current mean
     Staging staging;
+    // cm_run_schedule's two host result buffers (pinned; the match lists are
+    // mapped), kept between calls: page-locking them costs more than a row
+    struct PinnedResult {
+        uint64_t* offsets = nullptr;
+        size_t n_offsets = 0;
+        uint32_t* matches = nullptr;
+        uint32_t* d_matches = nullptr;
+        size_t n_matches = 0;
+    } pinned[2];
+
+    ~cm_index() {
+        for (auto& b : pinned) {
+            if (b.offsets) cudaFreeHost(b.offsets);
+            if (b.matches) cudaFreeHost(b.matches);
+        }
+    }
 
     template <class T>
     T* at(uint64_t off) const { return reinterpret_cast<T*>(arena + off); }
@@ -239,6 +256,19 @@ struct cm_index {
         return h;
     }
 };
+
+// Early loading for the pipeline: index_prefetch places the slots of images
+// (all or none; *placed = false when the arena has no room now) and copies
+// their descriptors from host memory on copy_stream; index_publish later makes
+// them resident and hashes them on the main stream, which must first wait for
+// the copies; index_cancel_prefetch returns placed slots that were never
+// published.
+namespace cm {
+cm_status index_prefetch(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc,
+                         cudaStream_t copy_stream, bool* placed);
+cm_status index_publish(cm_index* ix, int32_t count, const int32_t* ids, cudaStream_t s);
+void index_cancel_prefetch(cm_index* ix, int32_t count, const int32_t* ids);
+}  // namespace cm
 
 // Arena bytes of a plan: its pair table, the work counter and, for the
 // tensor-core reranks, the [rows][K] top-K hand-over from scan to rerank

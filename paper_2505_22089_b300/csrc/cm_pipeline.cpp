@@ -431,18 +431,29 @@ extern "C" cm_status cm_schedule_arena_bytes(const cm_schedule* s, const cm_para
     std::vector<char> res(n_images, 0);
     uint64_t cur = 0, peak = 0, largest = 0, plan = 0;
     const int32_t R = cm_schedule_num_rows(s);
+    // bytes each row loads: cm_run_schedule places row r+1's loads while row r
+    // is still resident, to copy them during row r
+    std::vector<uint64_t> load_bytes(R + 1, 0);
     for (int32_t r = 0; r < R; ++r) {
         cm_schedule_row row{};
         if ((st = cm_schedule_get_row(s, r, &row)) != CM_OK) return st;
         for (int k = 0; k < row.n_load; ++k) {
             const int i = row.load[k];
             if (i < 0 || i >= n_images) return fail(CM_ERR_INVALID, "cm_schedule_arena_bytes: image %d", i);
+            load_bytes[r] += align_up(slot_layout(p, n_desc[i], false).total);
+        }
+    }
+    for (int32_t r = 0; r < R; ++r) {
+        cm_schedule_row row{};
+        if ((st = cm_schedule_get_row(s, r, &row)) != CM_OK) return st;
+        for (int k = 0; k < row.n_load; ++k) {
+            const int i = row.load[k];
             const uint64_t b = align_up(slot_layout(p, n_desc[i], false).total);
             if (!res[i]) cur += b;
             res[i] = 1;
             largest = std::max(largest, b);
         }
-        peak = std::max(peak, cur);
+        peak = std::max(peak, cur + load_bytes[r + 1]);
         int64_t rows = 0;
         int32_t max_ni = 0;
         for (int64_t k = 0; k < row.n_pairs; ++k) {
@@ -505,7 +516,10 @@ extern "C" cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const c
     P.pairs = pairs;
     P.verify = verify;
     P.user = user;
-    std::vector<cudaEvent_t> ev_start(R, nullptr), ev_done(R, nullptr);
+    std::vector<cudaEvent_t> ev_start(R, nullptr), ev_done(R, nullptr), ev_copied(R, nullptr);
+    std::vector<char> prefetched(R, 0);   // row r's loads were placed and copied during row r-1
+    cudaStream_t cpy = nullptr;           // copies of the next row's descriptors
+    cudaEvent_t ev_origin = nullptr;
     std::vector<std::unique_ptr<RowJob>> jobs;
     std::vector<int32_t> loaded_by_us;
     std::vector<std::thread> threads;
@@ -519,12 +533,18 @@ extern "C" cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const c
         P.cv_job.notify_all();
         for (auto& t : threads) t.join();
         cudaStreamSynchronize(cs);
-        for (auto& b : P.buf) {
-            if (b.offsets) cudaFreeHost(b.offsets);
-            if (b.matches) cudaFreeHost(b.matches);
-        }
+        if (cpy) cudaStreamSynchronize(cpy);
+        for (int32_t r = 0; r < R; ++r)   // slots placed for a row that never ran
+            if (prefetched[r]) {
+                cm_schedule_row row{};
+                if (cm_schedule_get_row(s, r, &row) == CM_OK) index_cancel_prefetch(ix, row.n_load, row.load);
+                prefetched[r] = 0;
+            }
         for (auto e : ev_start) if (e) cudaEventDestroy(e);
         for (auto e : ev_done) if (e) cudaEventDestroy(e);
+        for (auto e : ev_copied) if (e) cudaEventDestroy(e);
+        if (ev_origin) cudaEventDestroy(ev_origin);
+        if (cpy) cudaStreamDestroy(cpy);
     };
     auto bail = [&](cm_status code) {
         std::string msg = cm_last_error();
@@ -539,19 +559,74 @@ extern "C" cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const c
         return code;
     };
 
-    for (auto& b : P.buf) {
-        if (cudaHostAlloc(&b.offsets, (size_t)(max_pairs + 1) * 8, cudaHostAllocDefault) != cudaSuccess ||
-            cudaHostAlloc(&b.matches, (size_t)std::max<int64_t>(max_rows, 1) * 4, cudaHostAllocMapped) != cudaSuccess ||
-            cudaHostGetDevicePointer(&b.d_matches, b.matches, 0) != cudaSuccess) {
+    static_assert(kBufs == 2, "one cached pinned buffer per result buffer");
+    for (int k = 0; k < kBufs; ++k) {   // the index's cached buffers, grown when this schedule needs more
+        auto& c = ix->pinned[k];
+        const size_t no = (size_t)(max_pairs + 1), nm = (size_t)std::max<int64_t>(max_rows, 1);
+        bool ok = true;
+        if (c.n_offsets < no) {
+            if (c.offsets) cudaFreeHost(c.offsets);
+            c.offsets = nullptr;
+            c.n_offsets = 0;
+            ok = cudaHostAlloc(reinterpret_cast<void**>(&c.offsets), no * 8, cudaHostAllocDefault) == cudaSuccess;
+            if (ok) c.n_offsets = no;
+        }
+        if (ok && c.n_matches < nm) {
+            if (c.matches) cudaFreeHost(c.matches);
+            c.matches = c.d_matches = nullptr;
+            c.n_matches = 0;
+            ok = cudaHostAlloc(reinterpret_cast<void**>(&c.matches), nm * 4, cudaHostAllocMapped) == cudaSuccess &&
+                 cudaHostGetDevicePointer(reinterpret_cast<void**>(&c.d_matches), c.matches, 0) == cudaSuccess;
+            if (ok) c.n_matches = nm;
+        }
+        if (!ok) {
             fail(CM_ERR_NOMEM, "cm_run_schedule: pinned result buffers (%lld matches)", (long long)max_rows);
             return bail(CM_ERR_NOMEM);
         }
+        P.buf[k].offsets = c.offsets;
+        P.buf[k].matches = c.matches;
+        P.buf[k].d_matches = c.d_matches;
     }
     for (int32_t r = 0; r < R; ++r)
-        if (cudaEventCreate(&ev_start[r]) != cudaSuccess || cudaEventCreate(&ev_done[r]) != cudaSuccess) {
+        if (cudaEventCreate(&ev_start[r]) != cudaSuccess || cudaEventCreate(&ev_done[r]) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev_copied[r], cudaEventDisableTiming) != cudaSuccess) {
             fail(CM_ERR_CUDA, "cm_run_schedule: event creation");
             return bail(CM_ERR_CUDA);
         }
+    if (cudaStreamCreateWithFlags(&cpy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_origin, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev_origin, cs) != cudaSuccess) {
+        fail(CM_ERR_CUDA, "cm_run_schedule: copy stream");
+        return bail(CM_ERR_CUDA);
+    }
+    // Places row r+1's loads and copies their descriptors on the copy stream
+    // while row r runs.  The copy waits for everything enqueued before row r
+    // (ev_done[r-1]): the space it writes was freed by earlier rows, whose
+    // readers all precede that event; row r's own images and plan are still
+    // placed, so the new slots cannot overlap them.  No room, or an image that
+    // row r frees and row r+1 loads again: row r+1 loads in order as usual.
+    auto prefetch_next = [&](int32_t r) -> cm_status {
+        if (r + 1 >= R) return CM_OK;
+        cm_schedule_row next{};
+        cm_status st2 = cm_schedule_get_row(s, r + 1, &next);
+        if (st2 != CM_OK || !next.n_load) return st2;
+        for (int k = 0; k < next.n_load; ++k) {   // an image row r frees and row r+1 loads again: load in order
+            const int i = next.load[k];
+            if (i < 0 || i >= ix->n_images || ix->resident[i] || ix->pending[i]) return CM_OK;
+        }
+        if (cudaStreamWaitEvent(cpy, r == 0 ? ev_origin : ev_done[r - 1], 0) != cudaSuccess)
+            return fail(CM_ERR_CUDA, "cm_run_schedule: copy stream wait");
+        std::vector<const uint8_t*> src(next.n_load);
+        for (int k = 0; k < next.n_load; ++k) src[k] = desc_host[next.load[k]];
+        bool placed = false;
+        if ((st2 = index_prefetch(ix, next.n_load, next.load, src.data(), cpy, &placed)) != CM_OK) return st2;
+        if (placed) {
+            if (cudaEventRecord(ev_copied[r + 1], cpy) != cudaSuccess)
+                return fail(CM_ERR_CUDA, "cm_run_schedule: event record");
+            prefetched[r + 1] = 1;
+        }
+        return CM_OK;
+    };
     for (int w = 0; w < n_workers; ++w) threads.emplace_back([&P] { P.worker(); });
     // hashing: (bias +) projection + buckets (+ the rerank row copies); matching: scan (+ tensor-core rerank)
     const int hash_kernels = (ix->p.projection == CM_PROJ_TC ? 3 : 2) + (tc_rerank(&ix->p) ? 1 : 0);
@@ -580,7 +655,16 @@ extern "C" cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const c
                 src[k] = desc_host[row.load[k]];
                 S.h2d_bytes += (uint64_t)ix->n_desc[row.load[k]] * kDim;
             }
-            if ((st = cm_index_load(ix, row.n_load, row.load, src.data(), CM_MEM_HOST, stream)) != CM_OK) return bail(st);
+            if (prefetched[r]) {   // copied during the previous row: make resident and hash
+                if (cudaStreamWaitEvent(cs, ev_copied[r], 0) != cudaSuccess) {
+                    fail(CM_ERR_CUDA, "cm_run_schedule: stream wait");
+                    return bail(CM_ERR_CUDA);
+                }
+                if ((st = index_publish(ix, row.n_load, row.load, cs)) != CM_OK) return bail(st);
+                prefetched[r] = 0;
+            } else if ((st = cm_index_load(ix, row.n_load, row.load, src.data(), CM_MEM_HOST, stream)) != CM_OK) {
+                return bail(st);
+            }
             loaded_by_us.insert(loaded_by_us.end(), row.load, row.load + row.n_load);
             S.kernels += hash_kernels;
         }
@@ -598,6 +682,7 @@ extern "C" cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const c
                                            (uint64_t)pl->rows, stream);
             S.queries += pl->rows;
             S.kernels += (pl->n_items ? match_kernels : 0) + 3;
+            if (st == CM_OK) st = prefetch_next(r);   // while this row's plan still holds its space
             cm_match_plan_destroy(pl);  // its table is reused only by work ordered after this row
             if (st != CM_OK) return bail(st);
             if (cudaMemcpyAsync(P.buf[b].offsets, d_offsets, (size_t)(row.n_pairs + 1) * 8, cudaMemcpyDeviceToHost,
@@ -608,6 +693,7 @@ extern "C" cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const c
             S.d2h_bytes += (uint64_t)(row.n_pairs + 1) * 8;
         } else {
             P.buf[b].offsets[0] = 0;
+            if ((st = prefetch_next(r)) != CM_OK) return bail(st);
         }
         if (cudaEventRecord(ev_done[r], cs) != cudaSuccess) {
             fail(CM_ERR_CUDA, "cm_run_schedule: event record");

@@ -247,3 +247,38 @@ def test_autotune_chooses_K_under_an_agreement_floor():
     # a floor of 1.0 leaves only K values whose decisions equal the largest K's
     r2 = index.autotune(wl.pairs[:12], Ks=[4, 8, 16], min_agreement=1.0)
     assert r2["agreement"] == 1.0
+
+
+@pytest.mark.parametrize("strategy", ["per_pair", "pair_blocks", "load_free_list", "graph_partition"])
+def test_other_schedule_strategies_give_the_same_matches(strategy):
+    """Caller-built rows (cm_schedule_from_rows) through the pipeline: rows
+    that reload an image the previous row frees, rows without loads, many
+    small rows; the match lists equal direct matching."""
+    from paper_2505_22089_b300 import strategies as st
+    wl, desc, p, _, host, _ = _grid_case()
+    ib = np.array([cm.image_bytes(p, int(n)) for n in wl.n_desc], dtype=np.int64)
+    budget = int(ib.sum() // 3)
+    order = st.connection_order(wl.pairs, wl.n_images, cm.gps_order)
+    rows = {"per_pair": lambda: st.per_pair(wl.pairs),
+            "pair_blocks": lambda: st.pair_blocks(wl.pairs, ib, budget),
+            "load_free_list": lambda: st.load_free_list(wl.pairs, ib, budget, order),
+            "graph_partition": lambda: st.graph_partition(wl.pairs, ib, budget, order,
+                                                          max(1, int(budget // 2 // ib.max())))}[strategy]()
+    sched = cm.schedule_from_rows(rows, wl.pairs, wl.n_images)
+    sums = desc.astype(np.uint64).sum(0)
+    index = cm.Index(p, wl.n_desc, arena_bytes=cm.schedule_arena_bytes(sched, p, wl.n_desc))
+    index.set_mean(sums, int(wl.total_desc))
+    got = {}
+
+    def collect(row, pair_id, ij, matches):
+        got[pair_id] = matches
+        return 0
+
+    stats, _ = cm.run_schedule(index, sched, host, verify=collect, workers=2)
+    direct = _index(wl, p, desc)
+    plan, best = _direct(direct, wl.pairs)
+    want = _lists(plan, best)
+    assert sorted(got) == list(range(len(wl.pairs)))
+    for k in range(len(wl.pairs)):
+        assert np.array_equal(got[k], want[k]), k
+    assert stats["rows"] == len(rows)
