@@ -122,3 +122,19 @@ def test_host_argument_checks_of_the_later_entry_points():
     assert lib.cm_vlad_workspace_bytes(3, 100, cm.ctypes.byref(b)) == cm.CM_OK and b.value % 256 == 0
     assert lib.cm_nn_workspace_bytes(3, 7, cm.ctypes.byref(b)) == cm.CM_OK and b.value % 256 == 0
     assert lib.cm_nn_workspace_bytes(-1, 7, cm.ctypes.byref(b)) == cm.CM_ERR_INVALID
+
+
+def test_images_above_65535_descriptors_are_rejected():
+    lib = cm.lib()
+    p = cm.Params.make()
+    b = cm.ctypes.c_uint64()
+    assert lib.cm_image_bytes(cm.ctypes.byref(p), 65535, cm.ctypes.byref(b)) == cm.CM_OK
+    assert lib.cm_image_bytes(cm.ctypes.byref(p), 65536, cm.ctypes.byref(b)) == cm.CM_ERR_INVALID
+    nd = np.array([10, 65536], dtype=np.int32)
+    assert lib.cm_index_bytes(cm.ctypes.byref(p), 2, nd.ctypes.data, 0, cm.ctypes.byref(b)) == cm.CM_ERR_INVALID
+    off = np.array([0, 10, 10 + 65536], dtype=np.int64)
+    pr = np.array([[0, 1]], dtype=np.int32)
+    fake = cm.ctypes.c_void_p(1 << 20)   # never dereferenced: the sizes are rejected first
+    assert lib.cm_nn_pairs(fake, off.ctypes.data, 2, pr.ctypes.data, 1, 4, 5, fake, 1 << 30, fake, None, None,
+                           None) == cm.CM_ERR_INVALID
+    assert b"65535" in lib.cm_last_error()
