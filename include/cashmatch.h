@@ -269,6 +269,25 @@ cm_status cm_match_plan_compact(cm_match_plan* pl, const int32_t* d_best_j, uint
  * decisions.  d_best_in: a cm_match_plan_run best_j output; d_best_out: a
  * distinct device array of the same rows.  Async. */
 cm_status cm_match_plan_mutual(cm_match_plan* pl, const int32_t* d_best_in, int32_t* d_best_out, cm_stream stream);
+/* Device workspace of cm_match_plan_sao for this plan. */
+cm_status cm_match_plan_sao_bytes(const cm_match_plan* pl, uint64_t* bytes);
+/* The SAO local constraint (see cm_sao_filter: same neighbours, orders,
+ * scores and decisions, bit for bit) on the GPU for every pair of the plan:
+ * each pair's initial matches are the queries with d_best_in >= 0, in query
+ * order; a match whose score exceeds max_score gets -1 in d_best_out, so the
+ * compaction that follows hands only kept matches to verification.
+ *  - d_best_in: a cm_match_plan_run best_j; d_best_out may be the same array.
+ *  - d_kp: device float [rows][2] keypoints of all images concatenated;
+ *    d_kp_off: device int64 [n_images + 1] first row of each image there.
+ *  - k_nn: 1..16; max_score >= 0.
+ *  - d_score (optional): device float per plan row, the match's score (0 for
+ *    rows without a match).
+ *  - d_work / work_bytes: cm_match_plan_sao_bytes, 256-byte aligned.
+ * Asynchronous on `stream`.  Errors: CM_ERR_INVALID, CM_ERR_STATE (index
+ * destroyed), CM_ERR_BUDGET (workspace), CM_ERR_CUDA. */
+cm_status cm_match_plan_sao(cm_match_plan* pl, const int32_t* d_best_in, int32_t* d_best_out, const float* d_kp,
+                            const int64_t* d_kp_off, int32_t k_nn, float max_score, float* d_score, void* d_work,
+                            uint64_t work_bytes, cm_stream stream);
 void cm_match_plan_destroy(cm_match_plan* pl);
 /* Convenience: plan, run on stream, wait for the stream, destroy the plan. */
 cm_status cm_match_pairs(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, const cm_match_out* out,

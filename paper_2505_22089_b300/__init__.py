@@ -52,7 +52,8 @@ EXPORTS = [
     "cm_match_plan_compact", "cm_match_plan_mutual", "cm_match_plan_destroy", "cm_match_pairs", "cm_sequence_create", "cm_sequence_launch",
     "cm_sequence_kernels", "cm_sequence_destroy", "cm_schedule_arena_bytes", "cm_pipeline_workspace_bytes", "cm_run_schedule",
     "cm_verify_affine", "cm_affine_verify_cb", "cm_sao_filter", "cm_schedule_from_rows", "cm_vlad_workspace_bytes", "cm_vlad_encode",
-    "cm_workspace_status", "cm_nn_workspace_bytes", "cm_nn_pairs", "cm_selftest_wait", "cm_autotune", "cm_match_pair_noalloc",
+    "cm_workspace_status", "cm_nn_workspace_bytes", "cm_nn_pairs", "cm_selftest_wait", "cm_match_plan_sao_bytes",
+    "cm_match_plan_sao", "cm_autotune", "cm_match_pair_noalloc",
 ]
 
 
@@ -184,6 +185,8 @@ def lib():
             "cm_vlad_encode": (i32, [vp, vp, i32, vp, i32, vp, u64, vp, vp, vp]),
             "cm_workspace_status": (i32, [vp, vp]),
             "cm_selftest_wait": (i32, [i32, vp]),
+            "cm_match_plan_sao_bytes": (i32, [vp, ctypes.POINTER(u64)]),
+            "cm_match_plan_sao": (i32, [vp, vp, vp, vp, vp, i32, ctypes.c_float, vp, vp, u64, vp]),
             "cm_nn_workspace_bytes": (i32, [i32, i64, ctypes.POINTER(u64)]),
             "cm_nn_pairs": (i32, [vp, vp, i32, vp, i64, i32, i32, vp, u64, vp, vp, vp, vp]),
             "cm_autotune": (i32, [vp, vp, i64, vp, i32, ctypes.c_float, vp, ctypes.POINTER(TuneResult)]),
@@ -613,6 +616,23 @@ class MatchPlan:
         out = torch.empty_like(best_j)
         check(lib().cm_match_plan_mutual(self.h, _ptr(best_j), _ptr(out), _stream(stream)))
         return out
+
+    def sao(self, best_j, kp, kp_off, k: int = 8, max_score: float = 0.875, stream=None, want_score: bool = False):
+        """cm_match_plan_sao: decisions with the SAO local constraint applied
+        (new CUDA tensor) and, optionally, the per-row scores.  kp: CUDA float
+        [rows][2] of all images, kp_off: CUDA int64 [n_images + 1]."""
+        import torch
+        out = torch.empty_like(best_j)
+        b = ctypes.c_uint64()
+        check(lib().cm_match_plan_sao_bytes(self.h, ctypes.byref(b)))
+        work = torch.empty(int(b.value) + 256, dtype=torch.uint8, device=best_j.device)
+        wbase = (work.data_ptr() + 255) // 256 * 256
+        score = torch.empty(best_j.numel(), dtype=torch.float32, device=best_j.device) if want_score else None
+        check(lib().cm_match_plan_sao(self.h, _ptr(best_j), _ptr(out), _ptr(kp), _ptr(kp_off), int(k),
+                                      float(max_score), _ptr(score), ctypes.c_void_p(wbase), int(b.value),
+                                      _stream(stream)))
+        self._sao_work = work   # kept until the next call: the launch may still read it
+        return (out, score) if want_score else out
 
     def close(self):
         if getattr(self, "h", None):
