@@ -384,6 +384,25 @@ cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const cm_pair* pai
                           const uint8_t* const* desc_host, void* d_work, uint64_t work_bytes, cm_verify_fn verify,
                           void* user, int32_t n_workers, cm_stream stream, cm_pipeline_stats* stats);
 
+/* Options of cm_run_schedule_ex.  sao_k > 0 runs the SAO local constraint
+ * on the GPU for every row, right after the match launch
+ * (cm_match_plan_sao), so verification receives only the kept matches;
+ * d_kp / d_kp_off are as in cm_match_plan_sao and must cover every image. */
+typedef struct cm_pipeline_opts {
+    int32_t sao_k;             /* 0: off; 1..16 */
+    float sao_max_score;
+    const float* d_kp;         /* device float [rows][2], all images concatenated */
+    const int64_t* d_kp_off;   /* device int64 [n_images + 1] */
+} cm_pipeline_opts;
+/* cm_pipeline_workspace_bytes for a run with these options (NULL: none). */
+cm_status cm_pipeline_workspace_bytes_ex(const cm_index* ix, const cm_schedule* s, const cm_pair* pairs,
+                                         int64_t n_pairs, const cm_pipeline_opts* opts, uint64_t* bytes);
+/* cm_run_schedule with options (NULL: the same as cm_run_schedule). */
+cm_status cm_run_schedule_ex(cm_index* ix, const cm_schedule* s, const cm_pair* pairs, int64_t n_pairs,
+                             const uint8_t* const* desc_host, void* d_work, uint64_t work_bytes, cm_verify_fn verify,
+                             void* user, int32_t n_workers, const cm_pipeline_opts* opts, cm_stream stream,
+                             cm_pipeline_stats* stats);
+
 /* RANSAC fit of a 2-D affine map u = A [x y 1]^T from the query image's
  * keypoints to the database image's over one pair's matches (the global
  * geometric constraint of Sec. 2.3.2; an affine map is exact for the planar

@@ -53,7 +53,7 @@ EXPORTS = [
     "cm_sequence_kernels", "cm_sequence_destroy", "cm_schedule_arena_bytes", "cm_pipeline_workspace_bytes", "cm_run_schedule",
     "cm_verify_affine", "cm_affine_verify_cb", "cm_sao_filter", "cm_schedule_from_rows", "cm_vlad_workspace_bytes", "cm_vlad_encode",
     "cm_workspace_status", "cm_nn_workspace_bytes", "cm_nn_pairs", "cm_selftest_wait", "cm_match_plan_sao_bytes",
-    "cm_match_plan_sao", "cm_autotune", "cm_match_pair_noalloc",
+    "cm_match_plan_sao", "cm_pipeline_workspace_bytes_ex", "cm_run_schedule_ex", "cm_autotune", "cm_match_pair_noalloc",
 ]
 
 
@@ -110,6 +110,11 @@ class AffineVerifier(ctypes.Structure):
 
 VERIFY_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                              ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32))
+
+
+class PipelineOpts(ctypes.Structure):
+    _fields_ = [("sao_k", ctypes.c_int32), ("sao_max_score", ctypes.c_float), ("d_kp", ctypes.c_void_p),
+                ("d_kp_off", ctypes.c_void_p)]
 
 
 class TuneResult(ctypes.Structure):
@@ -187,6 +192,8 @@ def lib():
             "cm_selftest_wait": (i32, [i32, vp]),
             "cm_match_plan_sao_bytes": (i32, [vp, ctypes.POINTER(u64)]),
             "cm_match_plan_sao": (i32, [vp, vp, vp, vp, vp, i32, ctypes.c_float, vp, vp, u64, vp]),
+            "cm_pipeline_workspace_bytes_ex": (i32, [vp, vp, vp, i64, vp, ctypes.POINTER(u64)]),
+            "cm_run_schedule_ex": (i32, [vp, vp, vp, i64, vp, vp, u64, vp, vp, i32, vp, vp, vp]),
             "cm_nn_workspace_bytes": (i32, [i32, i64, ctypes.POINTER(u64)]),
             "cm_nn_pairs": (i32, [vp, vp, i32, vp, i64, i32, i32, vp, u64, vp, vp, vp, vp]),
             "cm_autotune": (i32, [vp, vp, i64, vp, i32, ctypes.c_float, vp, ctypes.POINTER(TuneResult)]),
@@ -700,18 +707,25 @@ def compact_out(plan: "MatchPlan", capacity: int | None = None) -> dict:
 
 def run_schedule(index: Index, sched: Schedule, desc_host, verify=None, keypoints=None, thresh_px: float = 3.0,
                  max_iters: int = 500, seed: int = 7, workers: int = 4, stream=None, sao_k: int = 0,
-                 sao_max_score: float = 0.875, sao_kept=None):
+                 sao_max_score: float = 0.875, sao_kept=None, gpu_sao_k: int = 0, kp_dev=None, kp_off_dev=None):
     """cm_run_schedule.  desc_host: per image a host uint8 [n][128] array or
     pinned CPU tensor.  verify: None (count matches only), "affine" (the
     library's RANSAC callback over `keypoints`, per image float [n][2], after
     the SAO local constraint when sao_k > 0; sao_kept: optional int64 array,
     one entry per pair, receiving the matches SAO kept), or a Python callable
-    f(row, pair_id, (i, j), matches: np.ndarray uint32) -> int.
+    f(row, pair_id, (i, j), matches: np.ndarray uint32) -> int.  gpu_sao_k > 0
+    runs the SAO constraint on the GPU for every row before the matches reach
+    the host (kp_dev: CUDA float [rows][2] of all images, kp_off_dev: CUDA
+    int64 [n_images + 1]); verification then sees only the kept matches.
     Returns (stats dict, inliers per pair or None)."""
     import torch
     pairs = sched.pairs
+    opts = None
+    if gpu_sao_k:
+        opts = PipelineOpts(int(gpu_sao_k), float(sao_max_score), kp_dev.data_ptr(), kp_off_dev.data_ptr())
     ws = ctypes.c_uint64()
-    check(lib().cm_pipeline_workspace_bytes(index.h, sched.h, pairs.ctypes.data, len(pairs), ctypes.byref(ws)))
+    check(lib().cm_pipeline_workspace_bytes_ex(index.h, sched.h, pairs.ctypes.data, len(pairs),
+                                               ctypes.byref(opts) if opts is not None else None, ctypes.byref(ws)))
     work = torch.empty(int(ws.value) + 256, dtype=torch.uint8, device="cuda")
     wbase = (work.data_ptr() + 255) // 256 * 256
     ptrs = (ctypes.c_void_p * len(desc_host))(*[d.data_ptr() if hasattr(d, "data_ptr") else
@@ -740,7 +754,9 @@ def run_schedule(index: Index, sched: Schedule, desc_host, verify=None, keypoint
         keep.append(cb)
         fn = ctypes.cast(cb, ctypes.c_void_p)
     st = PipelineStats()
-    check(lib().cm_run_schedule(index.h, sched.h, pairs.ctypes.data, len(pairs), ptrs, ctypes.c_void_p(wbase),
-                                int(ws.value), fn, user, int(workers), _stream(stream), ctypes.byref(st)))
+    check(lib().cm_run_schedule_ex(index.h, sched.h, pairs.ctypes.data, len(pairs), ptrs, ctypes.c_void_p(wbase),
+                                   int(ws.value), fn, user, int(workers),
+                                   ctypes.byref(opts) if opts is not None else None, _stream(stream),
+                                   ctypes.byref(st)))
     del keep
     return st.as_dict(), inliers

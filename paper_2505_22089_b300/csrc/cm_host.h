@@ -268,6 +268,8 @@ cm_status index_prefetch(cm_index* ix, int32_t count, const int32_t* ids, const 
                          cudaStream_t copy_stream, bool* placed);
 cm_status index_publish(cm_index* ix, int32_t count, const int32_t* ids, cudaStream_t s);
 void index_cancel_prefetch(cm_index* ix, int32_t count, const int32_t* ids);
+// Device workspace of cm_match_plan_sao for a plan of n_pairs pairs and rows query rows.
+uint64_t sao_work_bytes(int64_t n_pairs, int64_t rows);
 }  // namespace cm
 
 // Arena bytes of a plan: its pair table, the work counter and, for the

@@ -287,20 +287,25 @@ extern "C" int32_t cm_affine_verify_cb(void* user, int32_t, int64_t pair_id, con
 namespace {
 
 struct WorkLayout {
-    uint64_t best_j, counts, offsets, total;
+    uint64_t best_j, counts, offsets, sao, sao_bytes, total;
 };
 
-// Workspace of the largest row: best_j per query, counts and offsets (+ total) per pair.
-WorkLayout work_layout(int64_t max_rows, int64_t max_pairs) {
+// Workspace of the largest row: best_j per query, counts and offsets (+ total)
+// per pair, and, with the GPU SAO constraint, its compaction scratch.
+WorkLayout work_layout(int64_t max_rows, int64_t max_pairs, bool sao) {
     WorkLayout w{};
     uint64_t o = 0;
     auto take = [&](uint64_t bytes) { uint64_t at = o; o = align_up(o + bytes); return at; };
     w.best_j = take((uint64_t)std::max<int64_t>(max_rows, 1) * 4);
     w.counts = take((uint64_t)std::max<int64_t>(max_pairs, 1) * 4);
     w.offsets = take((uint64_t)(max_pairs + 1) * 8);  // the total sits right after the offsets
+    w.sao_bytes = sao ? sao_work_bytes(max_pairs, max_rows) : 0;
+    w.sao = take(w.sao_bytes);
     w.total = o;
     return w;
 }
+
+bool sao_on(const cm_pipeline_opts* o) { return o && o->sao_k > 0; }
 
 cm_status row_sizes(const cm_index* ix, const cm_schedule* s, const cm_pair* pairs, int64_t n_pairs, int64_t* max_rows,
                     int64_t* max_pairs) {
@@ -477,29 +482,44 @@ extern "C" cm_status cm_schedule_arena_bytes(const cm_schedule* s, const cm_para
     return CM_OK;
 }
 
-extern "C" cm_status cm_pipeline_workspace_bytes(const cm_index* ix, const cm_schedule* s, const cm_pair* pairs,
-                                                 int64_t n_pairs, uint64_t* bytes) {
+extern "C" cm_status cm_pipeline_workspace_bytes_ex(const cm_index* ix, const cm_schedule* s, const cm_pair* pairs,
+                                                    int64_t n_pairs, const cm_pipeline_opts* opts, uint64_t* bytes) {
     if (!ix || !s || !bytes || n_pairs < 0 || (n_pairs && !pairs))
         return fail(CM_ERR_INVALID, "cm_pipeline_workspace_bytes: bad argument");
     int64_t mr = 0, mp = 0;
     cm_status st = row_sizes(ix, s, pairs, n_pairs, &mr, &mp);
     if (st != CM_OK) return st;
-    *bytes = work_layout(mr, mp).total;
+    *bytes = work_layout(mr, mp, sao_on(opts)).total;
     return CM_OK;
+}
+
+extern "C" cm_status cm_pipeline_workspace_bytes(const cm_index* ix, const cm_schedule* s, const cm_pair* pairs,
+                                                 int64_t n_pairs, uint64_t* bytes) {
+    return cm_pipeline_workspace_bytes_ex(ix, s, pairs, n_pairs, nullptr, bytes);
 }
 
 extern "C" cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const cm_pair* pairs, int64_t n_pairs,
                                      const uint8_t* const* desc_host, void* d_work, uint64_t work_bytes,
                                      cm_verify_fn verify, void* user, int32_t n_workers, cm_stream stream,
                                      cm_pipeline_stats* stats) {
+    return cm_run_schedule_ex(ix, s, pairs, n_pairs, desc_host, d_work, work_bytes, verify, user, n_workers, nullptr,
+                              stream, stats);
+}
+
+extern "C" cm_status cm_run_schedule_ex(cm_index* ix, const cm_schedule* s, const cm_pair* pairs, int64_t n_pairs,
+                                        const uint8_t* const* desc_host, void* d_work, uint64_t work_bytes,
+                                        cm_verify_fn verify, void* user, int32_t n_workers,
+                                        const cm_pipeline_opts* opts, cm_stream stream, cm_pipeline_stats* stats) {
     const auto t_start = Clock::now();
     if (!ix || !s || !desc_host || !d_work || n_pairs < 0 || (n_pairs && !pairs) || n_workers < 1 || n_workers > 256)
         return fail(CM_ERR_INVALID, "cm_run_schedule: bad argument");
+    if (sao_on(opts) && (opts->sao_k > 16 || !opts->d_kp || !opts->d_kp_off || !(opts->sao_max_score >= 0.f)))
+        return fail(CM_ERR_INVALID, "cm_run_schedule: bad SAO options (1 <= sao_k <= 16, keypoints on the device)");
     if (!ix->mean_set) return fail(CM_ERR_STATE, "cm_run_schedule: centring mean not set");
     int64_t max_rows = 0, max_pairs = 0;
     cm_status st = row_sizes(ix, s, pairs, n_pairs, &max_rows, &max_pairs);
     if (st != CM_OK) return st;
-    const WorkLayout wl = work_layout(max_rows, max_pairs);
+    const WorkLayout wl = work_layout(max_rows, max_pairs, sao_on(opts));
     if (work_bytes < wl.total)
         return fail(CM_ERR_BUDGET, "cm_run_schedule: workspace %llu bytes, %llu needed", (unsigned long long)work_bytes,
                     (unsigned long long)wl.total);
@@ -677,6 +697,11 @@ extern "C" cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const c
             cm_match_out mo{};
             mo.best_j = d_best;
             st = cm_match_plan_run(pl, &mo, stream);
+            if (st == CM_OK && sao_on(opts)) {   // local constraint on the GPU: rejected matches leave best_j
+                st = cm_match_plan_sao(pl, d_best, d_best, opts->d_kp, opts->d_kp_off, opts->sao_k,
+                                       opts->sao_max_score, nullptr, work + wl.sao, wl.sao_bytes, stream);
+                S.kernels += 4;
+            }
             if (st == CM_OK)
                 st = cm_match_plan_compact(pl, d_best, d_counts, d_offsets, d_offsets + row.n_pairs, P.buf[b].d_matches,
                                            (uint64_t)pl->rows, stream);

@@ -244,6 +244,8 @@ SaoWork sao_layout(int64_t n_pairs, int64_t rows) {
 
 }  // namespace
 
+uint64_t sao_work_bytes(int64_t n_pairs, int64_t rows) { return sao_layout(n_pairs, rows).total; }
+
 }  // namespace cm
 
 using namespace cm;

@@ -282,3 +282,30 @@ def test_other_schedule_strategies_give_the_same_matches(strategy):
     for k in range(len(wl.pairs)):
         assert np.array_equal(got[k], want[k]), k
     assert stats["rows"] == len(rows)
+
+
+def test_pipeline_with_the_gpu_sao_constraint():
+    """SAO on the GPU inside the pipeline: verification receives exactly the
+    matches the host form keeps from the unfiltered lists."""
+    wl, desc, p, sched, host, kps = _grid_case()
+    index = _pipeline_index(wl, p, desc)
+    kp_all = np.concatenate(kps).astype(np.float32)
+    kp_dev = torch.from_numpy(kp_all).cuda()
+    off_dev = torch.from_numpy(wl.row_off.astype(np.int64)).cuda()
+    got = {}
+
+    def collect(row, pair_id, ij, matches):
+        got[pair_id] = matches
+        return 0
+
+    stats, _ = cm.run_schedule(index, sched, host, verify=collect, workers=3, gpu_sao_k=8, sao_max_score=0.875,
+                               kp_dev=kp_dev, kp_off_dev=off_dev)
+    direct = _index(wl, p, desc)
+    plan, best = _direct(direct, wl.pairs)
+    want = _lists(plan, best)
+    kept = 0
+    for k, (i, j) in enumerate(wl.pairs):
+        _, keep, n = cm.sao_filter(kps[i], kps[j], want[k], 8, 0.875)
+        assert np.array_equal(got[k], want[k][keep]), k
+        kept += n
+    assert stats["matches"] == kept
