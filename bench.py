@@ -13,8 +13,9 @@ with the descriptors already resident in HBM (headline rerank form; the other
 forms are timed the same way under "forms").  `e2e` runs the public pipeline
 call with the descriptors in pinned host memory: H2D, matching and the D2H of
 the match lists are inside its timed region.  "pipeline_verified" repeats it
-with outlier removal on the host cores overlapped with the GPU rows: affine
-RANSAC alone, and the SAO local constraint ahead of RANSAC.
+with outlier removal overlapped with the GPU rows: affine RANSAC alone on the
+host cores, the SAO local constraint ahead of it on the host, and SAO on the
+GPU (per block row, before the matches reach the host) ahead of it.
 
 The workloads are synthetic stand-ins for the paper's UAV datasets (see
 synth/).  `--impl reference` times the FP64 CPU oracle on the host cores on a
@@ -367,17 +368,24 @@ def pipeline_e2e(args, wl, host, kp, sums, stream, world, dev):
         # RANSAC alone, then the SAO local constraint ahead of RANSAC (Sec. 2.3.3)
         kl = [kp[off[i]:off[i + 1]] for i in range(wl.n_images)]
         ver = {"overlap": "GPU rows overlap CPU verification when wall_ms < gpu_ms + verify_ms / workers"}
-        for mode, sao_k in (("ransac", 0), ("sao_ransac", 8)):
+        kp_dev = torch.from_numpy(np.ascontiguousarray(kp, dtype=np.float32)).to(dev)
+        kp_off_dev = torch.from_numpy(off.astype(np.int64)).to(dev)
+        for mode, sao_k, gpu_sao_k in (("ransac", 0, 0), ("sao_ransac", 8, 0), ("gpu_sao_ransac", 0, 8)):
             kept = np.zeros(len(wl.pairs), dtype=np.int64)
             st, inl = cm.run_schedule(index, sched, hl, verify="affine", keypoints=kl, thresh_px=4.0,
-                                      workers=args.verify_workers, stream=stream, sao_k=sao_k, sao_kept=kept)
+                                      workers=args.verify_workers, stream=stream, sao_k=sao_k, sao_kept=kept,
+                                      gpu_sao_k=gpu_sao_k, kp_dev=kp_dev, kp_off_dev=kp_off_dev)
             v = {k: (round(x, 2) if isinstance(x, float) else x) for k, x in st.items()}
             v["inliers"] = int(inl.sum())
             v["inlier_share"] = float(inl.sum() / max(1, st["matches"]))
             if sao_k:
                 v["sao_kept"] = int(kept.sum())
-                v["sao"] = {"k": sao_k, "max_score": 0.875}
+                v["sao"] = {"k": sao_k, "max_score": 0.875, "where": "host worker threads"}
+            if gpu_sao_k:
+                v["sao"] = {"k": gpu_sao_k, "max_score": 0.875, "where": "GPU, per block row before compaction",
+                            "note": "matches counts the kept ones"}
             ver[mode] = v
+        del kp_dev, kp_off_dev
     index.close()
     sched.close()
     return out, ver
