@@ -4,18 +4,19 @@
 //
 // The plan's decisions are first compacted into per-pair match lists in the
 // workspace (query order, as the verifier receives them).  Then one CTA per
-// pair walks its list in chunks of 256 matches, one thread per match:
-//   - nearest neighbours, in the query image and then in the database image:
-//     the pair's matched keypoints stream through shared memory in tiles of
-//     1,024 and each thread keeps the T = k + 4 smallest FP32 squared
-//     distances (by distance, then index); those T are re-scored exactly in
-//     FP64 and sorted by (d^2, index).  The FP32 pre-selection is exact:
-//     every point left out has an FP32 distance at least that of the T-th,
-//     hence an exact one above d_T / (1 + 1e-6); when the k-th exact distance
-//     is not below that bound, the thread scans all points in FP64 instead;
-//   - angular order by half-plane and the sign of an exact cross product,
-//     the cyclic edit distance of the two label sequences, the score and the
-//     decision, with the same roundings as the host (no fused multiply-adds).
+// pair:
+//   - builds, for the query image and for the database image, a uniform grid
+//     over the pair's matched keypoints (about two per cell, shaped like the
+//     bounding box; a counting sort into workspace memory);
+//   - walks its list in chunks of 256 matches, one thread per match: the
+//     exact k nearest neighbours by (d^2 in FP64, entry index), searched ring
+//     by ring with cells skipped when their distance bound exceeds the k-th
+//     and the search stopped once no unvisited cell can hold a closer point
+//     (the bounds carry a slack for coordinates rounded into a neighbouring
+//     cell); then the angular order by half-plane and the sign of an exact
+//     cross product, the cyclic edit distance of the two label sequences, the
+//     score and the decision, with the host's roundings (no fused
+//     multiply-adds in the FP64 arithmetic).
 // A rejected match's decision becomes -1 in the output, so the usual
 // compaction afterwards hands only the kept matches to verification.
 #include <cuda_runtime.h>
@@ -29,7 +30,6 @@ namespace cm {
 namespace {
 
 constexpr int kSaoThreads = 256;
-constexpr int kSaoTile = 1024;
 constexpr int kSaoMaxK = 16;
 
 // One space (query or database image) of a pair's match list: entry e has its
@@ -62,99 +62,186 @@ __device__ __forceinline__ bool ray_less(double ax, double ay, int al, double bx
     return al < bl;
 }
 
-// Exact k nearest list entries of entry m in one space, by (d^2, entry), then
-// their labels in angular order around m.  Returns the neighbour count.
-template <int T>
-__device__ int neighbours(const uint32_t* list, int n, int m, bool active, Space sp, int k, float* tx, float* ty,
-                          int32_t* labels) {
-    const int tid = threadIdx.x;
-    float2 me = make_float2(0.f, 0.f);
-    if (active) me = sp.at(list, m);
-    // FP32 pre-selection of T candidates, kept as (float bits << 32 | entry), ascending
-    uint64_t s[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) s[t] = ~0ull;
-    for (int t0 = 0; t0 < n; t0 += kSaoTile) {
-        __syncthreads();
-        for (int u = tid; u < kSaoTile && t0 + u < n; u += kSaoThreads) {
-            const float2 p = sp.at(list, t0 + u);
-            tx[u] = p.x;
-            ty[u] = p.y;
-        }
-        __syncthreads();
-        if (!active) continue;
-        const int lim = min(kSaoTile, n - t0);
-        for (int u = 0; u < lim; ++u) {
-            const float dx = tx[u] - me.x, dy = ty[u] - me.y;
-            const float d = dx * dx + dy * dy;
-            const uint64_t key = ((uint64_t)__float_as_uint(d) << 32) | (uint32_t)(t0 + u);
-            if (key < s[T - 1] && t0 + u != m) {
-#pragma unroll
-                for (int i = T - 1; i > 0; --i) s[i] = max(s[i - 1], min(s[i], key));
-                s[0] = min(s[0], key);
-            }
-        }
+// A grid over one space of a pair's match list, in the pair's workspace.
+struct Grid {
+    double x0, y0, csx, csy, slack;
+    int gx, gy;
+    int32_t* start;   // [gx * gy + 1] first sorted entry of each cell
+    float2* pts;      // [n] keypoints in cell order
+    int32_t* ids;     // [n] their list entries
+};
+
+__device__ __forceinline__ int cell_coord(double v, double cs, int g) {
+    const int c = (int)(v / cs);
+    return c < 0 ? 0 : (c >= g ? g - 1 : c);
+}
+
+// Builds the grid of one space (all threads of the CTA take part).
+__device__ void build_grid(const uint32_t* list, int n, Space sp, Grid& G, int32_t* fill, double* red) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    float lo_x = __uint_as_float(0x7F800000u), lo_y = lo_x, hi_x = -lo_x, hi_y = -lo_x;
+    for (int e = tid; e < n; e += kSaoThreads) {
+        const float2 p = sp.at(list, e);
+        lo_x = fminf(lo_x, p.x);
+        lo_y = fminf(lo_y, p.y);
+        hi_x = fmaxf(hi_x, p.x);
+        hi_y = fmaxf(hi_y, p.y);
     }
-    if (!active) return 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo_x = fminf(lo_x, __shfl_xor_sync(0xFFFFFFFFu, lo_x, o));
+        lo_y = fminf(lo_y, __shfl_xor_sync(0xFFFFFFFFu, lo_y, o));
+        hi_x = fmaxf(hi_x, __shfl_xor_sync(0xFFFFFFFFu, hi_x, o));
+        hi_y = fmaxf(hi_y, __shfl_xor_sync(0xFFFFFFFFu, hi_y, o));
+    }
+    __syncthreads();   // red may still be read from the previous build
+    if (lane == 0) {
+        red[4 * w + 0] = lo_x;
+        red[4 * w + 1] = lo_y;
+        red[4 * w + 2] = hi_x;
+        red[4 * w + 3] = hi_y;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double x0 = red[0], y0 = red[1], x1 = red[2], y1 = red[3];
+        for (int k = 1; k < kSaoThreads / 32; ++k) {
+            x0 = fmin(x0, red[4 * k]);
+            y0 = fmin(y0, red[4 * k + 1]);
+            x1 = fmax(x1, red[4 * k + 2]);
+            y1 = fmax(y1, red[4 * k + 3]);
+        }
+        const double wd = x1 - x0, hd = y1 - y0;
+        const double cells = fmax(1.0, floor((double)n / 2.0));
+        int gx, gy;
+        if (wd > 0 && hd > 0) {
+            gx = (int)fmin(fmax(round(sqrt(cells * wd / hd)), 1.0), cells);
+            gy = (int)fmin(fmax(round(cells / gx), 1.0), cells);
+        } else {
+            gx = wd > 0 ? (int)cells : 1;
+            gy = hd > 0 ? (int)cells : 1;
+        }
+        G.x0 = x0;
+        G.y0 = y0;
+        G.gx = gx;
+        G.gy = gy;
+        G.csx = wd > 0 ? wd / gx : 1.0;
+        G.csy = hd > 0 ? hd / gy : 1.0;
+        G.slack = 1e-9 * (wd + hd + fabs(x0) + fabs(y0) + 1.0);
+    }
+    __syncthreads();
+    const int nc = G.gx * G.gy;
+    for (int c = tid; c < nc; c += kSaoThreads) fill[c] = 0;
+    __syncthreads();
+    for (int e = tid; e < n; e += kSaoThreads) {
+        const float2 p = sp.at(list, e);
+        const int c = cell_coord((double)p.x - G.x0, G.csx, G.gx) + G.gx * cell_coord((double)p.y - G.y0, G.csy, G.gy);
+        atomicAdd(&fill[c], 1);
+    }
+    __syncthreads();
+    // exclusive prefix of the counts into start (chunks of the CTA), then fill restarts at 0
+    __shared__ int s_part[kSaoThreads];
+    __shared__ int s_carry;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nc; base += kSaoThreads) {
+        const int c = base + tid;
+        const int v = c < nc ? fill[c] : 0;
+        s_part[tid] = v;
+        __syncthreads();
+        for (int o = 1; o < kSaoThreads; o <<= 1) {
+            const int add = tid >= o ? s_part[tid - o] : 0;
+            __syncthreads();
+            s_part[tid] += add;
+            __syncthreads();
+        }
+        if (c < nc) {
+            G.start[c] = s_carry + s_part[tid] - v;
+            fill[c] = 0;
+        }
+        __syncthreads();
+        if (tid == kSaoThreads - 1) s_carry += s_part[tid];
+        __syncthreads();
+    }
+    if (tid == 0) G.start[nc] = n;
+    __syncthreads();
+    for (int e = tid; e < n; e += kSaoThreads) {
+        const float2 p = sp.at(list, e);
+        const int c = cell_coord((double)p.x - G.x0, G.csx, G.gx) + G.gx * cell_coord((double)p.y - G.y0, G.csy, G.gy);
+        const int pos = G.start[c] + atomicAdd(&fill[c], 1);
+        G.pts[pos] = p;
+        G.ids[pos] = e;
+    }
+    __syncthreads();
+}
+
+// Exact k nearest list entries of entry m by (d^2, entry), then their labels
+// in angular order around m.  Returns the neighbour count.
+__device__ int neighbours(const uint32_t* list, int n, int m, Space sp, const Grid& G, int k, int32_t* labels) {
     const int want = min(k, n - 1);
     if (want <= 0) return 0;
-    const int have = min(T, n - 1);
-    // exact FP64 distances of the candidates, sorted by (d^2, entry)
-    double dd[T];
-    int ee[T];
-    const double mx = me.x, my = me.y;
-    for (int c = 0; c < have; ++c) {
-        const int e = (int)(s[c] & 0xFFFFFFFFu);
-        const float2 p = sp.at(list, e);
-        const double d = d2_exact(mx, my, p.x, p.y);
-        int pos = c;
-        while (pos > 0 && (d < dd[pos - 1] || (d == dd[pos - 1] && e < ee[pos - 1]))) {
-            dd[pos] = dd[pos - 1];
-            ee[pos] = ee[pos - 1];
-            --pos;
-        }
-        dd[pos] = d;
-        ee[pos] = e;
-    }
-    if (have < n - 1) {
-        // a point outside the candidates has an exact distance above this bound
-        const double bound = (double)__uint_as_float((uint32_t)(s[T - 1] >> 32)) / (1.0 + 1e-6);
-        if (!(dd[want - 1] < bound)) {
-            // not decided by the pre-selection: every point in FP64
-            for (int c = 0; c < want; ++c) {
-                dd[c] = __longlong_as_double(0x7FF0000000000000ll);
-                ee[c] = 0x7FFFFFFF;
-            }
-            for (int e = 0; e < n; ++e) {
-                if (e == m) continue;
-                const float2 p = sp.at(list, e);
-                const double d = d2_exact(mx, my, p.x, p.y);
-                if (!(d < dd[want - 1] || (d == dd[want - 1] && e < ee[want - 1]))) continue;
-                int pos = want - 1;
-                while (pos > 0 && (d < dd[pos - 1] || (d == dd[pos - 1] && e < ee[pos - 1]))) {
-                    dd[pos] = dd[pos - 1];
-                    ee[pos] = ee[pos - 1];
-                    --pos;
+    const float2 me = sp.at(list, m);
+    const double px = me.x, py = me.y;
+    const int cx = cell_coord(px - G.x0, G.csx, G.gx), cy = cell_coord(py - G.y0, G.csy, G.gy);
+    double dd[kSaoMaxK];
+    int ee[kSaoMaxK];
+    int cnt = 0;   // dd / ee ascending by (d^2, entry)
+    for (int r = 0;; ++r) {
+        const int xa = cx - r, xb = cx + r, ya = cy - r, yb = cy + r;
+        for (int yy = max(ya, 0); yy <= min(yb, G.gy - 1); ++yy) {
+            const bool edge_row = yy == ya || yy == yb;
+            const double gy0 = G.y0 + yy * G.csy - G.slack - py, gy1 = py - (G.y0 + (yy + 1) * G.csy + G.slack);
+            const double ry = gy0 > 0 ? gy0 : (gy1 > 0 ? gy1 : 0.0);
+            const int x_lo = max(xa, 0), x_hi = min(xb, G.gx - 1);
+            for (int xx = x_lo; xx <= x_hi; ++xx) {
+                if (!edge_row && xx != xa && xx != xb) continue;   // the ring only
+                if (cnt == want) {   // a cell that cannot hold a point closer than the k-th
+                    const double gx0 = G.x0 + xx * G.csx - G.slack - px, gx1 = px - (G.x0 + (xx + 1) * G.csx + G.slack);
+                    const double rx = gx0 > 0 ? gx0 : (gx1 > 0 ? gx1 : 0.0);
+                    if (__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)) > dd[cnt - 1]) continue;
                 }
-                dd[pos] = d;
-                ee[pos] = e;
+                const int c = yy * G.gx + xx;
+                for (int t = G.start[c]; t < G.start[c + 1]; ++t) {
+                    const int e = G.ids[t];
+                    if (e == m) continue;
+                    const float2 p = G.pts[t];
+                    const double d = d2_exact(px, py, p.x, p.y);
+                    if (cnt == want && !(d < dd[cnt - 1] || (d == dd[cnt - 1] && e < ee[cnt - 1]))) continue;
+                    int pos = cnt < want ? cnt++ : cnt - 1;
+                    while (pos > 0 && (d < dd[pos - 1] || (d == dd[pos - 1] && e < ee[pos - 1]))) {
+                        dd[pos] = dd[pos - 1];
+                        ee[pos] = ee[pos - 1];
+                        --pos;
+                    }
+                    dd[pos] = d;
+                    ee[pos] = e;
+                }
             }
+        }
+        if (xa <= 0 && ya <= 0 && xb >= G.gx - 1 && yb >= G.gy - 1) break;
+        if (cnt == want) {   // distance from p to the nearest cell outside the visited block
+            double lb = __longlong_as_double(0x7FF0000000000000ll);
+            if (xa > 0) lb = fmin(lb, px - (G.x0 + xa * G.csx));
+            if (xb < G.gx - 1) lb = fmin(lb, G.x0 + (xb + 1) * G.csx - px);
+            if (ya > 0) lb = fmin(lb, py - (G.y0 + ya * G.csy));
+            if (yb < G.gy - 1) lb = fmin(lb, G.y0 + (yb + 1) * G.csy - py);
+            lb -= G.slack;
+            if (lb > 0 && dd[cnt - 1] < __dmul_rn(lb, lb)) break;
         }
     }
     // angular order of the want nearest around m
-    double rx[kSaoMaxK], ry[kSaoMaxK];
+    double rxs[kSaoMaxK], rys[kSaoMaxK];
     for (int c = 0; c < want; ++c) {
         const float2 p = sp.at(list, ee[c]);
-        const double x = __dsub_rn((double)p.x, mx), y = __dsub_rn((double)p.y, my);
+        const double x = __dsub_rn((double)p.x, px), y = __dsub_rn((double)p.y, py);
         int pos = c;
-        while (pos > 0 && ray_less(x, y, ee[c], rx[pos - 1], ry[pos - 1], labels[pos - 1])) {
-            rx[pos] = rx[pos - 1];
-            ry[pos] = ry[pos - 1];
+        while (pos > 0 && ray_less(x, y, ee[c], rxs[pos - 1], rys[pos - 1], labels[pos - 1])) {
+            rxs[pos] = rxs[pos - 1];
+            rys[pos] = rys[pos - 1];
             labels[pos] = labels[pos - 1];
             --pos;
         }
-        rx[pos] = x;
-        ry[pos] = y;
+        rxs[pos] = x;
+        rys[pos] = y;
         labels[pos] = ee[c];
     }
     return want;
@@ -202,26 +289,40 @@ __device__ int cyclic_edit_distance(const int32_t* a, int na, const int32_t* b, 
     return best;
 }
 
-template <int T>
 __global__ void __launch_bounds__(kSaoThreads) k_sao_pairs(const DevPair* __restrict__ pairs,
                                                            const unsigned long long* __restrict__ offsets,
                                                            const uint32_t* __restrict__ matches,
                                                            const float* __restrict__ kp,
                                                            const int64_t* __restrict__ kp_off, int k, float max_score,
-                                                           int32_t* __restrict__ best_out, float* __restrict__ score) {
-    __shared__ float tx[kSaoTile], ty[kSaoTile];
+                                                           int32_t* __restrict__ best_out, float* __restrict__ score,
+                                                           float2* __restrict__ gpts, int32_t* __restrict__ gids,
+                                                           int32_t* __restrict__ gcells, int64_t rows) {
+    __shared__ Grid grid[2];
+    __shared__ double red[4 * (kSaoThreads / 32)];
     const DevPair P = pairs[blockIdx.x];
     const unsigned long long o0 = offsets[blockIdx.x];
     const int n = (int)(offsets[blockIdx.x + 1] - o0);
+    if (n == 0) return;
     const uint32_t* list = matches + o0;
-    const Space sp{kp + 2 * kp_off[P.i], 16}, sq{kp + 2 * kp_off[P.j], 0};
+    const Space sp[2] = {{kp + 2 * kp_off[P.i], 16}, {kp + 2 * kp_off[P.j], 0}};
+    // workspace of this pair: entries [o0, o0 + n) per space, and for the cells
+    // (at most n / 2 + 1 starts and counts) slots [o0 + pair, o0 + pair + n + 1)
+    for (int g = 0; g < 2; ++g) {
+        const int64_t cbase = (int64_t)o0 + blockIdx.x;
+        if (threadIdx.x == 0) {
+            grid[g].pts = gpts + g * rows + o0;
+            grid[g].ids = gids + g * rows + o0;
+            grid[g].start = gcells + g * 2 * (rows + gridDim.x) + cbase;
+        }
+        __syncthreads();
+        build_grid(list, n, sp[g], grid[g], gcells + (g * 2 + 1) * (rows + gridDim.x) + cbase, red);
+    }
     for (int c0 = 0; c0 < n; c0 += kSaoThreads) {
         const int m = c0 + (int)threadIdx.x;
-        const bool active = m < n;
+        if (m >= n) continue;
         int32_t la[kSaoMaxK], lb[kSaoMaxK];
-        const int na = neighbours<T>(list, n, m, active, sp, k, tx, ty, la);
-        const int nb = neighbours<T>(list, n, m, active, sq, k, tx, ty, lb);
-        if (!active) continue;
+        const int na = neighbours(list, n, m, sp[0], grid[0], k, la);
+        const int nb = neighbours(list, n, m, sp[1], grid[1], k, lb);
         const float s = na ? (float)cyclic_edit_distance(la, na, lb, nb) / (float)na : 0.f;
         const int64_t row = P.row_off + (int64_t)(list[m] >> 16);
         if (!(s <= max_score)) best_out[row] = -1;
@@ -229,16 +330,23 @@ __global__ void __launch_bounds__(kSaoThreads) k_sao_pairs(const DevPair* __rest
     }
 }
 
+// Workspace: compaction (counts, offsets, match lists), then per space the
+// grid's sorted keypoints and entries [rows] and its cell starts and counts
+// [rows + pairs] each.
 struct SaoWork {
-    uint64_t counts, offsets, matches, total;
+    uint64_t counts, offsets, matches, pts, ids, cells, total;
 };
 
 SaoWork sao_layout(int64_t n_pairs, int64_t rows) {
     SaoWork w{};
+    const uint64_t r = (uint64_t)std::max<int64_t>(rows, 1);
     w.counts = 0;
     w.offsets = align_up(4 * (uint64_t)n_pairs);
     w.matches = align_up(w.offsets + 8 * (uint64_t)(n_pairs + 1));
-    w.total = align_up(w.matches + 4 * (uint64_t)std::max<int64_t>(rows, 1));
+    w.pts = align_up(w.matches + 4 * r);
+    w.ids = align_up(w.pts + 2 * 8 * r);
+    w.cells = align_up(w.ids + 2 * 4 * r);
+    w.total = align_up(w.cells + 4 * 4 * (r + (uint64_t)n_pairs));
     return w;
 }
 
@@ -279,12 +387,11 @@ extern "C" cm_status cm_match_plan_sao(cm_match_plan* pl, const int32_t* d_best_
     CM_CUDA(launch_compact(dp, (int)pl->n_pairs, ix->at<DevImage>(ix->fx.imgs), d_best_in,
                            reinterpret_cast<uint32_t*>(base + w.counts), offsets, offsets + pl->n_pairs, matches,
                            (unsigned long long)std::max<int64_t>(pl->rows, 1), s));
-    if (k_nn + 4 <= 12)
-        k_sao_pairs<12><<<(unsigned)pl->n_pairs, kSaoThreads, 0, s>>>(dp, offsets, matches, d_kp, d_kp_off, k_nn,
-                                                                       max_score, d_best_out, d_score);
-    else
-        k_sao_pairs<20><<<(unsigned)pl->n_pairs, kSaoThreads, 0, s>>>(dp, offsets, matches, d_kp, d_kp_off, k_nn,
-                                                                       max_score, d_best_out, d_score);
+    const int64_t r = std::max<int64_t>(pl->rows, 1);
+    k_sao_pairs<<<(unsigned)pl->n_pairs, kSaoThreads, 0, s>>>(
+        dp, offsets, matches, d_kp, d_kp_off, k_nn, max_score, d_best_out, d_score,
+        reinterpret_cast<float2*>(base + w.pts), reinterpret_cast<int32_t*>(base + w.ids),
+        reinterpret_cast<int32_t*>(base + w.cells), r);
     CM_CUDA(cudaGetLastError());
     return CM_OK;
 }
