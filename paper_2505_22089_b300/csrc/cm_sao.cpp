@@ -23,10 +23,11 @@
 #include <vector>
 
 #include "cm_host.h"
+#include "cm_sao_common.cuh"
 
 namespace {
 
-constexpr int kMaxSaoK = 32;
+constexpr int kMaxSaoK = cm::sao::kMaxK;
 
 struct Nb {
     double d2;
@@ -110,8 +111,7 @@ public:
                     for (int32_t t = start_[c]; t < start_[c + 1]; ++t) {
                         const int32_t id = sid_[t];
                         if (id == m) continue;
-                        const double dx = sx_[t] - px, dy = sy_[t] - py;
-                        const Nb cand{dx * dx + dy * dy, id};
+                        const Nb cand{cm::sao::d2(px, py, sx_[t], sy_[t]), id};
                         if (cnt == want && !(cand < out[cnt - 1])) continue;
                         int pos = cnt < want ? cnt++ : cnt - 1;
                         while (pos > 0 && cand < out[pos - 1]) {
@@ -163,59 +163,7 @@ struct Ray {
     int32_t id;
 };
 
-// true when a comes before b in angular order from the +x axis, in [0, 2*pi)
-bool ray_less(const Ray& a, const Ray& b) {
-    const int ha = (a.dy < 0 || (a.dy == 0 && a.dx < 0)) ? 1 : 0;
-    const int hb = (b.dy < 0 || (b.dy == 0 && b.dx < 0)) ? 1 : 0;
-    if (ha != hb) return ha < hb;
-    const bool za = a.dy == 0 && a.dx >= 0, zb = b.dy == 0 && b.dx >= 0;   // angle exactly 0 (or a zero vector)
-    if (za || zb) return za && zb ? a.id < b.id : za;
-    const double cr = a.dx * b.dy - a.dy * b.dx;
-    if (cr != 0) return cr > 0;
-    return a.id < b.id;
-}
-
-// Unit-cost edit distance of a and b, or any value above `cap` once every
-// entry of a DP row exceeds it (the distance can only grow from there).
-int levenshtein(const int32_t* a, int na, const int32_t* b, int nb, int cap, int* row) {
-    for (int j = 0; j <= nb; ++j) row[j] = j;
-    for (int i = 1; i <= na; ++i) {
-        int diag = row[0];
-        row[0] = i;
-        int lo = i;
-        for (int j = 1; j <= nb; ++j) {
-            const int up = row[j];
-            row[j] = std::min({up + 1, row[j - 1] + 1, diag + (a[i - 1] == b[j - 1] ? 0 : 1)});
-            diag = up;
-            lo = std::min(lo, row[j]);
-        }
-        if (lo > cap) return lo;
-    }
-    return row[nb];
-}
-
-int cyclic_edit_distance(const int32_t* a, int na, const int32_t* b, int nb) {
-    int row[kMaxSaoK + 1];
-    if (na == 0 || nb == 0) return std::max(na, nb);
-    int32_t rot[kMaxSaoK];
-    // first the rotation of a that starts with b's first label (the usual
-    // optimum, exact 0 for an unchanged order), then the others bounded by it
-    int r0 = 0;
-    for (int t = 0; t < na; ++t)
-        if (a[t] == b[0]) r0 = t;
-    if (na == nb) {   // the same cyclic order: distance 0 without a table
-        int t = 0;
-        while (t < na && a[(r0 + t) % na] == b[t]) ++t;
-        if (t == na) return 0;
-    }
-    int best = na + nb;
-    for (int step = 0; step < na && best > 0; ++step) {
-        const int r = (r0 + step) % na;
-        for (int t = 0; t < na; ++t) rot[t] = a[(r + t) % na];
-        best = std::min(best, levenshtein(rot, na, b, nb, best - 1, row));
-    }
-    return best;
-}
+bool ray_less(const Ray& a, const Ray& b) { return cm::sao::ray_less(a.dx, a.dy, a.id, b.dx, b.dy, b.id); }
 
 // Neighbour labels of centre m in angular order.
 int ordered(const Grid& g, const std::vector<double>& x, const std::vector<double>& y, int64_t m, int k,
@@ -223,7 +171,7 @@ int ordered(const Grid& g, const std::vector<double>& x, const std::vector<doubl
     Nb nb[kMaxSaoK];
     const int cnt = g.query(m, x[m], y[m], k, nb);
     Ray r[kMaxSaoK];
-    for (int t = 0; t < cnt; ++t) r[t] = {x[nb[t].id] - x[m], y[nb[t].id] - y[m], nb[t].id};
+    for (int t = 0; t < cnt; ++t) r[t] = {cm::sao::sub(x[nb[t].id], x[m]), cm::sao::sub(y[nb[t].id], y[m]), nb[t].id};
     std::sort(r, r + cnt, ray_less);
     for (int t = 0; t < cnt; ++t) labels[t] = r[t].id;
     return cnt;
@@ -251,7 +199,7 @@ extern "C" cm_status cm_sao_filter(const float* kp_i, const float* kp_j, int64_t
         int32_t a[kMaxSaoK], b[kMaxSaoK];
         const int na = ordered(gp, px, py, (int64_t)m, k_nn, a);
         const int nb = ordered(gq, qx, qy, (int64_t)m, k_nn, b);
-        const float s = na ? (float)cyclic_edit_distance(a, na, b, nb) / (float)na : 0.f;
+        const float s = na ? (float)cm::sao::cyclic_edit_distance(a, na, b, nb) / (float)na : 0.f;
         const bool k = s <= max_score;
         if (score) score[m] = s;
         if (keep) keep[m] = k;

@@ -24,6 +24,7 @@
 #include <cstdint>
 
 #include "cm_host.h"
+#include "cm_sao_common.cuh"
 
 namespace cm {
 
@@ -43,24 +44,6 @@ struct Space {
         return make_float2(kp[2 * i], kp[2 * i + 1]);
     }
 };
-
-__device__ __forceinline__ double d2_exact(double ax, double ay, double bx, double by) {
-    const double dx = __dsub_rn(bx, ax), dy = __dsub_rn(by, ay);
-    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-}
-
-// true when ray a comes before ray b (angle from the +x axis in [0, 2 pi), a
-// zero vector at angle 0, ties by label)
-__device__ __forceinline__ bool ray_less(double ax, double ay, int al, double bx, double by, int bl) {
-    const int ha = (ay < 0 || (ay == 0 && ax < 0)) ? 1 : 0;
-    const int hb = (by < 0 || (by == 0 && bx < 0)) ? 1 : 0;
-    if (ha != hb) return ha < hb;
-    const bool za = ay == 0 && ax >= 0, zb = by == 0 && bx >= 0;
-    if (za || zb) return za && zb ? al < bl : za;
-    const double cr = __dsub_rn(__dmul_rn(ax, by), __dmul_rn(ay, bx));
-    if (cr != 0) return cr > 0;
-    return al < bl;
-}
 
 // A grid over one space of a pair's match list, in the pair's workspace.
 struct Grid {
@@ -197,14 +180,14 @@ __device__ int neighbours(const uint32_t* list, int n, int m, Space sp, const Gr
                 if (cnt == want) {   // a cell that cannot hold a point closer than the k-th
                     const double gx0 = G.x0 + xx * G.csx - G.slack - px, gx1 = px - (G.x0 + (xx + 1) * G.csx + G.slack);
                     const double rx = gx0 > 0 ? gx0 : (gx1 > 0 ? gx1 : 0.0);
-                    if (__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)) > dd[cnt - 1]) continue;
+                    if (sao::add(sao::mul(rx, rx), sao::mul(ry, ry)) > dd[cnt - 1]) continue;
                 }
                 const int c = yy * G.gx + xx;
                 for (int t = G.start[c]; t < G.start[c + 1]; ++t) {
                     const int e = G.ids[t];
                     if (e == m) continue;
                     const float2 p = G.pts[t];
-                    const double d = d2_exact(px, py, p.x, p.y);
+                    const double d = sao::d2(px, py, p.x, p.y);
                     if (cnt == want && !(d < dd[cnt - 1] || (d == dd[cnt - 1] && e < ee[cnt - 1]))) continue;
                     int pos = cnt < want ? cnt++ : cnt - 1;
                     while (pos > 0 && (d < dd[pos - 1] || (d == dd[pos - 1] && e < ee[pos - 1]))) {
@@ -225,16 +208,16 @@ __device__ int neighbours(const uint32_t* list, int n, int m, Space sp, const Gr
             if (ya > 0) lb = fmin(lb, py - (G.y0 + ya * G.csy));
             if (yb < G.gy - 1) lb = fmin(lb, G.y0 + (yb + 1) * G.csy - py);
             lb -= G.slack;
-            if (lb > 0 && dd[cnt - 1] < __dmul_rn(lb, lb)) break;
+            if (lb > 0 && dd[cnt - 1] < sao::mul(lb, lb)) break;
         }
     }
     // angular order of the want nearest around m
     double rxs[kSaoMaxK], rys[kSaoMaxK];
     for (int c = 0; c < want; ++c) {
         const float2 p = sp.at(list, ee[c]);
-        const double x = __dsub_rn((double)p.x, px), y = __dsub_rn((double)p.y, py);
+        const double x = sao::sub((double)p.x, px), y = sao::sub((double)p.y, py);
         int pos = c;
-        while (pos > 0 && ray_less(x, y, ee[c], rxs[pos - 1], rys[pos - 1], labels[pos - 1])) {
+        while (pos > 0 && sao::ray_less(x, y, ee[c], rxs[pos - 1], rys[pos - 1], labels[pos - 1])) {
             rxs[pos] = rxs[pos - 1];
             rys[pos] = rys[pos - 1];
             labels[pos] = labels[pos - 1];
@@ -245,48 +228,6 @@ __device__ int neighbours(const uint32_t* list, int n, int m, Space sp, const Gr
         labels[pos] = ee[c];
     }
     return want;
-}
-
-// Unit-cost edit distance, or a value above cap once a whole DP row exceeds it.
-__device__ int levenshtein(const int32_t* a, int na, const int32_t* b, int nb, int cap) {
-    int row[kSaoMaxK + 1];
-    for (int j = 0; j <= nb; ++j) row[j] = j;
-    for (int i = 1; i <= na; ++i) {
-        int diag = row[0];
-        row[0] = i;
-        int lo = i;
-        for (int j = 1; j <= nb; ++j) {
-            const int up = row[j];
-            const int v = min(min(up + 1, row[j - 1] + 1), diag + (a[i - 1] == b[j - 1] ? 0 : 1));
-            row[j] = v;
-            diag = up;
-            lo = min(lo, v);
-        }
-        if (lo > cap) return lo;
-    }
-    return row[nb];
-}
-
-// Cyclic edit distance: rotations of a only (an alignment of two rotations can
-// be re-cut where b starts), the rotation starting with b's first label first.
-__device__ int cyclic_edit_distance(const int32_t* a, int na, const int32_t* b, int nb) {
-    if (na == 0 || nb == 0) return max(na, nb);
-    int r0 = 0;
-    for (int t = 0; t < na; ++t)
-        if (a[t] == b[0]) r0 = t;
-    if (na == nb) {
-        int t = 0;
-        while (t < na && a[(r0 + t) % na] == b[t]) ++t;
-        if (t == na) return 0;
-    }
-    int32_t rot[kSaoMaxK];
-    int best = na + nb;
-    for (int step = 0; step < na && best > 0; ++step) {
-        const int r = (r0 + step) % na;
-        for (int t = 0; t < na; ++t) rot[t] = a[(r + t) % na];
-        best = min(best, levenshtein(rot, na, b, nb, best - 1));
-    }
-    return best;
 }
 
 __global__ void __launch_bounds__(kSaoThreads) k_sao_pairs(const DevPair* __restrict__ pairs,
@@ -323,7 +264,7 @@ __global__ void __launch_bounds__(kSaoThreads) k_sao_pairs(const DevPair* __rest
         int32_t la[kSaoMaxK], lb[kSaoMaxK];
         const int na = neighbours(list, n, m, sp[0], grid[0], k, la);
         const int nb = neighbours(list, n, m, sp[1], grid[1], k, lb);
-        const float s = na ? (float)cyclic_edit_distance(la, na, lb, nb) / (float)na : 0.f;
+        const float s = na ? (float)sao::cyclic_edit_distance(la, na, lb, nb) / (float)na : 0.f;
         const int64_t row = P.row_off + (int64_t)(list[m] >> 16);
         if (!(s <= max_score)) best_out[row] = -1;
         if (score) score[row] = s;
