@@ -48,6 +48,7 @@ struct Space {
 // A grid over one space of a pair's match list, in the pair's workspace.
 struct Grid {
     double x0, y0, csx, csy, slack;
+    float fx0, fy0, fcsx, fcsy, fslack;   // the same in FP32, the slack wide enough for FP32 rounding
     int gx, gy;
     int32_t* start;   // [gx * gy + 1] first sorted entry of each cell
     float2* pts;      // [n] keypoints in cell order
@@ -110,6 +111,11 @@ __device__ void build_grid(const uint32_t* list, int n, Space sp, Grid& G, int32
         G.csx = wd > 0 ? wd / gx : 1.0;
         G.csy = hd > 0 ? hd / gy : 1.0;
         G.slack = 1e-9 * (wd + hd + fabs(x0) + fabs(y0) + 1.0);
+        G.fx0 = (float)x0;
+        G.fy0 = (float)y0;
+        G.fcsx = (float)G.csx;
+        G.fcsy = (float)G.csy;
+        G.fslack = (float)(1e-5 * (wd + hd + fabs(x0) + fabs(y0) + 1.0));
     }
     __syncthreads();
     const int nc = G.gx * G.gy;
@@ -157,25 +163,18 @@ __device__ void build_grid(const uint32_t* list, int n, Space sp, Grid& G, int32
     __syncthreads();
 }
 
-// Exact k nearest list entries of entry m by (d^2, entry), then their labels
-// in angular order around m.  Returns the neighbour count.
-__device__ int neighbours(const uint32_t* list, int n, int m, Space sp, const Grid& G, int k, int32_t* labels) {
-    const int want = min(k, n - 1);
-    if (want <= 0) return 0;
-    const float2 me = sp.at(list, m);
-    const double px = me.x, py = me.y;
+// Exact k nearest list entries of entry m by (d^2 in FP64, entry), searched
+// ring by ring; writes them ascending to dd / ee.
+__device__ void knn_exact(int m, double px, double py, const Grid& G, int want, double* dd, int* ee) {
     const int cx = cell_coord(px - G.x0, G.csx, G.gx), cy = cell_coord(py - G.y0, G.csy, G.gy);
-    double dd[kSaoMaxK];
-    int ee[kSaoMaxK];
-    int cnt = 0;   // dd / ee ascending by (d^2, entry)
+    int cnt = 0;
     for (int r = 0;; ++r) {
         const int xa = cx - r, xb = cx + r, ya = cy - r, yb = cy + r;
         for (int yy = max(ya, 0); yy <= min(yb, G.gy - 1); ++yy) {
             const bool edge_row = yy == ya || yy == yb;
             const double gy0 = G.y0 + yy * G.csy - G.slack - py, gy1 = py - (G.y0 + (yy + 1) * G.csy + G.slack);
             const double ry = gy0 > 0 ? gy0 : (gy1 > 0 ? gy1 : 0.0);
-            const int x_lo = max(xa, 0), x_hi = min(xb, G.gx - 1);
-            for (int xx = x_lo; xx <= x_hi; ++xx) {
+            for (int xx = max(xa, 0); xx <= min(xb, G.gx - 1); ++xx) {
                 if (!edge_row && xx != xa && xx != xb) continue;   // the ring only
                 if (cnt == want) {   // a cell that cannot hold a point closer than the k-th
                     const double gx0 = G.x0 + xx * G.csx - G.slack - px, gx1 = px - (G.x0 + (xx + 1) * G.csx + G.slack);
@@ -211,21 +210,140 @@ __device__ int neighbours(const uint32_t* list, int n, int m, Space sp, const Gr
             if (lb > 0 && dd[cnt - 1] < sao::mul(lb, lb)) break;
         }
     }
-    // angular order of the want nearest around m
-    double rxs[kSaoMaxK], rys[kSaoMaxK];
+}
+
+// The same set from an FP32 search of T = want + 4 candidates, re-scored in
+// FP64 and sorted by (d^2, entry).  A point left out either has an FP32
+// distance (relative error below 1e-6) at least the T-th candidate's d_T, or
+// lies in a cell whose FP32 lower bound, widened by a slack for FP32
+// rounding, exceeds d_T (1 + 4e-6).  So when the want-th exact distance is
+// below d_T / (1 + 1e-6), no point left out can rank among the first want and
+// the set is exact.  Returns false when that test fails (knn_exact decides).
+__device__ bool knn_fast(const uint32_t* list, Space sp, int m, int n, float pxf, float pyf, const Grid& G, int want,
+                         double* dd, int* ee) {
+    const int T = min(want + 4, n - 1);
+    const float grow = 1.f + 4e-6f;
+    float df[kSaoMaxK + 4];
+    int ef[kSaoMaxK + 4];
+    int cnt = 0;
+    const int cx = cell_coord((double)pxf - G.x0, G.csx, G.gx), cy = cell_coord((double)pyf - G.y0, G.csy, G.gy);
+    for (int r = 0;; ++r) {
+        const int xa = cx - r, xb = cx + r, ya = cy - r, yb = cy + r;
+        for (int yy = max(ya, 0); yy <= min(yb, G.gy - 1); ++yy) {
+            const bool edge_row = yy == ya || yy == yb;
+            const float gy0 = G.fy0 + yy * G.fcsy - G.fslack - pyf, gy1 = pyf - (G.fy0 + (yy + 1) * G.fcsy + G.fslack);
+            const float ry = gy0 > 0 ? gy0 : (gy1 > 0 ? gy1 : 0.f);
+            for (int xx = max(xa, 0); xx <= min(xb, G.gx - 1); ++xx) {
+                if (!edge_row && xx != xa && xx != xb) continue;
+                if (cnt == T) {
+                    const float gx0 = G.fx0 + xx * G.fcsx - G.fslack - pxf, gx1 = pxf - (G.fx0 + (xx + 1) * G.fcsx + G.fslack);
+                    const float rx = gx0 > 0 ? gx0 : (gx1 > 0 ? gx1 : 0.f);
+                    if (rx * rx + ry * ry > df[T - 1] * grow) continue;
+                }
+                const int c = yy * G.gx + xx;
+                for (int t = G.start[c]; t < G.start[c + 1]; ++t) {
+                    const int e = G.ids[t];
+                    if (e == m) continue;
+                    const float2 p = G.pts[t];
+                    const float dx = p.x - pxf, dy = p.y - pyf;
+                    const float d = dx * dx + dy * dy;
+                    if (cnt == T && !(d < df[T - 1] || (d == df[T - 1] && e < ef[T - 1]))) continue;
+                    int pos = cnt < T ? cnt++ : T - 1;
+                    while (pos > 0 && (d < df[pos - 1] || (d == df[pos - 1] && e < ef[pos - 1]))) {
+                        df[pos] = df[pos - 1];
+                        ef[pos] = ef[pos - 1];
+                        --pos;
+                    }
+                    df[pos] = d;
+                    ef[pos] = e;
+                }
+            }
+        }
+        if (xa <= 0 && ya <= 0 && xb >= G.gx - 1 && yb >= G.gy - 1) break;
+        if (cnt == T) {
+            float lb = __uint_as_float(0x7F800000u);
+            if (xa > 0) lb = fminf(lb, pxf - (G.fx0 + xa * G.fcsx));
+            if (xb < G.gx - 1) lb = fminf(lb, G.fx0 + (xb + 1) * G.fcsx - pxf);
+            if (ya > 0) lb = fminf(lb, pyf - (G.fy0 + ya * G.fcsy));
+            if (yb < G.gy - 1) lb = fminf(lb, G.fy0 + (yb + 1) * G.fcsy - pyf);
+            lb -= G.fslack;
+            if (lb > 0 && df[T - 1] * grow < lb * lb) break;
+        }
+    }
+    // exact re-score of the candidates, keeping the first want by (d^2, entry)
+    const double px = pxf, py = pyf;
+    int kept = 0;
+    for (int c = 0; c < cnt; ++c) {
+        const int e = ef[c];
+        const float2 p = sp.at(list, e);
+        const double d = sao::d2(px, py, p.x, p.y);
+        if (kept == want && !(d < dd[want - 1] || (d == dd[want - 1] && e < ee[want - 1]))) continue;
+        int pos = kept < want ? kept++ : want - 1;
+        while (pos > 0 && (d < dd[pos - 1] || (d == dd[pos - 1] && e < ee[pos - 1]))) {
+            dd[pos] = dd[pos - 1];
+            ee[pos] = ee[pos - 1];
+            --pos;
+        }
+        dd[pos] = d;
+        ee[pos] = e;
+    }
+    if (cnt < n - 1) {
+        const double bound = (double)df[T - 1] / (1.0 + 1e-6);
+        if (!(dd[want - 1] < bound)) return false;
+    }
+    return true;
+}
+
+// Exact k nearest list entries of entry m, then their labels in angular
+// order around m.  Returns the neighbour count.
+__device__ int neighbours(const uint32_t* list, int n, int m, Space sp, const Grid& G, int k, int32_t* labels) {
+    const int want = min(k, n - 1);
+    if (want <= 0) return 0;
+    const float2 me = sp.at(list, m);
+    double dd[kSaoMaxK];
+    int ee[kSaoMaxK];
+    if (!knn_fast(list, sp, m, n, me.x, me.y, G, want, dd, ee)) knn_exact(m, me.x, me.y, G, want, dd, ee);
+    // angular order of the want nearest around m.  Rays are compared in FP32
+    // where that is certain: the half-plane tests use only signs and zeros of
+    // the coordinate differences, which FP32 subtraction keeps, and a cross
+    // product whose FP32 value exceeds 1e-6 of its terms' magnitudes has the
+    // sign of the exact one; otherwise the host's FP64 comparison decides.
+    const double px = me.x, py = me.y;
+    float xs[kSaoMaxK], ys[kSaoMaxK];
     for (int c = 0; c < want; ++c) {
         const float2 p = sp.at(list, ee[c]);
-        const double x = sao::sub((double)p.x, px), y = sao::sub((double)p.y, py);
+        const float x = p.x - me.x, y = p.y - me.y;
+        const int e = ee[c];
         int pos = c;
-        while (pos > 0 && sao::ray_less(x, y, ee[c], rxs[pos - 1], rys[pos - 1], labels[pos - 1])) {
-            rxs[pos] = rxs[pos - 1];
-            rys[pos] = rys[pos - 1];
+        while (pos > 0) {
+            const float bx = xs[pos - 1], by = ys[pos - 1];
+            const int bl = labels[pos - 1];
+            bool less;
+            const int ha = (y < 0 || (y == 0 && x < 0)) ? 1 : 0, hb = (by < 0 || (by == 0 && bx < 0)) ? 1 : 0;
+            const bool za = y == 0 && x >= 0, zb = by == 0 && bx >= 0;
+            if (ha != hb) {
+                less = ha < hb;
+            } else if (za || zb) {
+                less = za && zb ? e < bl : za;
+            } else {
+                const float t1 = x * by, t2 = y * bx, cr = t1 - t2;
+                if (fabsf(cr) > 1e-6f * (fabsf(t1) + fabsf(t2))) {
+                    less = cr > 0;
+                } else {   // too close to call in FP32: the host's FP64 comparison
+                    const float2 q = sp.at(list, bl);
+                    less = sao::ray_less(sao::sub((double)p.x, px), sao::sub((double)p.y, py), e,
+                                         sao::sub((double)q.x, px), sao::sub((double)q.y, py), bl);
+                }
+            }
+            if (!less) break;
+            xs[pos] = xs[pos - 1];
+            ys[pos] = ys[pos - 1];
             labels[pos] = labels[pos - 1];
             --pos;
         }
-        rxs[pos] = x;
-        rys[pos] = y;
-        labels[pos] = ee[c];
+        xs[pos] = x;
+        ys[pos] = y;
+        labels[pos] = e;
     }
     return want;
 }
