@@ -8,15 +8,16 @@
 //   - builds, for the query image and for the database image, a uniform grid
 //     over the pair's matched keypoints (about two per cell, shaped like the
 //     bounding box; a counting sort into workspace memory);
-//   - walks its list in chunks of 256 matches, one thread per match: the
-//     exact k nearest neighbours by (d^2 in FP64, entry index), searched ring
-//     by ring with cells skipped when their distance bound exceeds the k-th
-//     and the search stopped once no unvisited cell can hold a closer point
-//     (the bounds carry a slack for coordinates rounded into a neighbouring
-//     cell); then the angular order by half-plane and the sign of an exact
-//     cross product, the cyclic edit distance of the two label sequences, the
-//     score and the decision, with the host's roundings (no fused
-//     multiply-adds in the FP64 arithmetic).
+//   - walks its list in chunks of 256 matches, one thread per match: a ring
+//     by ring grid search for the k + 4 nearest in FP32 (cells skipped, and
+//     the search stopped, by FP32 bounds widened for FP32 rounding), those
+//     re-scored in FP64 and ordered by (d^2, entry); when the k-th exact
+//     distance does not clear the FP32 screen by its error margin, the same
+//     search runs in FP64 alone.  Then the angular order: FP32 comparisons
+//     where their outcome is certain, the host's FP64 comparison otherwise;
+//     the cyclic edit distance, the score and the decision.  Every decision
+//     is the host's: FP64 arithmetic without fused multiply-adds
+//     (cm_sao_common.cuh) wherever FP32 cannot be certain.
 // A rejected match's decision becomes -1 in the output, so the usual
 // compaction afterwards hands only the kept matches to verification.
 #include <cuda_runtime.h>
