@@ -630,7 +630,11 @@ extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, in
     cm_match_plan* pl = new (std::nothrow) cm_match_plan();
     if (!pl) return fail(CM_ERR_NOMEM, "plan: host allocation");
     const uint64_t bytes = plan_bytes(&ix->p, n_pairs, rows, max_ni);
-    if (!ix->alloc.alloc(bytes, &pl->table_at)) {
+    if (ix->plan_reserve_bytes >= bytes && !ix->plan_reserve_busy) {   // the pipeline's reserved block
+        pl->table_at = ix->plan_reserve_at;
+        pl->reserved = true;
+        ix->plan_reserve_busy = true;
+    } else if (!ix->alloc.alloc(bytes, &pl->table_at)) {
         delete pl;
         return fail(CM_ERR_BUDGET, "plan: arena full (%llu bytes for the pair table)", (unsigned long long)bytes);
     }
@@ -734,7 +738,10 @@ extern "C" cm_status cm_match_plan_mutual(cm_match_plan* pl, const int32_t* d_be
 extern "C" void cm_match_plan_destroy(cm_match_plan* pl) {
     if (!pl) return;
     if (pl->ix) {
-        pl->ix->alloc.release(pl->table_at);
+        if (pl->reserved)
+            pl->ix->plan_reserve_busy = false;
+        else
+            pl->ix->alloc.release(pl->table_at);
         pl->ix->plans.erase(pl);
         ++pl->ix->generation;
     }

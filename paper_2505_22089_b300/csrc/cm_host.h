@@ -211,6 +211,9 @@ struct cm_index {
     std::vector<uint64_t> slot_at;     // arena offset of each image's slot (valid if resident)
     std::vector<char> resident;
     std::vector<char> pending;         // slot placed and descriptors on their way, not yet published
+    uint64_t plan_reserve_at = 0;      // arena block reserved by cm_run_schedule for its rows' plans
+    uint64_t plan_reserve_bytes = 0;   // 0: none
+    bool plan_reserve_busy = false;    // a live plan occupies it
     bool mean_set = false;
     bool sums_on_host = false;         // the mean came from cm_index_set_mean
     uint64_t host_sums[kDim] = {};
@@ -309,6 +312,7 @@ struct cm_match_plan {
     int64_t rows = 0;
     int32_t n_items = 0;
     int32_t max_ni = 0;      // largest query image of the plan
+    bool reserved = false;   // placed in the index's reserved plan block
 };
 
 

@@ -308,14 +308,16 @@ WorkLayout work_layout(int64_t max_rows, int64_t max_pairs, bool sao) {
 bool sao_on(const cm_pipeline_opts* o) { return o && o->sao_k > 0; }
 
 cm_status row_sizes(const cm_index* ix, const cm_schedule* s, const cm_pair* pairs, int64_t n_pairs, int64_t* max_rows,
-                    int64_t* max_pairs) {
+                    int64_t* max_pairs, uint64_t* max_plan = nullptr) {
     const int32_t R = cm_schedule_num_rows(s);
     *max_rows = *max_pairs = 0;
+    if (max_plan) *max_plan = 0;
     for (int32_t r = 0; r < R; ++r) {
         cm_schedule_row row{};
         cm_status st = cm_schedule_get_row(s, r, &row);
         if (st != CM_OK) return st;
         int64_t q = 0;
+        int32_t max_ni = 0;
         for (int64_t k = 0; k < row.n_pairs; ++k) {
             const int64_t id = row.pairs[k];
             if (id < 0 || id >= n_pairs) return fail(CM_ERR_INVALID, "pipeline: schedule names pair %lld of %lld",
@@ -323,9 +325,11 @@ cm_status row_sizes(const cm_index* ix, const cm_schedule* s, const cm_pair* pai
             const int i = pairs[id].i;
             if (i < 0 || i >= ix->n_images) return fail(CM_ERR_INVALID, "pipeline: pair %lld has a bad image id", (long long)id);
             q += ix->n_desc[i];
+            max_ni = std::max(max_ni, ix->n_desc[i]);
         }
         *max_rows = std::max(*max_rows, q);
         *max_pairs = std::max<int64_t>(*max_pairs, row.n_pairs);
+        if (max_plan && row.n_pairs) *max_plan = std::max(*max_plan, plan_bytes(&ix->p, row.n_pairs, q, max_ni));
     }
     return CM_OK;
 }
@@ -517,7 +521,8 @@ extern "C" cm_status cm_run_schedule_ex(cm_index* ix, const cm_schedule* s, cons
         return fail(CM_ERR_INVALID, "cm_run_schedule: bad SAO options (1 <= sao_k <= 16, keypoints on the device)");
     if (!ix->mean_set) return fail(CM_ERR_STATE, "cm_run_schedule: centring mean not set");
     int64_t max_rows = 0, max_pairs = 0;
-    cm_status st = row_sizes(ix, s, pairs, n_pairs, &max_rows, &max_pairs);
+    uint64_t max_plan = 0;
+    cm_status st = row_sizes(ix, s, pairs, n_pairs, &max_rows, &max_pairs, &max_plan);
     if (st != CM_OK) return st;
     const WorkLayout wl = work_layout(max_rows, max_pairs, sao_on(opts));
     if (work_bytes < wl.total)
@@ -560,6 +565,11 @@ extern "C" cm_status cm_run_schedule_ex(cm_index* ix, const cm_schedule* s, cons
                 if (cm_schedule_get_row(s, r, &row) == CM_OK) index_cancel_prefetch(ix, row.n_load, row.load);
                 prefetched[r] = 0;
             }
+        if (ix->plan_reserve_bytes) {   // the rows' plans are gone: give the reserved block back
+            ix->alloc.release(ix->plan_reserve_at);
+            ix->plan_reserve_bytes = 0;
+            ix->plan_reserve_busy = false;
+        }
         for (auto e : ev_start) if (e) cudaEventDestroy(e);
         for (auto e : ev_done) if (e) cudaEventDestroy(e);
         for (auto e : ev_copied) if (e) cudaEventDestroy(e);
@@ -647,6 +657,13 @@ extern "C" cm_status cm_run_schedule_ex(cm_index* ix, const cm_schedule* s, cons
         }
         return CM_OK;
     };
+    // One block of the arena serves every row's plan in turn, placed before any
+    // image of the run: plans then never fragment the space the images use.
+    // No room: each plan is placed on its own as usual.
+    if (max_plan && !ix->plan_reserve_bytes && ix->alloc.alloc(max_plan, &ix->plan_reserve_at)) {
+        ix->plan_reserve_bytes = max_plan;
+        ix->plan_reserve_busy = false;
+    }
     for (int w = 0; w < n_workers; ++w) threads.emplace_back([&P] { P.worker(); });
     // hashing: (bias +) projection + buckets (+ the rerank row copies); matching: scan (+ tensor-core rerank)
     const int hash_kernels = (ix->p.projection == CM_PROJ_TC ? 3 : 2) + (tc_rerank(&ix->p) ? 1 : 0);
