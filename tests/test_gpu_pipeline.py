@@ -249,13 +249,18 @@ def test_autotune_chooses_K_under_an_agreement_floor():
     assert r2["agreement"] == 1.0
 
 
-@pytest.mark.parametrize("strategy", ["per_pair", "pair_blocks", "load_free_list", "graph_partition"])
-def test_other_schedule_strategies_give_the_same_matches(strategy):
+@pytest.mark.parametrize("strategy,rerank", [("per_pair", "fp32"), ("pair_blocks", "fp32"), ("load_free_list", "fp32"),
+                                             ("graph_partition", "fp32"), ("graph_partition", "fp8"),
+                                             ("pair_blocks", "bf16")])
+def test_other_schedule_strategies_give_the_same_matches(strategy, rerank):
     """Caller-built rows (cm_schedule_from_rows) through the pipeline: rows
     that reload an image the previous row frees, rows without loads, many
-    small rows; the match lists equal direct matching."""
+    small rows, and the tensor-core forms whose plans carry large hand-overs,
+    all in an arena of exactly cm_schedule_arena_bytes; the match lists equal
+    direct matching."""
     from paper_2505_22089_b300 import strategies as st
-    wl, desc, p, _, host, _ = _grid_case()
+    wl, desc, _, _, host, _ = _grid_case()
+    p = cm.Params.make(rerank=rerank)
     ib = np.array([cm.image_bytes(p, int(n)) for n in wl.n_desc], dtype=np.int64)
     budget = int(ib.sum() // 3)
     order = st.connection_order(wl.pairs, wl.n_images, cm.gps_order)
