@@ -8,11 +8,12 @@
 // tile is staged once as the A operand; the database image is walked in
 // chunks of up to 256 rows, each staged as the B operand and multiplied on
 // the tensor cores (128 x N x 128, BF16, FP32 accumulate: every partial sum
-// of x.y is an integer below 2^24, so exact).  The 4 warps read their lanes
-// back and keep, per query, the smallest (d^2, j) and the second smallest
-// d^2, with d^2 = |x|^2 + |y|^2 - 2 x.y exact as an FP32 integer; the last
-// chunk is followed by the exact integer ratio test.  Two CTAs per SM overlap one's
-// staging with the other's MMA and epilogue.
+// of x.y is an integer below 2^24, so exact).  The epilogue keeps, per query,
+// the smallest (d^2, j) and the second smallest d^2, with
+// d^2 = |x|^2 + |y|^2 - 2 x.y exact as an FP32 integer; the last chunk is
+// followed by the exact integer ratio test.  Producers, the MMA issuer and
+// the epilogue are separate warps with double-buffered operands and
+// accumulators (see the kernel).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -26,7 +27,6 @@ namespace cm {
 
 namespace {
 
-constexpr int kNnThreads = 128;
 constexpr int kNnRows = 128;      // queries per work item (M)
 constexpr int kNnChunk = 256;     // database rows per MMA (N)
 constexpr int kNnPolls = 1 << 24;
@@ -38,104 +38,222 @@ struct NnPair {
     int32_t pad;
 };
 
-__global__ void __launch_bounds__(kNnThreads, 2)
+// Warp roles of k_nn_exhaustive (288 threads, one CTA per SM):
+//   warps 0-3  producers: stage each work item's 128 query rows (A) and each
+//              database chunk of 256 rows into one of two B buffers, with
+//              the chunk's database norms;
+//   warp 4     MMA issuer: one thread, each chunk into one of two TMEM
+//              accumulators (2 x 256 columns), commits that free the B
+//              buffer, fill the accumulator and, after an item, free A;
+//   warps 5-8  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one query
+//              each), keeps q1 (d^2, j) and q2's d^2, and writes the outputs.
+// Staging, MMA and epilogue of neighbouring chunks overlap.  The norms go to
+// a ring of four buffers that the epilogue reads after a barrier of its own
+// (the producers cannot get four chunks ahead of the epilogue, so a buffer is
+// never refilled while it is read).  Every wait is bounded and also gives up
+// once another role has aborted.
+constexpr int kNnProd = 128;
+constexpr int kNnMmaWarp = 4;
+constexpr int kNnPipeThreads = 288;
+constexpr uint32_t kNnA = kNnRows * 256, kNnB = kNnChunk * 256;
+
+__device__ __forceinline__ bool nn_wait(uint64_t* mbar, uint32_t parity, volatile int* abort_flag) {
+    for (int it = 0; it < kNnPolls; it += 64) {
+        if (tc::mbar_wait(mbar, parity, 64)) return true;
+        if (*abort_flag) return false;
+    }
+    return false;
+}
+
+// One work item: a tile of up to 128 queries of one pair.
+struct NnItem {
+    int64_t oi, oj, row0;
+    int ni, nj, q0;
+};
+
+__device__ __forceinline__ NnItem nn_item(const NnPair* pairs, int n_pairs, const int64_t* img_off, int item) {
+    int lo = 0, hi = n_pairs;   // last pair with item0 <= item
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pairs[mid].item0 <= item) lo = mid; else hi = mid;
+    }
+    const NnPair P = pairs[lo];
+    NnItem t;
+    t.oi = img_off[P.i];
+    t.oj = img_off[P.j];
+    t.ni = (int)(img_off[P.i + 1] - t.oi);
+    t.nj = (int)(img_off[P.j + 1] - t.oj);
+    t.q0 = (item - P.item0) * kNnRows;
+    t.row0 = P.row_off + t.q0;
+    return t;
+}
+
+__device__ __forceinline__ uint32_t row_norm(const uint8_t* row) {
+    uint32_t nn = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(row) + c);
+        nn = __dp4a(v.x, v.x, nn);
+        nn = __dp4a(v.y, v.y, nn);
+        nn = __dp4a(v.z, v.z, nn);
+        nn = __dp4a(v.w, v.w, nn);
+    }
+    return nn;
+}
+
+__global__ void __launch_bounds__(kNnPipeThreads, 1)
 k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ img_off, const NnPair* __restrict__ pairs,
                 int n_pairs, int n_items, int ratio_num, int ratio_den, int32_t* __restrict__ best_j,
                 uint32_t* __restrict__ d1sq, uint32_t* __restrict__ d2sq, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* At = smem;                                    // 128 x 256 B
-    unsigned char* Bt = At + kNnRows * 256;                      // 256 x 256 B
-    float* nb = reinterpret_cast<float*>(Bt + kNnChunk * 256);   // [256] |y|^2 (+inf past the image)
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(nb + kNnChunk);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    unsigned char* At = smem;                                   // 128 x 256 B
+    unsigned char* Bt = At + kNnA;                              // 2 x 256 x 256 B
+    float* nbr = reinterpret_cast<float*>(Bt + 2 * kNnB);       // [4][256] chunk norms (+inf past the image)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(nbr + 4 * kNnChunk);
+    uint64_t *fullB = bar, *emptyB = bar + 2, *accFull = bar + 4, *accEmpty = bar + 6, *fullA = bar + 8,
+             *emptyA = bar + 9, *nbFull = bar + 10;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float kInf = __uint_as_float(0x7F800000u);
-
-    if (tid == 0) tc::mbar_init(mbar, 1);
-    if (warp == 0) tc::tmem_alloc(tslot, kNnChunk);
+    if (tid == 0) {
+        for (int k = 0; k < 2; ++k) {
+            tc::mbar_init(&fullB[k], kNnProd);
+            tc::mbar_init(&emptyB[k], 1);
+            tc::mbar_init(&accFull[k], 1);
+            tc::mbar_init(&accEmpty[k], 128);
+        }
+        tc::mbar_init(fullA, kNnProd);
+        tc::mbar_init(emptyA, 1);
+        for (int k = 0; k < 4; ++k) tc::mbar_init(&nbFull[k], kNnProd);
+        s_abort = 0;
+    }
+    if (warp == kNnMmaWarp) tc::tmem_alloc(&s_tmem, 2 * kNnChunk);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    const uint32_t tmem = *tslot;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-    uint32_t parity = 0;
-    bool failed = false;
+    const uint32_t tmem = s_tmem;
+    volatile int* abort_flag = &s_abort;
+    auto give_up = [&]() {
+        *abort_flag = 1;
+        atomicExch(err, 1);
+    };
 
-    for (int item = blockIdx.x; item < n_items && !failed; item += gridDim.x) {
-        int lo = 0, hi = n_pairs;   // last pair with item0 <= item
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (pairs[mid].item0 <= item) lo = mid; else hi = mid;
-        }
-        const NnPair P = pairs[lo];
-        const int64_t oi = img_off[P.i], oj = img_off[P.j];
-        const int ni = (int)(img_off[P.i + 1] - oi), nj = (int)(img_off[P.j + 1] - oj);
-        const int q = (item - P.item0) * kNnRows + tid;
-        const bool qv = q < ni;
-        uint4 v[8];
-        stage::load_row(desc + (size_t)(oi + (qv ? q : 0)) * kDim, qv, v);
-        const float nq = (float)stage::store_row(v, At, tid, kNnRows);
-        float e1 = kInf, e2 = kInf;
-        int j1 = -1;
-
-        for (int c0 = 0; c0 < nj; c0 += kNnChunk) {
-            const int nc = min(kNnChunk, nj - c0);
-            const int N = (nc + 15) / 16 * 16;
-            for (int r = tid; r < N; r += kNnThreads) {
-                const bool have = r < nc;
-                stage::load_row(desc + (size_t)(oj + c0 + (have ? r : 0)) * kDim, have, v);
-                const uint32_t nn = stage::store_row(v, Bt, r, N);
-                nb[r] = have ? (float)nn : kInf;
-            }
+    if (warp < 4) {
+        // ---------------- producers
+        uint32_t g = 0, it = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++it) {
+            const NnItem t = nn_item(pairs, n_pairs, img_off, item);
+            if (!nn_wait(emptyA, (it & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+            uint4 v[8];
+            const bool qv = t.q0 + tid < t.ni;
+            stage::load_row(desc + (size_t)(t.oi + t.q0 + (qv ? tid : 0)) * kDim, qv, v);
+            stage::store_row(v, At, tid, kNnRows);
             tc::fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
-                tc::fence_after();
-                stage::mma_128xN(tmem, At, Bt, N);
-                tc::commit(mbar);
-            }
-            const bool ok = tc::mbar_wait(mbar, parity, kNnPolls);
-            parity ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                // the accumulator never completed: report, give the MMA a last bounded wait, stop
-                if (tid == 0) atomicExch(err, 1);
-                tc::mbar_wait(mbar, parity ^ 1u, kNnPolls);
-                failed = true;
-                break;
-            }
-            tc::fence_after();
-            // q1 keeps its index, q2 only its value (the outputs need no j2);
-            // columns in ascending j, so a tie keeps the smaller j as q1
-            for (int cc = 0; cc < N; cc += 16) {
-                uint32_t acc[16];
-                tc::tmem_ld16(lane_base + cc, acc);
-                tc::tmem_wait_ld();
-                const int jb = c0 + cc;
-#pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    // exact: |x|^2 + |y|^2 < 2^24 and the result is a squared distance
-                    const float d = fmaf(-2.f, __uint_as_float(acc[u]), nq + nb[cc + u]);
-                    j1 = d < e1 ? jb + u : j1;
-                    e2 = fminf(e2, fmaxf(e1, d));
-                    e1 = fminf(e1, d);
+            tc::mbar_arrive(fullA);
+            for (int c0 = 0; c0 < t.nj; c0 += kNnChunk, ++g) {
+                const int nc = min(kNnChunk, t.nj - c0), N = (nc + 15) / 16 * 16;
+                const uint32_t s = g & 1u, ph = (g >> 1) & 1u;
+                if (!nn_wait(&emptyB[s], ph ^ 1u, abort_flag)) { ok = false; break; }
+                unsigned char* B = Bt + s * kNnB;
+                float* nb = nbr + (g & 3u) * kNnChunk;
+                for (int r = tid; r < N; r += kNnProd) {
+                    const bool have = r < nc;
+                    stage::load_row(desc + (size_t)(t.oj + c0 + (have ? r : 0)) * kDim, have, v);
+                    const uint32_t nn = stage::store_row(v, B, r, N);
+                    nb[r] = have ? (float)nn : kInf;
                 }
+                tc::fence_proxy_async();
+                tc::mbar_arrive(&fullB[s]);
+                tc::mbar_arrive(&nbFull[g & 3u]);
             }
-            tc::fence_before();
-            __syncthreads();   // TMEM and the B tile are reused by the next chunk
         }
-        if (!failed && qv) {
-            const int64_t row = P.row_off + q;
-            const bool has2 = nj >= 2;   // e2 is finite exactly when J has two rows
-            const uint32_t u1 = j1 >= 0 ? (uint32_t)e1 : 0xFFFFFFFFu, u2 = has2 ? (uint32_t)e2 : 0xFFFFFFFFu;
-            const bool pass = has2 && (int64_t)ratio_den * ratio_den * u1 < (int64_t)ratio_num * ratio_num * u2;
-            best_j[row] = pass ? j1 : -1;
-            if (d1sq) d1sq[row] = u1;
-            if (d2sq) d2sq[row] = u2;
+        if (!ok) give_up();
+    } else if (warp == kNnMmaWarp) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            uint32_t g = 0, it = 0;
+            int64_t last = -1;   // the last chunk committed
+            bool ok = true;
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++it) {
+                const NnItem t = nn_item(pairs, n_pairs, img_off, item);
+                if (!nn_wait(fullA, it & 1u, abort_flag)) { ok = false; break; }
+                for (int c0 = 0; c0 < t.nj; c0 += kNnChunk, ++g) {
+                    const int nc = min(kNnChunk, t.nj - c0), N = (nc + 15) / 16 * 16;
+                    const uint32_t s = g & 1u, ph = (g >> 1) & 1u;
+                    if (!nn_wait(&fullB[s], ph, abort_flag) || !nn_wait(&accEmpty[s], ph ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    stage::mma_128xN(tmem + s * kNnChunk, At, Bt + s * kNnB, N);
+                    tc::commit(&emptyB[s]);
+                    tc::commit(&accFull[s]);
+                    last = g;
+                }
+                if (ok) tc::commit(emptyA);   // A is free once this item's MMAs have read it
+            }
+            if (!ok) give_up();
+            // the tensor memory is freed below: wait (bounded) for the last MMAs issued
+            if (last >= 0) tc::mbar_wait(&accFull[last & 1], (uint32_t)(last >> 1) & 1u, kNnPolls);
         }
-        __syncthreads();   // the A tile is restaged by the next item
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: query row 32 (warp % 4) + lane of each item
+        const int row = 32 * (warp & 3) + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        uint32_t g = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+            const NnItem t = nn_item(pairs, n_pairs, img_off, item);
+            const int q = t.q0 + row;
+            const bool qv = q < t.ni;
+            const float nq = qv ? (float)row_norm(desc + (size_t)(t.oi + q) * kDim) : 0.f;
+            float e1 = kInf, e2 = kInf;
+            int j1 = -1;
+            for (int c0 = 0; c0 < t.nj; c0 += kNnChunk, ++g) {
+                const int nc = min(kNnChunk, t.nj - c0), N = (nc + 15) / 16 * 16;
+                const uint32_t s = g & 1u, ph = (g >> 1) & 1u;
+                const float* nb = nbr + (g & 3u) * kNnChunk;
+                bool got = true;
+                if (lane == 0)
+                    got = nn_wait(&nbFull[g & 3u], (g >> 2) & 1u, abort_flag) && nn_wait(&accFull[s], ph, abort_flag);
+                if (!__shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0)) { ok = false; break; }
+                tc::fence_after();
+                for (int cc = 0; cc < N; cc += 16) {
+                    uint32_t acc[16];
+                    tc::tmem_ld16(lane_base + s * kNnChunk + cc, acc);
+                    tc::tmem_wait_ld();
+                    const int jb = c0 + cc;
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        // exact: |x|^2 + |y|^2 < 2^24 and the result is a squared distance
+                        const float d = fmaf(-2.f, __uint_as_float(acc[u]), nq + nb[cc + u]);
+                        j1 = d < e1 ? jb + u : j1;
+                        e2 = fminf(e2, fmaxf(e1, d));
+                        e1 = fminf(e1, d);
+                    }
+                }
+                tc::fence_before();
+                tc::mbar_arrive(&accEmpty[s]);
+            }
+            if (!ok) break;
+            if (qv) {
+                const int64_t o = t.row0 + row;
+                const bool has2 = t.nj >= 2;   // e2 is finite exactly when J has two rows
+                const uint32_t u1 = j1 >= 0 ? (uint32_t)e1 : 0xFFFFFFFFu, u2 = has2 ? (uint32_t)e2 : 0xFFFFFFFFu;
+                const bool pass = has2 && (int64_t)ratio_den * ratio_den * u1 < (int64_t)ratio_num * ratio_num * u2;
+                best_j[o] = pass ? j1 : -1;
+                if (d1sq) d1sq[o] = u1;
+                if (d2sq) d2sq[o] = u2;
+            }
+        }
+        if (!ok) give_up();
     }
+    tc::fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kNnChunk);
+    if (warp == kNnMmaWarp) tc::tmem_dealloc(tmem, 2 * kNnChunk);
 }
 
 // Workspace: error flag (fixed place), image offsets, pair records.
@@ -201,14 +319,14 @@ extern "C" cm_status cm_nn_pairs(const uint8_t* desc, const int64_t* img_off, in
     int dev = 0, sms = 148;
     CM_CUDA(cudaGetDevice(&dev));
     CM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // two CTAs per SM at most: their TMEM (2 x 256 columns) always fits
-    size_t smem = (size_t)kNnRows * 256 + (size_t)kNnChunk * 256 + kNnChunk * 4 + 64;
-    smem = std::max(smem, (size_t)(228 * 1024) / 3 + 1024);
+    // one CTA per SM: A, two B buffers and the norm ring in shared memory, two
+    // 256-column accumulators (all of TMEM)
+    const size_t smem = (size_t)kNnA + 2 * (size_t)kNnB + 4 * kNnChunk * 4 + 16 * 8 + 1024;
     CM_CUDA(cudaFuncSetAttribute(k_nn_exhaustive, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = (int)std::min<int64_t>(items, 2 * (int64_t)sms);
-    k_nn_exhaustive<<<grid, kNnThreads, smem, s>>>(desc, reinterpret_cast<const int64_t*>(base + w.off),
-                                                   reinterpret_cast<const NnPair*>(base + w.pairs), (int)n_pairs,
-                                                   (int)items, ratio_num, ratio_den, best_j, d1sq, d2sq, err);
+    const int grid = (int)std::min<int64_t>(items, (int64_t)sms);
+    k_nn_exhaustive<<<grid, kNnPipeThreads, smem, s>>>(desc, reinterpret_cast<const int64_t*>(base + w.off),
+                                                       reinterpret_cast<const NnPair*>(base + w.pairs), (int)n_pairs,
+                                                       (int)items, ratio_num, ratio_den, best_j, d1sq, d2sq, err);
     CM_CUDA(cudaGetLastError());
     return CM_OK;
 }
