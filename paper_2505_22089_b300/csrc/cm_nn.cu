@@ -221,18 +221,28 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
                     got = nn_wait(&nbFull[g & 3u], (g >> 2) & 1u, abort_flag) && nn_wait(&accFull[s], ph, abort_flag);
                 if (!__shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0)) { ok = false; break; }
                 tc::fence_after();
+                // t = |y|^2 - 2 x.y, exact (|t| < 2^24); d^2 = |x|^2 + t is added at the end.
+                // A group of 16 columns with no t below q2's is skipped whole: it
+                // cannot change q1 or q2.
                 for (int cc = 0; cc < N; cc += 16) {
                     uint32_t acc[16];
                     tc::tmem_ld16(lane_base + s * kNnChunk + cc, acc);
                     tc::tmem_wait_ld();
-                    const int jb = c0 + cc;
+                    float tv[16];
+                    float m = kInf;
 #pragma unroll
                     for (int u = 0; u < 16; ++u) {
-                        // exact: |x|^2 + |y|^2 < 2^24 and the result is a squared distance
-                        const float d = fmaf(-2.f, __uint_as_float(acc[u]), nq + nb[cc + u]);
-                        j1 = d < e1 ? jb + u : j1;
-                        e2 = fminf(e2, fmaxf(e1, d));
-                        e1 = fminf(e1, d);
+                        tv[u] = fmaf(-2.f, __uint_as_float(acc[u]), nb[cc + u]);
+                        m = fminf(m, tv[u]);
+                    }
+                    if (__any_sync(0xFFFFFFFFu, m < e2)) {
+                        const int jb = c0 + cc;
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            j1 = tv[u] < e1 ? jb + u : j1;   // columns in ascending j: a tie keeps the smaller j
+                            e2 = fminf(e2, fmaxf(e1, tv[u]));
+                            e1 = fminf(e1, tv[u]);
+                        }
                     }
                 }
                 tc::fence_before();
@@ -242,7 +252,8 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
             if (qv) {
                 const int64_t o = t.row0 + row;
                 const bool has2 = t.nj >= 2;   // e2 is finite exactly when J has two rows
-                const uint32_t u1 = j1 >= 0 ? (uint32_t)e1 : 0xFFFFFFFFu, u2 = has2 ? (uint32_t)e2 : 0xFFFFFFFFu;
+                const uint32_t u1 = j1 >= 0 ? (uint32_t)(e1 + nq) : 0xFFFFFFFFu,   // exact sums of integers
+                               u2 = has2 ? (uint32_t)(e2 + nq) : 0xFFFFFFFFu;
                 const bool pass = has2 && (int64_t)ratio_den * ratio_den * u1 < (int64_t)ratio_num * ratio_num * u2;
                 best_j[o] = pass ? j1 : -1;
                 if (d1sq) d1sq[o] = u1;
