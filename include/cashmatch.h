@@ -496,8 +496,11 @@ cm_status cm_workspace_status(const void* d_work, cm_stream stream);
 cm_status cm_selftest_wait(int32_t polls, cm_stream stream);
 
 /* ---- exhaustive nearest neighbours (quality ceiling) --------------------- */
-/* Device workspace of cm_nn_pairs. */
-cm_status cm_nn_workspace_bytes(int32_t n_images, int64_t n_pairs, uint64_t* bytes);
+/* Device workspace of cm_nn_pairs for these images and pairs (it holds a BF16
+ * operand copy of every database image the pairs name: 128 KB per 256 rows,
+ * 64 KB of it the tile). */
+cm_status cm_nn_workspace_bytes(const int64_t* img_off, int32_t n_images, const cm_pair* pairs, int64_t n_pairs,
+                                uint64_t* bytes);
 /* Exhaustive nearest neighbours with the exact ratio test for each pair: for
  * every query x of image i, q1 and q2 = the two smallest (d^2, j) over ALL
  * rows y of image j (d^2 exact squared Euclidean distance on the uint8 rows,

@@ -194,7 +194,7 @@ def lib():
             "cm_match_plan_sao": (i32, [vp, vp, vp, vp, vp, i32, ctypes.c_float, vp, vp, u64, vp]),
             "cm_pipeline_workspace_bytes_ex": (i32, [vp, vp, vp, i64, vp, ctypes.POINTER(u64)]),
             "cm_run_schedule_ex": (i32, [vp, vp, vp, i64, vp, vp, u64, vp, vp, i32, vp, vp, vp]),
-            "cm_nn_workspace_bytes": (i32, [i32, i64, ctypes.POINTER(u64)]),
+            "cm_nn_workspace_bytes": (i32, [vp, i32, vp, i64, ctypes.POINTER(u64)]),
             "cm_nn_pairs": (i32, [vp, vp, i32, vp, i64, i32, i32, vp, u64, vp, vp, vp, vp]),
             "cm_autotune": (i32, [vp, vp, i64, vp, i32, ctypes.c_float, vp, ctypes.POINTER(TuneResult)]),
         }
@@ -398,7 +398,8 @@ def nn_pairs(desc, n_desc, pairs, ratio=(4, 5), stream=None, check_status: bool 
     pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
     rows = np.concatenate([[0], np.cumsum(nd[pr[:, 0]])]).astype(np.int64) if len(pr) else np.zeros(1, np.int64)
     ws = ctypes.c_uint64()
-    check(lib().cm_nn_workspace_bytes(len(nd), len(pr), ctypes.byref(ws)))
+    check(lib().cm_nn_workspace_bytes(off.ctypes.data, len(nd), pr.ctypes.data if len(pr) else None, len(pr),
+                                      ctypes.byref(ws)))
     work = torch.empty(int(ws.value) + 256, dtype=torch.uint8, device=desc.device)
     wbase = (work.data_ptr() + 255) // 256 * 256
     n = int(rows[-1])

@@ -38,17 +38,22 @@ struct NnPair {
     int32_t pad;
 };
 
+// k_nn_tile writes each database image once as BF16 operand tiles of 256 rows
+// (64 KB each, zero rows past the image) in the MMA's shared-memory layout,
+// with the rows' squared norms (+inf past the image).
+//
 // Warp roles of k_nn_exhaustive (288 threads, one CTA per SM):
-//   warps 0-3  producers: stage each work item's 128 query rows (A) and each
-//              database chunk of 256 rows into one of two B buffers, with
-//              the chunk's database norms;
+//   warps 0-3  producers: stage each work item's 128 query rows (A, converted
+//              from uint8); one thread copies each database tile and its
+//              norms with bulk copies into one of two B buffers and the norm
+//              ring;
 //   warp 4     MMA issuer: one thread, each chunk into one of two TMEM
 //              accumulators (2 x 256 columns), commits that free the B
 //              buffer, fill the accumulator and, after an item, free A;
 //   warps 5-8  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one query
 //              each), keeps q1 (d^2, j) and q2's d^2, and writes the outputs.
-// Staging, MMA and epilogue of neighbouring chunks overlap.  The norms go to
-// a ring of four buffers that the epilogue reads after a barrier of its own
+// Copies, MMA and epilogue of neighbouring chunks overlap.  The norms go to a
+// ring of four buffers that the epilogue reads after a barrier of its own
 // (the producers cannot get four chunks ahead of the epilogue, so a buffer is
 // never refilled while it is read).  Every wait is bounded and also gives up
 // once another role has aborted.
@@ -68,7 +73,7 @@ __device__ __forceinline__ bool nn_wait(uint64_t* mbar, uint32_t parity, volatil
 // One work item: a tile of up to 128 queries of one pair.
 struct NnItem {
     int64_t oi, oj, row0;
-    int ni, nj, q0;
+    int ni, nj, q0, pj;
 };
 
 __device__ __forceinline__ NnItem nn_item(const NnPair* pairs, int n_pairs, const int64_t* img_off, int item) {
@@ -85,6 +90,7 @@ __device__ __forceinline__ NnItem nn_item(const NnPair* pairs, int n_pairs, cons
     t.nj = (int)(img_off[P.j + 1] - t.oj);
     t.q0 = (item - P.item0) * kNnRows;
     t.row0 = P.row_off + t.q0;
+    t.pj = P.j;
     return t;
 }
 
@@ -101,9 +107,24 @@ __device__ __forceinline__ uint32_t row_norm(const uint8_t* row) {
     return nn;
 }
 
+__global__ void __launch_bounds__(kNnChunk)
+k_nn_tile(const uint8_t* __restrict__ desc, const int64_t* __restrict__ img_off, const int32_t* __restrict__ chunk_img,
+          const int32_t* __restrict__ chunk_c0, unsigned char* __restrict__ tiles, float* __restrict__ norms) {
+    const int c = blockIdx.x, r = threadIdx.x;
+    const int img = chunk_img[c];
+    const int64_t o = img_off[img];
+    const int n = (int)(img_off[img + 1] - o), row = chunk_c0[c] + r;
+    const bool have = row < n;
+    uint4 v[8];
+    stage::load_row(desc + (size_t)(o + (have ? row : 0)) * kDim, have, v);
+    const uint32_t nn = stage::store_row(v, tiles + (size_t)c * kNnB, r, kNnChunk);
+    norms[(size_t)c * kNnChunk + r] = have ? (float)nn : __uint_as_float(0x7F800000u);
+}
+
 __global__ void __launch_bounds__(kNnPipeThreads, 1)
 k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ img_off, const NnPair* __restrict__ pairs,
-                int n_pairs, int n_items, int ratio_num, int ratio_den, int32_t* __restrict__ best_j,
+                int n_pairs, int n_items, int ratio_num, int ratio_den, const unsigned char* __restrict__ tiles,
+                const float* __restrict__ norms, const int64_t* __restrict__ tile_of, int32_t* __restrict__ best_j,
                 uint32_t* __restrict__ d1sq, uint32_t* __restrict__ d2sq, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* At = smem;                                   // 128 x 256 B
@@ -118,14 +139,14 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
     const float kInf = __uint_as_float(0x7F800000u);
     if (tid == 0) {
         for (int k = 0; k < 2; ++k) {
-            tc::mbar_init(&fullB[k], kNnProd);
+            tc::mbar_init(&fullB[k], 1);
             tc::mbar_init(&emptyB[k], 1);
             tc::mbar_init(&accFull[k], 1);
             tc::mbar_init(&accEmpty[k], 128);
         }
         tc::mbar_init(fullA, kNnProd);
         tc::mbar_init(emptyA, 1);
-        for (int k = 0; k < 4; ++k) tc::mbar_init(&nbFull[k], kNnProd);
+        for (int k = 0; k < 4; ++k) tc::mbar_init(&nbFull[k], 1);
         s_abort = 0;
     }
     if (warp == kNnMmaWarp) tc::tmem_alloc(&s_tmem, 2 * kNnChunk);
@@ -152,21 +173,17 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
             stage::store_row(v, At, tid, kNnRows);
             tc::fence_proxy_async();
             tc::mbar_arrive(fullA);
-            for (int c0 = 0; c0 < t.nj; c0 += kNnChunk, ++g) {
-                const int nc = min(kNnChunk, t.nj - c0), N = (nc + 15) / 16 * 16;
-                const uint32_t s = g & 1u, ph = (g >> 1) & 1u;
-                if (!nn_wait(&emptyB[s], ph ^ 1u, abort_flag)) { ok = false; break; }
-                unsigned char* B = Bt + s * kNnB;
-                float* nb = nbr + (g & 3u) * kNnChunk;
-                for (int r = tid; r < N; r += kNnProd) {
-                    const bool have = r < nc;
-                    stage::load_row(desc + (size_t)(t.oj + c0 + (have ? r : 0)) * kDim, have, v);
-                    const uint32_t nn = stage::store_row(v, B, r, N);
-                    nb[r] = have ? (float)nn : kInf;
+            if (tid == 0) {   // the database tiles of this item, one bulk copy each
+                const int64_t tb = tile_of[t.pj];
+                for (int c0 = 0; c0 < t.nj; c0 += kNnChunk, ++g) {
+                    const uint32_t s = g & 1u, ph = (g >> 1) & 1u;
+                    if (!nn_wait(&emptyB[s], ph ^ 1u, abort_flag)) { ok = false; break; }
+                    const int64_t c = tb + c0 / kNnChunk;
+                    tc::mbar_arrive_expect_tx(&fullB[s], kNnB);
+                    tc::bulk_g2s(Bt + s * kNnB, tiles + (size_t)c * kNnB, kNnB, &fullB[s]);
+                    tc::mbar_arrive_expect_tx(&nbFull[g & 3u], kNnChunk * 4);
+                    tc::bulk_g2s(nbr + (g & 3u) * kNnChunk, norms + (size_t)c * kNnChunk, kNnChunk * 4, &nbFull[g & 3u]);
                 }
-                tc::fence_proxy_async();
-                tc::mbar_arrive(&fullB[s]);
-                tc::mbar_arrive(&nbFull[g & 3u]);
             }
         }
         if (!ok) give_up();
@@ -180,14 +197,13 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
                 const NnItem t = nn_item(pairs, n_pairs, img_off, item);
                 if (!nn_wait(fullA, it & 1u, abort_flag)) { ok = false; break; }
                 for (int c0 = 0; c0 < t.nj; c0 += kNnChunk, ++g) {
-                    const int nc = min(kNnChunk, t.nj - c0), N = (nc + 15) / 16 * 16;
                     const uint32_t s = g & 1u, ph = (g >> 1) & 1u;
                     if (!nn_wait(&fullB[s], ph, abort_flag) || !nn_wait(&accEmpty[s], ph ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc::fence_after();
-                    stage::mma_128xN(tmem + s * kNnChunk, At, Bt + s * kNnB, N);
+                    stage::mma_128xN(tmem + s * kNnChunk, At, Bt + s * kNnB, kNnChunk);   // whole tiles
                     tc::commit(&emptyB[s]);
                     tc::commit(&accFull[s]);
                     last = g;
@@ -213,7 +229,7 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
             float e1 = kInf, e2 = kInf;
             int j1 = -1;
             for (int c0 = 0; c0 < t.nj; c0 += kNnChunk, ++g) {
-                const int nc = min(kNnChunk, t.nj - c0), N = (nc + 15) / 16 * 16;
+                constexpr int N = kNnChunk;   // columns past the image have norm +inf and never win
                 const uint32_t s = g & 1u, ph = (g >> 1) & 1u;
                 const float* nb = nbr + (g & 3u) * kNnChunk;
                 bool got = true;
@@ -267,18 +283,59 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
     if (warp == kNnMmaWarp) tc::tmem_dealloc(tmem, 2 * kNnChunk);
 }
 
-// Workspace: error flag (fixed place), image offsets, pair records.
+// Workspace: error flag (fixed place), image offsets, pair records, the tile
+// index of each image (-1: not a database image here), the chunk table, the
+// database images' BF16 tiles (64 KB per 256 rows) and their norms.
 struct NnWork {
-    uint64_t err, off, pairs, total;
+    uint64_t err, off, pairs, tile_of, chunk_img, chunk_c0, tiles, norms, total;
 };
 
-NnWork nn_layout(int32_t n_images, int64_t n_pairs) {
+NnWork nn_layout(int32_t n_images, int64_t n_pairs, int64_t n_chunks) {
     NnWork w{};
     w.err = 0;
     w.off = align_up(4);
     w.pairs = align_up(w.off + 8 * (uint64_t)(n_images + 1));
-    w.total = align_up(w.pairs + sizeof(NnPair) * (uint64_t)n_pairs);
+    w.tile_of = align_up(w.pairs + sizeof(NnPair) * (uint64_t)n_pairs);
+    w.chunk_img = align_up(w.tile_of + 8 * (uint64_t)std::max(n_images, 1));
+    w.chunk_c0 = align_up(w.chunk_img + 4 * (uint64_t)n_chunks);
+    w.tiles = align_up(w.chunk_c0 + 4 * (uint64_t)n_chunks);
+    w.norms = align_up(w.tiles + (uint64_t)kNnB * (uint64_t)n_chunks);
+    w.total = align_up(w.norms + 4 * (uint64_t)kNnChunk * (uint64_t)n_chunks);
     return w;
+}
+
+// The database images of the pair list in first-use order and their tiles.
+struct NnTiles {
+    std::vector<int64_t> tile_of;   // [n_images]
+    std::vector<int32_t> chunk_img, chunk_c0;
+};
+
+cm_status nn_tiles(const int64_t* img_off, int32_t n_images, const cm_pair* pairs, int64_t n_pairs, NnTiles* t) {
+    t->tile_of.assign((size_t)std::max(n_images, 0), -1);
+    t->chunk_img.clear();
+    t->chunk_c0.clear();
+    for (int64_t k = 0; k < n_pairs; ++k) {
+        const cm_pair pr = pairs[k];
+        if (pr.i < 0 || pr.j < 0 || pr.i >= n_images || pr.j >= n_images)
+            return host_fail(CM_ERR_INVALID, "cm_nn_pairs: pair %lld names an image out of range", (long long)k);
+        if (t->tile_of[pr.j] >= 0) continue;
+        t->tile_of[pr.j] = (int64_t)t->chunk_img.size();
+        const int64_t n = img_off[pr.j + 1] - img_off[pr.j];
+        for (int64_t c0 = 0; c0 < n; c0 += kNnChunk) {
+            t->chunk_img.push_back(pr.j);
+            t->chunk_c0.push_back((int32_t)c0);
+        }
+    }
+    return CM_OK;
+}
+
+cm_status nn_check_offsets(const int64_t* img_off, int32_t n_images) {
+    if (n_images < 0 || !img_off) return host_fail(CM_ERR_INVALID, "cm_nn_pairs: bad image offsets");
+    if (img_off[0] != 0) return host_fail(CM_ERR_INVALID, "cm_nn_pairs: img_off[0] must be 0");
+    for (int32_t i = 0; i < n_images; ++i)
+        if (img_off[i + 1] < img_off[i] || img_off[i + 1] - img_off[i] > 65535)
+            return host_fail(CM_ERR_INVALID, "cm_nn_pairs: img_off not ascending or an image above 65535 rows");
+    return CM_OK;
 }
 
 }  // namespace
@@ -287,9 +344,14 @@ NnWork nn_layout(int32_t n_images, int64_t n_pairs) {
 
 using namespace cm;
 
-extern "C" cm_status cm_nn_workspace_bytes(int32_t n_images, int64_t n_pairs, uint64_t* bytes) {
-    if (n_images < 0 || n_pairs < 0 || !bytes) return host_fail(CM_ERR_INVALID, "cm_nn_workspace_bytes: bad argument");
-    *bytes = nn_layout(n_images, n_pairs).total;
+extern "C" cm_status cm_nn_workspace_bytes(const int64_t* img_off, int32_t n_images, const cm_pair* pairs,
+                                           int64_t n_pairs, uint64_t* bytes) {
+    if (n_pairs < 0 || (n_pairs && !pairs) || !bytes) return host_fail(CM_ERR_INVALID, "cm_nn_workspace_bytes: bad argument");
+    cm_status st = nn_check_offsets(img_off, n_images);
+    if (st != CM_OK) return st;
+    NnTiles t;
+    if ((st = nn_tiles(img_off, n_images, pairs, n_pairs, &t)) != CM_OK) return st;
+    *bytes = nn_layout(n_images, n_pairs, (int64_t)t.chunk_img.size()).total;
     return CM_OK;
 }
 
@@ -297,22 +359,21 @@ extern "C" cm_status cm_nn_pairs(const uint8_t* desc, const int64_t* img_off, in
                                  int64_t n_pairs, int32_t ratio_num, int32_t ratio_den, void* d_work,
                                  uint64_t work_bytes, int32_t* best_j, uint32_t* d1sq, uint32_t* d2sq,
                                  cm_stream stream) {
-    if (n_images < 0 || !img_off || n_pairs < 0 || (n_pairs && (!pairs || !best_j)) || !d_work || ratio_num < 1 ||
-        ratio_den <= ratio_num || ratio_den > 1024)
+    if (n_pairs < 0 || (n_pairs && (!pairs || !best_j)) || !d_work || ratio_num < 1 || ratio_den <= ratio_num ||
+        ratio_den > 1024)
         return host_fail(CM_ERR_INVALID, "cm_nn_pairs: bad argument");
-    if (img_off[0] != 0) return host_fail(CM_ERR_INVALID, "cm_nn_pairs: img_off[0] must be 0");
-    for (int32_t i = 0; i < n_images; ++i)
-        if (img_off[i + 1] < img_off[i] || img_off[i + 1] - img_off[i] > 65535)
-            return host_fail(CM_ERR_INVALID, "cm_nn_pairs: img_off not ascending or an image above 65535 rows");
-    const NnWork w = nn_layout(n_images, n_pairs);
+    cm_status st = nn_check_offsets(img_off, n_images);
+    if (st != CM_OK) return st;
+    NnTiles tl;
+    if ((st = nn_tiles(img_off, n_images, pairs, n_pairs, &tl)) != CM_OK) return st;
+    const int64_t n_chunks = (int64_t)tl.chunk_img.size();
+    const NnWork w = nn_layout(n_images, n_pairs, n_chunks);
     if (work_bytes < w.total || (reinterpret_cast<uintptr_t>(d_work) & (kAlign - 1)))
         return host_fail(CM_ERR_BUDGET, "cm_nn_pairs: workspace smaller than cm_nn_workspace_bytes or not 256-byte aligned");
     std::vector<NnPair> rec((size_t)n_pairs);
     int64_t rows = 0, items = 0;
     for (int64_t k = 0; k < n_pairs; ++k) {
         const cm_pair pr = pairs[k];
-        if (pr.i < 0 || pr.j < 0 || pr.i >= n_images || pr.j >= n_images)
-            return host_fail(CM_ERR_INVALID, "cm_nn_pairs: pair %lld names an image out of range", (long long)k);
         const int64_t ni = img_off[pr.i + 1] - img_off[pr.i];
         rec[k] = {pr.i, pr.j, rows, (int32_t)items, 0};
         rows += ni;
@@ -327,6 +388,16 @@ extern "C" cm_status cm_nn_pairs(const uint8_t* desc, const int64_t* img_off, in
     if (items == 0) return CM_OK;
     CM_CUDA(cudaMemcpyAsync(base + w.off, img_off, 8 * (size_t)(n_images + 1), cudaMemcpyHostToDevice, s));
     CM_CUDA(cudaMemcpyAsync(base + w.pairs, rec.data(), sizeof(NnPair) * rec.size(), cudaMemcpyHostToDevice, s));
+    CM_CUDA(cudaMemcpyAsync(base + w.tile_of, tl.tile_of.data(), 8 * tl.tile_of.size(), cudaMemcpyHostToDevice, s));
+    if (n_chunks) {
+        CM_CUDA(cudaMemcpyAsync(base + w.chunk_img, tl.chunk_img.data(), 4 * (size_t)n_chunks, cudaMemcpyHostToDevice, s));
+        CM_CUDA(cudaMemcpyAsync(base + w.chunk_c0, tl.chunk_c0.data(), 4 * (size_t)n_chunks, cudaMemcpyHostToDevice, s));
+        k_nn_tile<<<(unsigned)n_chunks, kNnChunk, 0, s>>>(desc, reinterpret_cast<const int64_t*>(base + w.off),
+                                                          reinterpret_cast<const int32_t*>(base + w.chunk_img),
+                                                          reinterpret_cast<const int32_t*>(base + w.chunk_c0),
+                                                          base + w.tiles, reinterpret_cast<float*>(base + w.norms));
+        CM_CUDA(cudaGetLastError());
+    }
     int dev = 0, sms = 148;
     CM_CUDA(cudaGetDevice(&dev));
     CM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -335,9 +406,10 @@ extern "C" cm_status cm_nn_pairs(const uint8_t* desc, const int64_t* img_off, in
     const size_t smem = (size_t)kNnA + 2 * (size_t)kNnB + 4 * kNnChunk * 4 + 16 * 8 + 1024;
     CM_CUDA(cudaFuncSetAttribute(k_nn_exhaustive, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<int64_t>(items, (int64_t)sms);
-    k_nn_exhaustive<<<grid, kNnPipeThreads, smem, s>>>(desc, reinterpret_cast<const int64_t*>(base + w.off),
-                                                       reinterpret_cast<const NnPair*>(base + w.pairs), (int)n_pairs,
-                                                       (int)items, ratio_num, ratio_den, best_j, d1sq, d2sq, err);
+    k_nn_exhaustive<<<grid, kNnPipeThreads, smem, s>>>(
+        desc, reinterpret_cast<const int64_t*>(base + w.off), reinterpret_cast<const NnPair*>(base + w.pairs),
+        (int)n_pairs, (int)items, ratio_num, ratio_den, base + w.tiles, reinterpret_cast<const float*>(base + w.norms),
+        reinterpret_cast<const int64_t*>(base + w.tile_of), best_j, d1sq, d2sq, err);
     CM_CUDA(cudaGetLastError());
     return CM_OK;
 }

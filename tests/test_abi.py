@@ -120,8 +120,13 @@ def test_host_argument_checks_of_the_later_entry_points():
     assert lib.cm_nn_pairs(None, off.ctypes.data, 1, None, 0, 5, 4, None, 0, None, None, None, None) == cm.CM_ERR_INVALID
     b = cm.ctypes.c_uint64()
     assert lib.cm_vlad_workspace_bytes(3, 100, cm.ctypes.byref(b)) == cm.CM_OK and b.value % 256 == 0
-    assert lib.cm_nn_workspace_bytes(3, 7, cm.ctypes.byref(b)) == cm.CM_OK and b.value % 256 == 0
-    assert lib.cm_nn_workspace_bytes(-1, 7, cm.ctypes.byref(b)) == cm.CM_ERR_INVALID
+    off3 = np.array([0, 300, 700, 700], dtype=np.int64)
+    pr3 = np.array([[0, 1], [1, 0], [2, 0]], dtype=np.int32)   # database images 1 (400 rows) and 0 (300 rows)
+    assert lib.cm_nn_workspace_bytes(off3.ctypes.data, 3, pr3.ctypes.data, 3, cm.ctypes.byref(b)) == cm.CM_OK
+    assert b.value % 256 == 0 and b.value >= 4 * (65536 + 1024)   # two 256-row tiles per database image
+    assert lib.cm_nn_workspace_bytes(off3.ctypes.data, 3, pr3.ctypes.data, -1, cm.ctypes.byref(b)) == cm.CM_ERR_INVALID
+    bad = np.array([[0, 5]], dtype=np.int32)
+    assert lib.cm_nn_workspace_bytes(off3.ctypes.data, 3, bad.ctypes.data, 1, cm.ctypes.byref(b)) == cm.CM_ERR_INVALID
 
 
 def test_images_above_65535_descriptors_are_rejected():
