@@ -42,7 +42,7 @@ struct NnPair {
 // (64 KB each, zero rows past the image) in the MMA's shared-memory layout,
 // with the rows' squared norms (+inf past the image).
 //
-// Warp roles of k_nn_exhaustive (416 threads, one CTA per SM):
+// Warp roles of k_nn_exhaustive ((5 + 4 kNnSplit) warps, one CTA per SM):
 //   warps 0-3  producers: stage each work item's 128 query rows (A, converted
 //              from uint8); one thread copies each database tile and its
 //              norms with bulk copies into one of two B buffers and the norm
@@ -50,10 +50,10 @@ struct NnPair {
 //   warp 4     MMA issuer: one thread, each chunk into one of two TMEM
 //              accumulators (2 x 256 columns), commits that free the B
 //              buffer, fill the accumulator and, after an item, free A;
-//   warps 5-12 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one query
-//              each) for one half of every chunk's columns (the two warps of a
-//              lane quarter split the chunk), keeps q1 (d^2, j) and q2's d^2,
-//              and the two halves are merged for the outputs.
+//   warps 5..  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one query
+//              each) for part (w - 5) / 4 of every chunk's columns (the
+//              kNnSplit warps of a lane quarter split the chunk), keeps q1
+//              (d^2, j) and q2's d^2, and the parts are merged for the outputs.
 // Copies, MMA and epilogue of neighbouring chunks overlap.  The norms go to a
 // ring of four buffers that the epilogue reads after a barrier of its own
 // (the producers cannot get four chunks ahead of the epilogue, so a buffer is
@@ -61,7 +61,8 @@ struct NnPair {
 // once another role has aborted.
 constexpr int kNnProd = 128;
 constexpr int kNnMmaWarp = 4;
-constexpr int kNnEpiWarps = 8;   // two per TMEM lane quarter, each on half of a chunk's columns
+constexpr int kNnSplit = 4;                  // epilogue warps per TMEM lane quarter
+constexpr int kNnEpiWarps = 4 * kNnSplit;    // each on 1 / kNnSplit of a chunk's columns
 constexpr int kNnPipeThreads = (5 + kNnEpiWarps) * 32;
 constexpr uint32_t kNnA = kNnRows * 256, kNnB = kNnChunk * 256;
 
@@ -147,8 +148,8 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
              *emptyA = bar + 9, *nbFull = bar + 10;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
-    __shared__ float s_half_e1[kNnRows], s_half_e2[kNnRows];   // the upper column halves' partial results
-    __shared__ int s_half_j1[kNnRows];
+    __shared__ float s_part_e1[kNnSplit - 1][kNnRows], s_part_e2[kNnSplit - 1][kNnRows];   // partial results
+    __shared__ int s_part_j1[kNnSplit - 1][kNnRows];                                        // of parts 1..
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float kInf = __uint_as_float(0x7F800000u);
     if (tid == 0) {
@@ -231,18 +232,18 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
         __syncwarp();
     } else {
         // ---------------- epilogue: query row 32 (warp % 4) + lane of each item,
-        // columns [half * 128, half * 128 + 128) of every chunk
+        // columns [part * H, part * H + H) of every chunk
         const int row = 32 * (warp & 3) + lane;
-        const int half = (warp - 5) >= 4 ? 1 : 0;
+        const int part = (warp - 5) / 4;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-        constexpr int H = kNnChunk / 2;
+        constexpr int H = kNnChunk / kNnSplit;
         uint32_t g = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
             const NnItem t = nn_item(pairs, n_pairs, img_off, item);
             const int q = t.q0 + row;
             const bool qv = q < t.ni;
-            const float nq = qv && half == 0 ? (float)row_norm(desc + (size_t)(t.oi + q) * kDim) : 0.f;
+            const float nq = qv && part == 0 ? (float)row_norm(desc + (size_t)(t.oi + q) * kDim) : 0.f;
             float e1 = kInf, e2 = kInf;
             int j1 = -1;
             for (int c0 = 0; c0 < t.nj; c0 += kNnChunk, ++g) {
@@ -256,7 +257,7 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
                 // t = |y|^2 - 2 x.y, exact (|t| < 2^24); d^2 = |x|^2 + t is added at the end.
                 // A group of 16 columns with no t below q2's is skipped whole: it
                 // cannot change q1 or q2.  Columns past the image have norm +inf.
-                for (int cc = half * H; cc < half * H + H; cc += 16) {
+                for (int cc = part * H; cc < part * H + H; cc += 16) {
                     uint32_t acc[16];
                     tc::tmem_ld16(lane_base + s * kNnChunk + cc, acc);
                     tc::tmem_wait_ld();
@@ -281,23 +282,26 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
                 tc::mbar_arrive(&accEmpty[s]);
             }
             if (!ok) give_up();
-            // merge the two column halves of each row: the upper half posts its
-            // partial result, and one barrier of the epilogue warps both orders the
+            // merge the column parts of each row: parts 1.. post their partial
+            // results, and one barrier of the epilogue warps both orders the
             // exchange and decides, the same way for every warp, whether to stop
-            if (half == 1) {
-                s_half_e1[row] = e1;
-                s_half_e2[row] = e2;
-                s_half_j1[row] = j1;
+            if (part > 0) {
+                s_part_e1[part - 1][row] = e1;
+                s_part_e2[part - 1][row] = e2;
+                s_part_j1[part - 1][row] = j1;
             }
             if (epi_bar_or(!ok || *abort_flag)) break;
-            if (half == 0 && qv) {
-                const float f1 = s_half_e1[row], f2 = s_half_e2[row];
-                const int k1 = s_half_j1[row];
-                const bool take = f1 < e1 || (f1 == e1 && k1 >= 0 && (j1 < 0 || k1 < j1));
-                const float m2 = fminf(fmaxf(e1, f1), fminf(e2, f2));
-                j1 = take ? k1 : j1;
-                e1 = fminf(e1, f1);
-                e2 = m2;
+            if (part == 0 && qv) {
+#pragma unroll
+                for (int p = 0; p < kNnSplit - 1; ++p) {   // (q1, q2) of a union: ties keep the smaller j
+                    const float f1 = s_part_e1[p][row], f2 = s_part_e2[p][row];
+                    const int k1 = s_part_j1[p][row];
+                    const bool take = f1 < e1 || (f1 == e1 && k1 >= 0 && (j1 < 0 || k1 < j1));
+                    const float m2 = fminf(fmaxf(e1, f1), fminf(e2, f2));
+                    j1 = take ? k1 : j1;
+                    e1 = fminf(e1, f1);
+                    e2 = m2;
+                }
                 const int64_t o = t.row0 + row;
                 const bool has2 = t.nj >= 2;   // e2 is finite exactly when J has two rows
                 const uint32_t u1 = j1 >= 0 ? (uint32_t)(e1 + nq) : 0xFFFFFFFFu,   // exact sums of integers
@@ -307,7 +311,7 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
                 if (d1sq) d1sq[o] = u1;
                 if (d2sq) d2sq[o] = u2;
             }
-            epi_bar_or(false);   // the halves are read before the next item overwrites them
+            epi_bar_or(false);   // the parts are read before the next item overwrites them
         }
     }
     tc::fence_before();
