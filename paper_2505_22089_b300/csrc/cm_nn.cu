@@ -7,11 +7,15 @@
 // k_nn_exhaustive: a work item is a tile of 128 queries of one pair.  The
 // tile is staged once as the A operand; the database image is walked in
 // chunks of up to 256 rows, each staged as the B operand and multiplied on
-// the tensor cores (128 x N x 128, BF16, FP32 accumulate: every partial sum
-// of x.y is an integer below 2^24, so exact).  The epilogue keeps, per query,
-// the smallest (d^2, j) and the second smallest d^2, with
-// d^2 = |x|^2 + |y|^2 - 2 x.y exact as an FP32 integer; the last chunk is
-// followed by the exact integer ratio test.  Producers, the MMA issuer and
+// the tensor cores (BF16, FP32 accumulate).  The product gives
+// t = |y|^2 - 2 x.y directly: K is 144, the 128 descriptor elements (x
+// against -2 y) and a block of 16 in which A holds (2^16, 2^8, 1, 0, ..) and B
+// the base-256 digits of |y|^2.  That block is issued first, so the
+// accumulator starts at |y|^2 and only decreases, to t >= -|x|^2: every
+// partial sum is an integer of magnitude below 2^23, so exact.  The epilogue
+// keeps, per query, the smallest (t, j) and the second smallest t; with
+// d^2 = |x|^2 + t (exact) the last chunk is followed by the exact integer
+// ratio test.  Producers, the MMA issuer and
 // the epilogue are separate warps with double-buffered operands and
 // accumulators (see the kernel).
 #include <cuda_runtime.h>
@@ -39,14 +43,14 @@ struct NnPair {
 };
 
 // k_nn_tile writes each database image once as BF16 operand tiles of 256 rows
-// (64 KB each, zero rows past the image) in the MMA's shared-memory layout,
-// with the rows' squared norms (+inf past the image).
+// (72 KB each) in the MMA's shared-memory layout; a row past the image has
+// y = 0 and digits (255, 0, 0), so its t = 255 * 2^16 is above every real t
+// (|t| <= 128 * 255^2 < 2^23) and it is never a neighbour.
 //
 // Warp roles of k_nn_exhaustive ((5 + 4 kNnSplit) warps, one CTA per SM):
 //   warps 0-3  producers: stage each work item's 128 query rows (A, converted
-//              from uint8); one thread copies each database tile and its
-//              norms with bulk copies into one of two B buffers and the norm
-//              ring;
+//              from uint8); one thread copies each database tile with a bulk
+//              copy into one of two B buffers;
 //   warp 4     MMA issuer: one thread, each chunk into one of two TMEM
 //              accumulators (2 x 256 columns), commits that free the B
 //              buffer, fill the accumulator and, after an item, free A;
@@ -54,17 +58,15 @@ struct NnPair {
 //              each) for part (w - 5) / 4 of every chunk's columns (the
 //              kNnSplit warps of a lane quarter split the chunk), keeps q1
 //              (d^2, j) and q2's d^2, and the parts are merged for the outputs.
-// Copies, MMA and epilogue of neighbouring chunks overlap.  The norms go to a
-// ring of four buffers that the epilogue reads after a barrier of its own
-// (the producers cannot get four chunks ahead of the epilogue, so a buffer is
-// never refilled while it is read).  Every wait is bounded and also gives up
-// once another role has aborted.
+// Copies, MMA and epilogue of neighbouring chunks overlap.  Every wait is
+// bounded and also gives up once another role has aborted.
 constexpr int kNnProd = 128;
 constexpr int kNnMmaWarp = 4;
 constexpr int kNnSplit = 4;                  // epilogue warps per TMEM lane quarter
 constexpr int kNnEpiWarps = 4 * kNnSplit;    // each on 1 / kNnSplit of a chunk's columns
 constexpr int kNnPipeThreads = (5 + kNnEpiWarps) * 32;
-constexpr uint32_t kNnA = kNnRows * 256, kNnB = kNnChunk * 256;
+constexpr int kNnK = kDim + 16;               // descriptor elements + the |y|^2 block
+constexpr uint32_t kNnA = kNnRows * kNnK * 2, kNnB = kNnChunk * kNnK * 2;
 
 __device__ __forceinline__ bool nn_wait(uint64_t* mbar, uint32_t parity, volatile int* abort_flag) {
     for (int it = 0; it < kNnPolls; it += 64) {
@@ -120,9 +122,20 @@ __device__ __forceinline__ uint32_t row_norm(const uint8_t* row) {
     return nn;
 }
 
+// Bytes b0 and b0+1 of w, each times -2, as two BF16 values: 2^23 + b by one
+// byte permute, then 2^24 - 2 (2^23 + b) = -2b exactly (at most 8
+// significant bits, so the FP32 upper half is its exact BF16).
+__device__ __forceinline__ uint32_t u8x2_to_bf16x2_m2(uint32_t w, int b0) {
+    const float f0 = fmaf(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540 + b0)), -2.f, 16777216.f);
+    const float f1 = fmaf(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7541 + b0)), -2.f, 16777216.f);
+    return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+
+__device__ __forceinline__ uint32_t bf16_hi(float f) { return __float_as_uint(f) >> 16; }
+
 __global__ void __launch_bounds__(kNnChunk)
 k_nn_tile(const uint8_t* __restrict__ desc, const int64_t* __restrict__ img_off, const int32_t* __restrict__ chunk_img,
-          const int32_t* __restrict__ chunk_c0, unsigned char* __restrict__ tiles, float* __restrict__ norms) {
+          const int32_t* __restrict__ chunk_c0, unsigned char* __restrict__ tiles) {
     const int c = blockIdx.x, r = threadIdx.x;
     const int img = chunk_img[c];
     const int64_t o = img_off[img];
@@ -130,22 +143,63 @@ k_nn_tile(const uint8_t* __restrict__ desc, const int64_t* __restrict__ img_off,
     const bool have = row < n;
     uint4 v[8];
     stage::load_row(desc + (size_t)(o + (have ? row : 0)) * kDim, have, v);
-    const uint32_t nn = stage::store_row(v, tiles + (size_t)c * kNnB, r, kNnChunk);
-    norms[(size_t)c * kNnChunk + r] = have ? (float)nn : __uint_as_float(0x7F800000u);
+    unsigned char* tile = tiles + (size_t)c * kNnB;
+    uint32_t nn = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        nn = __dp4a(v[k].x, v[k].x, nn);
+        nn = __dp4a(v[k].y, v[k].y, nn);
+        nn = __dp4a(v[k].z, v[k].z, nn);
+        nn = __dp4a(v[k].w, v[k].w, nn);
+        uint4 lo, hi;
+        lo.x = u8x2_to_bf16x2_m2(v[k].x, 0); lo.y = u8x2_to_bf16x2_m2(v[k].x, 2);
+        lo.z = u8x2_to_bf16x2_m2(v[k].y, 0); lo.w = u8x2_to_bf16x2_m2(v[k].y, 2);
+        hi.x = u8x2_to_bf16x2_m2(v[k].z, 0); hi.y = u8x2_to_bf16x2_m2(v[k].z, 2);
+        hi.z = u8x2_to_bf16x2_m2(v[k].w, 0); hi.w = u8x2_to_bf16x2_m2(v[k].w, 2);
+        *reinterpret_cast<uint4*>(tile + tc::chunk_off(r, 2 * k, kNnChunk)) = lo;
+        *reinterpret_cast<uint4*>(tile + tc::chunk_off(r, 2 * k + 1, kNnChunk)) = hi;
+    }
+    // |y|^2 <= 128 * 255^2 < 2^23: digits (|y|^2 >> 16, (|y|^2 >> 8) & 255, |y|^2 & 255)
+    const uint32_t d0 = have ? nn >> 16 : 255u, d1 = have ? (nn >> 8) & 255u : 0u, d2 = have ? nn & 255u : 0u;
+    uint4 dg;
+    dg.x = bf16_hi((float)d0) | (bf16_hi((float)d1) << 16);
+    dg.y = bf16_hi((float)d2);
+    dg.z = 0;
+    dg.w = 0;
+    *reinterpret_cast<uint4*>(tile + tc::chunk_off(r, 16, kNnChunk)) = dg;
+    *reinterpret_cast<uint4*>(tile + tc::chunk_off(r, 17, kNnChunk)) = make_uint4(0, 0, 0, 0);
+}
+
+// The 9 MMAs (K = 16 each) of one chunk: the |y|^2 block first (overwriting
+// the accumulator), then the 8 descriptor blocks.
+__device__ __forceinline__ void mma_chunk(uint32_t tmem_d, const unsigned char* A, const unsigned char* B) {
+    constexpr uint32_t lbo_a = (kNnRows / 8) * 128, lbo_b = (kNnChunk / 8) * 128;
+    const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B);
+    constexpr uint32_t idesc = tc::idesc_f16(kNnRows, kNnChunk, 1);
+    tc::mma_f16(tmem_d, tc::smem_desc(a0 + 16 * lbo_a, lbo_a, 128), tc::smem_desc(b0 + 16 * lbo_b, lbo_b, 128), idesc, 0);
+#pragma unroll
+    for (int ks = 0; ks < kDim / 16; ++ks)
+        tc::mma_f16(tmem_d, tc::smem_desc(a0 + ks * 2 * lbo_a, lbo_a, 128), tc::smem_desc(b0 + ks * 2 * lbo_b, lbo_b, 128),
+                    idesc, 1);
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
 }
 
 __global__ void __launch_bounds__(kNnPipeThreads, 1)
 k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ img_off, const NnPair* __restrict__ pairs,
                 int n_pairs, int n_items, int ratio_num, int ratio_den, const unsigned char* __restrict__ tiles,
-                const float* __restrict__ norms, const int64_t* __restrict__ tile_of, int32_t* __restrict__ best_j,
-                uint32_t* __restrict__ d1sq, uint32_t* __restrict__ d2sq, int* err) {
+                const int64_t* __restrict__ tile_of, int32_t* __restrict__ best_j, uint32_t* __restrict__ d1sq,
+                uint32_t* __restrict__ d2sq, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* At = smem;                                   // 128 x 256 B
-    unsigned char* Bt = At + kNnA;                              // 2 x 256 x 256 B
-    float* nbr = reinterpret_cast<float*>(Bt + 2 * kNnB);       // [4][256] chunk norms (+inf past the image)
-    uint64_t* bar = reinterpret_cast<uint64_t*>(nbr + 4 * kNnChunk);
+    unsigned char* At = smem;                                   // 128 rows x K
+    unsigned char* Bt = At + kNnA;                              // 2 x 256 rows x K
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Bt + 2 * kNnB);
     uint64_t *fullB = bar, *emptyB = bar + 2, *accFull = bar + 4, *accEmpty = bar + 6, *fullA = bar + 8,
-             *emptyA = bar + 9, *nbFull = bar + 10;
+             *emptyA = bar + 9;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ float s_part_e1[kNnSplit - 1][kNnRows], s_part_e2[kNnSplit - 1][kNnRows];   // partial results
@@ -161,7 +215,6 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
         }
         tc::mbar_init(fullA, kNnProd);
         tc::mbar_init(emptyA, 1);
-        for (int k = 0; k < 4; ++k) tc::mbar_init(&nbFull[k], 1);
         s_abort = 0;
     }
     if (warp == kNnMmaWarp) tc::tmem_alloc(&s_tmem, 2 * kNnChunk);
@@ -177,6 +230,11 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
 
     if (warp < 4) {
         // ---------------- producers
+        {   // A's |y|^2 block, the same for every item: (2^16, 2^8, 1, 0, ..)
+            const uint4 w = make_uint4(bf16_hi(65536.f) | (bf16_hi(256.f) << 16), bf16_hi(1.f), 0, 0);
+            *reinterpret_cast<uint4*>(At + tc::chunk_off(tid, 16, kNnRows)) = w;
+            *reinterpret_cast<uint4*>(At + tc::chunk_off(tid, 17, kNnRows)) = make_uint4(0, 0, 0, 0);
+        }
         uint32_t g = 0, it = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++it) {
@@ -196,8 +254,6 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
                     const int64_t c = tb + c0 / kNnChunk;
                     tc::mbar_arrive_expect_tx(&fullB[s], kNnB);
                     tc::bulk_g2s(Bt + s * kNnB, tiles + (size_t)c * kNnB, kNnB, &fullB[s]);
-                    tc::mbar_arrive_expect_tx(&nbFull[g & 3u], kNnChunk * 4);
-                    tc::bulk_g2s(nbr + (g & 3u) * kNnChunk, norms + (size_t)c * kNnChunk, kNnChunk * 4, &nbFull[g & 3u]);
                 }
             }
         }
@@ -218,7 +274,7 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
                         break;
                     }
                     tc::fence_after();
-                    stage::mma_128xN(tmem + s * kNnChunk, At, Bt + s * kNnB, kNnChunk);   // whole tiles
+                    mma_chunk(tmem + s * kNnChunk, At, Bt + s * kNnB);   // whole tiles
                     tc::commit(&emptyB[s]);
                     tc::commit(&accFull[s]);
                     last = g;
@@ -248,26 +304,23 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
             int j1 = -1;
             for (int c0 = 0; c0 < t.nj; c0 += kNnChunk, ++g) {
                 const uint32_t s = g & 1u, ph = (g >> 1) & 1u;
-                const float* nb = nbr + (g & 3u) * kNnChunk;
                 bool got = true;
-                if (lane == 0)
-                    got = nn_wait(&nbFull[g & 3u], (g >> 2) & 1u, abort_flag) && nn_wait(&accFull[s], ph, abort_flag);
+                if (lane == 0) got = nn_wait(&accFull[s], ph, abort_flag);
                 if (!__shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0)) { ok = false; break; }
                 tc::fence_after();
-                // t = |y|^2 - 2 x.y, exact (|t| < 2^24); d^2 = |x|^2 + t is added at the end.
-                // A group of 16 columns with no t below q2's is skipped whole: it
-                // cannot change q1 or q2.  Columns past the image have norm +inf.
+                // the accumulator holds t = |y|^2 - 2 x.y (exact); d^2 = |x|^2 + t is
+                // added at the end.  A group of 16 columns with no t below q2's is
+                // skipped whole: it cannot change q1 or q2.
+#pragma unroll
                 for (int cc = part * H; cc < part * H + H; cc += 16) {
                     uint32_t acc[16];
                     tc::tmem_ld16(lane_base + s * kNnChunk + cc, acc);
                     tc::tmem_wait_ld();
                     float tv[16];
-                    float m = kInf;
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        tv[u] = fmaf(-2.f, __uint_as_float(acc[u]), nb[cc + u]);
-                        m = fminf(m, tv[u]);
-                    }
+                    for (int u = 0; u < 16; ++u) tv[u] = __uint_as_float(acc[u]);
+                    const float m = fminf(min3f(min3f(tv[0], tv[1], tv[2]), min3f(tv[3], tv[4], tv[5]), min3f(tv[6], tv[7], tv[8])),
+                                          min3f(min3f(tv[9], tv[10], tv[11]), min3f(tv[12], tv[13], tv[14]), tv[15]));
                     if (__any_sync(0xFFFFFFFFu, m < e2)) {
                         const int jb = c0 + cc;
 #pragma unroll
@@ -321,9 +374,9 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
 
 // Workspace: error flag (fixed place), image offsets, pair records, the tile
 // index of each image (-1: not a database image here), the chunk table, the
-// database images' BF16 tiles (64 KB per 256 rows) and their norms.
+// database images' BF16 tiles (72 KB per 256 rows).
 struct NnWork {
-    uint64_t err, off, pairs, tile_of, chunk_img, chunk_c0, tiles, norms, total;
+    uint64_t err, off, pairs, tile_of, chunk_img, chunk_c0, tiles, total;
 };
 
 NnWork nn_layout(int32_t n_images, int64_t n_pairs, int64_t n_chunks) {
@@ -335,8 +388,7 @@ NnWork nn_layout(int32_t n_images, int64_t n_pairs, int64_t n_chunks) {
     w.chunk_img = align_up(w.tile_of + 8 * (uint64_t)std::max(n_images, 1));
     w.chunk_c0 = align_up(w.chunk_img + 4 * (uint64_t)n_chunks);
     w.tiles = align_up(w.chunk_c0 + 4 * (uint64_t)n_chunks);
-    w.norms = align_up(w.tiles + (uint64_t)kNnB * (uint64_t)n_chunks);
-    w.total = align_up(w.norms + 4 * (uint64_t)kNnChunk * (uint64_t)n_chunks);
+    w.total = align_up(w.tiles + (uint64_t)kNnB * (uint64_t)n_chunks);
     return w;
 }
 
@@ -431,21 +483,21 @@ extern "C" cm_status cm_nn_pairs(const uint8_t* desc, const int64_t* img_off, in
         k_nn_tile<<<(unsigned)n_chunks, kNnChunk, 0, s>>>(desc, reinterpret_cast<const int64_t*>(base + w.off),
                                                           reinterpret_cast<const int32_t*>(base + w.chunk_img),
                                                           reinterpret_cast<const int32_t*>(base + w.chunk_c0),
-                                                          base + w.tiles, reinterpret_cast<float*>(base + w.norms));
+                                                          base + w.tiles);
         CM_CUDA(cudaGetLastError());
     }
     int dev = 0, sms = 148;
     CM_CUDA(cudaGetDevice(&dev));
     CM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // one CTA per SM: A, two B buffers and the norm ring in shared memory, two
-    // 256-column accumulators (all of TMEM)
-    const size_t smem = (size_t)kNnA + 2 * (size_t)kNnB + 4 * kNnChunk * 4 + 16 * 8 + 1024;
+    // one CTA per SM: A and two B buffers in shared memory, two 256-column
+    // accumulators (all of TMEM)
+    const size_t smem = (size_t)kNnA + 2 * (size_t)kNnB + 16 * 8 + 1024;
     CM_CUDA(cudaFuncSetAttribute(k_nn_exhaustive, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<int64_t>(items, (int64_t)sms);
     k_nn_exhaustive<<<grid, kNnPipeThreads, smem, s>>>(
         desc, reinterpret_cast<const int64_t*>(base + w.off), reinterpret_cast<const NnPair*>(base + w.pairs),
-        (int)n_pairs, (int)items, ratio_num, ratio_den, base + w.tiles, reinterpret_cast<const float*>(base + w.norms),
-        reinterpret_cast<const int64_t*>(base + w.tile_of), best_j, d1sq, d2sq, err);
+        (int)n_pairs, (int)items, ratio_num, ratio_den, base + w.tiles, reinterpret_cast<const int64_t*>(base + w.tile_of),
+        best_j, d1sq, d2sq, err);
     CM_CUDA(cudaGetLastError());
     return CM_OK;
 }

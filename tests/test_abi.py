@@ -123,7 +123,7 @@ def test_host_argument_checks_of_the_later_entry_points():
     off3 = np.array([0, 300, 700, 700], dtype=np.int64)
     pr3 = np.array([[0, 1], [1, 0], [2, 0]], dtype=np.int32)   # database images 1 (400 rows) and 0 (300 rows)
     assert lib.cm_nn_workspace_bytes(off3.ctypes.data, 3, pr3.ctypes.data, 3, cm.ctypes.byref(b)) == cm.CM_OK
-    assert b.value % 256 == 0 and b.value >= 4 * (65536 + 1024)   # two 256-row tiles per database image
+    assert b.value % 256 == 0 and b.value >= 4 * 256 * 144 * 2   # two 256-row tiles (K = 144) per database image
     assert lib.cm_nn_workspace_bytes(off3.ctypes.data, 3, pr3.ctypes.data, -1, cm.ctypes.byref(b)) == cm.CM_ERR_INVALID
     bad = np.array([[0, 5]], dtype=np.int32)
     assert lib.cm_nn_workspace_bytes(off3.ctypes.data, 3, bad.ctypes.data, 1, cm.ctypes.byref(b)) == cm.CM_ERR_INVALID

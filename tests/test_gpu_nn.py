@@ -2,8 +2,8 @@
 quality ceiling of Sec. 2.3.1 with every database point a candidate) with the
 oracle's brute force: q1, q2 and their squared distances bit for bit and the
 exact ratio test, over pairs with empty, one-row and two-row database images,
-ragged tiles and chunks, duplicated database rows (ties to the smaller j) and
-two ratio thresholds."""
+ragged tiles and chunks, duplicated database rows (ties to the smaller j),
+rows at the largest squared norms and two ratio thresholds."""
 import numpy as np
 import pytest
 
@@ -50,6 +50,24 @@ def test_duplicated_database_rows_tie_to_the_smaller_index():
     desc[:100] = desc[200:300]                                # exact copies: d1 = d2 = 0, no match
     best = _check(desc, nd, [(0, 1)])
     assert (best[:100] == -1).all()
+
+
+def test_extreme_magnitudes_stay_exact():
+    # rows near the largest squared norm (128 * 255^2 < 2^23), all-255 and
+    # all-zero rows: d^2 and the ratio test must still be exact
+    rng = np.random.default_rng(3)
+    nd = np.array([300, 400, 257], dtype=np.int64)
+    desc = rng.integers(240, 256, (957, 128)).astype(np.uint8)
+    desc[[0, 300, 700]] = 255
+    desc[[1, 301, 956]] = 0
+    desc[2, :64] = 255
+    desc[2, 64:] = 0
+    desc[302, 64:] = 255
+    desc[302, :64] = 0
+    desc[303] = 254
+    desc[350:360] = np.clip(desc[10:20].astype(int) + 1, 0, 255)
+    _check(desc, nd, [(0, 1), (1, 0), (2, 0), (1, 2)])
+    _check(desc, nd, [(0, 1)], ratio=(1, 2))
 
 
 def test_a_synthetic_pair_and_a_strip():
