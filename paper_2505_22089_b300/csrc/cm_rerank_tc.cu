@@ -12,12 +12,14 @@
 // The kernel is persistent and warp-specialised, work items dealt round-robin:
 //   warps 0-7    producers: 16-byte cp.async copies of the A and B rows from the
 //                row copies into a ring of shared-memory stages, in the
-//                128-byte-swizzled K-major operand layout; a stage is handed to
-//                the MMA once its copies landed (wait_group, proxy fence,
-//                mbarrier arrive), several stages in flight per thread;
-//   warp 8       MMA issuer: one thread, tcgen05.mma into one of ACC TMEM
-//                accumulators, commits that free the stage and fill the
-//                accumulator;
+//                128-byte-swizzled K-major operand layout; each thread's copies
+//                arrive on the stage's mbarrier as they land
+//                (cp.async.mbarrier.arrive.noinc), so every stage of the ring
+//                can be in flight and no thread waits for its own copies;
+//   warp 8       MMA issuer: one thread, a proxy fence after each stage's
+//                wait (generic-proxy copies before async-proxy reads),
+//                tcgen05.mma into one of ACC TMEM accumulators, commits that
+//                free the stage and fill the accumulator;
 //   warps 9-16   two epilogue groups of 4 warps (each the 128 TMEM lanes),
 //                taking the sub-tiles in turn: d^2 = |x|^2 + |y|^2 - 2 x.y,
 //                q1 / q2 by (d^2, index) across the K lanes of a query, the
@@ -60,7 +62,6 @@ struct RR {
     static constexpr uint32_t STAGE = HALVES * (A_HALF + B_HALF);
     static constexpr int STAGES_FIT = (int)((216u * 1024u) / STAGE);
     static constexpr int STAGES = STAGES_FIT < 8 ? STAGES_FIT : 8;
-    static constexpr int DEPTH = STAGES - 1;              // cp.async groups in flight per producer thread
     static constexpr int ACC_FIT = 256 / NB;
     static constexpr int ACC = ACC_FIT < 8 ? ACC_FIT : 8;  // a multiple of the epilogue groups, which take turns
     static constexpr int STEPS = FP8 ? 4 : 8;              // MMAs of 32 bytes of K each
@@ -230,8 +231,8 @@ __global__ void __launch_bounds__(kRrThreads, 1) k_rerank_tc(MatchLaunch ml) {
                 jr[q] = (r < 128 && r / K < t.nq) ? (uint32_t)ml.topk16[t.row * K + r] : (uint32_t)kNoCand;
             }
         };
-        // copies sub-tile t into stage it % STAGES; after DEPTH - 1 later groups have been
-        // issued a group has landed: proxy fence, then its stage goes to the MMA
+        // copies sub-tile t into stage it % STAGES; the stage goes to the MMA once every
+        // producer thread's copies into it have landed
         auto issue = [&](const SubTile& t, const uint32_t (&jr)[C::PER_THREAD]) -> bool {
             const int s = it % C::STAGES;
             const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
@@ -255,12 +256,9 @@ __global__ void __launch_bounds__(kRrThreads, 1) k_rerank_tc(MatchLaunch ml) {
                                  : "memory");
                 }
             }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            if (it >= C::DEPTH - 1) {
-                asm volatile("cp.async.wait_group %0;" :: "n"(C::DEPTH - 1) : "memory");
-                tc::fence_proxy_async();
-                tc::mbar_arrive(&full[(it - (C::DEPTH - 1)) % C::STAGES]);
-            }
+            // this thread's arrival on the stage, made when all its copies so far have landed
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" :: "r"(tc::smem_addr(&full[s]))
+                         : "memory");
             ++it;
             return true;
         };
@@ -280,9 +278,7 @@ __global__ void __launch_bounds__(kRrThreads, 1) k_rerank_tc(MatchLaunch ml) {
             if (!issue(tB, jB)) { ok = false; break; }
         }
         if (!ok) give_up();
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        tc::fence_proxy_async();
-        for (int k2 = it - (C::DEPTH - 1) < 0 ? 0 : it - (C::DEPTH - 1); k2 < it; ++k2) tc::mbar_arrive(&full[k2 % C::STAGES]);
+        asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer
         if (lane == 0) {
@@ -296,6 +292,7 @@ __global__ void __launch_bounds__(kRrThreads, 1) k_rerank_tc(MatchLaunch ml) {
                 const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u, aph = (uint32_t)(it / C::ACC) & 1u;
                 if (!wait_or_abort(&full[s], ph, abort_flag)) { give_up(); break; }
                 if (!wait_or_abort(&tempty[a], aph ^ 1u, abort_flag)) { give_up(); break; }
+                tc::fence_proxy_async();   // the producers' copies (generic proxy) before the MMA's reads
                 tc::fence_after();
                 const uint32_t a0 = tc::smem_addr(ring + (size_t)s * C::STAGE);
                 const uint32_t b0 = a0 + C::HALVES * C::A_HALF;
