@@ -49,7 +49,7 @@ constexpr int kMmaWarp = kProdWarps;              // the MMA warp
 constexpr int kEpiGroups = 2;                     // epilogue groups of 4 warps
 constexpr int kEpiWarp0 = kProdWarps + 1;
 constexpr int kRrThreads = (kProdWarps + 1 + 4 * kEpiGroups) * 32;
-constexpr int kRrPolls = 1 << 24;
+constexpr int kRrSleeps = 1 << 20;
 constexpr uint16_t kNoCand = 0xFFFFu;
 
 template <int K, bool FP8>
@@ -133,10 +133,11 @@ struct Cursor {
     }
 };
 
-// Bounded wait for an mbarrier phase that also gives up once another role aborted.
+// Bounded wait for an mbarrier phase that also gives up once another role
+// aborted: sleeping try_waits of at most 2 us each, about 2 s in all.
 __device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, volatile int* abort_flag) {
-    for (int it = 0; it < kRrPolls; it += 32) {
-        if (tc::mbar_wait(mbar, parity, 32)) return true;
+    for (int it = 0; it < kRrSleeps; ++it) {
+        if (tc::mbar_try_wait_sleep(mbar, parity, 2000)) return true;
         if (*abort_flag) return false;
     }
     return false;

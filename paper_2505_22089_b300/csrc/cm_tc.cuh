@@ -88,6 +88,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int l
     return done != 0;
 }
 
+// One try_wait that may suspend the thread for up to hint_ns nanoseconds while
+// the phase is incomplete; it resumes once the phase completes.  A waiting
+// thread that sleeps issues no instructions, so the warps it shares an SM
+// sub-partition with keep the issue slots.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* mbar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(smem_addr(mbar)), "r"(parity), "r"(hint_ns) : "memory");
+    return done != 0;
+}
+
 // Arrival of the issuing thread that also announces `bytes` of bulk copies
 // to complete on this barrier (a barrier of count 1 per phase).
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
