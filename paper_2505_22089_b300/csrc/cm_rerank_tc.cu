@@ -320,7 +320,9 @@ __global__ void __launch_bounds__(kRrThreads, 1) k_rerank_tc(MatchLaunch ml) {
         const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31
         const int r = 32 * quarter + lane;          // candidate row of the A tile
         const int c = r / K, k = r % K;             // its query column and slot
-        const int chunk = (32 * quarter / K) / 16;  // 16-column chunk holding this warp's columns
+        constexpr int W = 32 / K;                   // columns of this warp's 32 rows (W >= 2)
+        static_assert(W == 2 || W == 4 || W == 8 || W == 16, "TMEM load width");
+        const int col0 = 32 * quarter / K;          // the first of them
         uint32_t rechecks = 0, matches = 0, swaps = 0;
         // inputs of one sub-tile for this thread: all contiguous (hand-over written by the scan)
         struct In {
@@ -366,13 +368,17 @@ __global__ void __launch_bounds__(kRrThreads, 1) k_rerank_tc(MatchLaunch ml) {
             const int j = hv ? (int)v.j : 0;
             if (!warp_wait(&tfull[a], aph, abort_flag)) return false;
             tc::fence_after();
-            uint32_t vv[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(a * C::NB + 16 * chunk), vv);
+            uint32_t vv[W];
+            tc::tmem_ld_cols<W>(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(a * C::NB + col0), vv);
             tc::tmem_wait_ld();
-            float dot = 0.f;
+            // column c = col0 + lane / K, picked by a binary tree of selects on the
+            // bits of lane / K (the values stay in registers)
+            const int sel = lane / K;
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
-                if (q == (c & 15)) dot = __uint_as_float(vv[q]);
+            for (int w = W / 2, bit = 1; w >= 1; w /= 2, bit *= 2)
+#pragma unroll
+                for (int q = 0; q < w; ++q) vv[q] = (sel & bit) ? vv[2 * q + 1] : vv[2 * q];
+            const float dot = __uint_as_float(vv[0]);
             tc::fence_before();
             tc::mbar_arrive(&tempty[a]);   // this thread's lane of the accumulator is read
 
