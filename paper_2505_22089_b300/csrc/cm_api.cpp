@@ -613,6 +613,7 @@ extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, in
         d.row_off = rows;
         d.item0 = (int32_t)items;
         d.nitems = (ix->n_desc[i] + S - 1) / S;
+        d.ni = ix->n_desc[i];
         rows += ix->n_desc[i];
         items += d.nitems;
         max_ni = std::max(max_ni, ix->n_desc[i]);
@@ -624,7 +625,6 @@ extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, in
         for (int64_t k = 0; k < n_pairs; ++k) {
             auto it = first.find(std::make_pair(tab[k].j, tab[k].i));
             tab[k].rev = it == first.end() ? -1 : (int32_t)it->second;
-            tab[k].pad = 0;
         }
     }
     cm_match_plan* pl = new (std::nothrow) cm_match_plan();

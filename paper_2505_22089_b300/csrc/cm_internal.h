@@ -45,7 +45,7 @@ struct DevPair {
     int32_t item0;         // first work item of this pair
     int32_t nitems;        // work items (query tiles) of this pair
     int32_t rev;           // index of the pair (j, i) in the same plan, -1 if absent
-    int32_t pad;
+    int32_t ni;            // rows of image i (the pair's queries)
 };
 
 struct HashLaunch {

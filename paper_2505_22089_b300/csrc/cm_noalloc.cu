@@ -138,6 +138,7 @@ extern "C" cm_status cm_match_pair_noalloc(const cm_params* p, const uint8_t* d_
     pair.row_off = 0;
     pair.item0 = 0;
     pair.nitems = (n_i + S - 1) / S;
+    pair.ni = n_i;
     pair.rev = -1;
 
     cudaError_t e = cudaSuccess;

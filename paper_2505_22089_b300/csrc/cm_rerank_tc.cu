@@ -92,7 +92,11 @@ struct SubTile {
 };
 
 // Walks a CTA's increasing sequence of sub-tiles; the current pair's record is
-// kept in registers and reloaded only when the sequence crosses into a later pair.
+// kept in registers and replaced only when the sequence crosses into a later
+// pair.  The next pair's record is loaded at the previous crossing, so a
+// crossing waits at most for the image records (IMG) and not for a chain of
+// dependent loads; the MMA issuer needs no image record at all.
+template <bool IMG>
 struct Cursor {
     int pair = -1, item0 = 0, item_end = 0, n_i = 0;
     int64_t row_off = 0;
@@ -100,24 +104,28 @@ struct Cursor {
     const uint32_t* inorm = nullptr;
     const float* iscale = nullptr;
     const uint8_t *idesc = nullptr, *jdesc = nullptr;
+    DevPair nxt{};   // record of pair + 1
 
     __device__ __forceinline__ SubTile at(const MatchLaunch& ml, int u, int per_item, int qs) {
         const int item = u / per_item;
         while (item >= item_end && pair + 1 < ml.n_pairs) {
             ++pair;
-            const DevPair P = ml.pairs[pair];
+            const DevPair P = pair == 0 ? ml.pairs[0] : nxt;
+            if (pair + 1 < ml.n_pairs) nxt = ml.pairs[pair + 1];   // used at the next crossing
             item0 = P.item0;
             item_end = P.item0 + P.nitems;
             row_off = P.row_off;
-            const DevImage& I = ml.imgs[P.i];
-            const DevImage& J = ml.imgs[P.j];
-            n_i = I.n;
-            ixq = static_cast<const unsigned char*>(I.xq);
-            jxq = static_cast<const unsigned char*>(J.xq);
-            inorm = I.norm;
-            iscale = I.xscale;
-            idesc = I.desc;
-            jdesc = J.desc;
+            n_i = P.ni;
+            if (IMG) {
+                const DevImage& I = ml.imgs[P.i];
+                const DevImage& J = ml.imgs[P.j];
+                ixq = static_cast<const unsigned char*>(I.xq);
+                jxq = static_cast<const unsigned char*>(J.xq);
+                inorm = I.norm;
+                iscale = I.xscale;
+                idesc = I.desc;
+                jdesc = J.desc;
+            }
         }
         SubTile t;
         t.q0 = (item - item0) * ml.S + (u % per_item) * qs;
@@ -212,7 +220,7 @@ __global__ void __launch_bounds__(kRrThreads, 1) k_rerank_tc(MatchLaunch ml) {
         // (chunk e: staged row e / CPR, 16-byte chunk e % CPR; rows 0-127 = A, then B)
         const int rb = FP8 ? 128 : 256;   // bytes per row copy
         int it = 0;          // sub-tiles issued
-        Cursor cursor;
+        Cursor<true> cursor;
         bool ok = true;
         int u = blockIdx.x - (int)gridDim.x;
         // advances to the next non-empty sub-tile of this CTA's sequence
@@ -285,7 +293,7 @@ __global__ void __launch_bounds__(kRrThreads, 1) k_rerank_tc(MatchLaunch ml) {
         if (lane == 0) {
             const uint32_t idesc = FP8 ? tc::idesc_e4m3(128, C::NB) : tc::idesc_f16(128, C::NB, 1);
             int it = 0;
-        Cursor cursor;
+            Cursor<false> cursor;
             for (int u = blockIdx.x; u < n_sub; u += gridDim.x) {
                 const SubTile t = cursor.at(ml, u, per_item, C::QS);
                 if (t.nq <= 0) continue;
@@ -344,7 +352,7 @@ __global__ void __launch_bounds__(kRrThreads, 1) k_rerank_tc(MatchLaunch ml) {
             return v;
         };
         int it = 0;          // position in the CTA's sequence of non-empty sub-tiles
-        Cursor cursor;
+        Cursor<true> cursor;
         int u = blockIdx.x - (int)gridDim.x;
         // advances to this group's next sub-tile (every kEpiGroups-th of the sequence)
         auto next = [&](SubTile& t, int& myit) -> bool {
