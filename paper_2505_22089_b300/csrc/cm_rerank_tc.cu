@@ -9,19 +9,21 @@
 // candidate rows each (M = 128), its B operand their QS query rows (N = NB >= 16,
 // padded).  One MMA chain (K = 128) gives every candidate's dot product with
 // every query of the sub-tile, of which candidate row r needs column r / K.
-// The kernel is persistent and warp-specialised, work items dealt round-robin:
-//   warps 0-7    producers: 16-byte cp.async copies of the A and B rows from the
+// The kernel is persistent and warp-specialised, two CTAs per SM (two MMA
+// issuers: one issuing thread's 8 MMAs per sub-tile bounded a CTA), work items
+// dealt round-robin:
+//   warps 0-3    producers: 16-byte cp.async copies of the A and B rows from the
 //                row copies into a ring of shared-memory stages, in the
 //                128-byte-swizzled K-major operand layout; each thread's copies
 //                arrive on the stage's mbarrier as they land
 //                (cp.async.mbarrier.arrive.noinc), so every stage of the ring
 //                can be in flight and no thread waits for its own copies;
-//   warp 8       MMA issuer: one thread, a proxy fence after each stage's
+//   warp 4       MMA issuer: one thread, a proxy fence after each stage's
 //                wait (generic-proxy copies before async-proxy reads),
 //                tcgen05.mma into one of ACC TMEM accumulators, commits that
 //                free the stage and fill the accumulator;
-//   warps 9-16   two epilogue groups of 4 warps (each the 128 TMEM lanes),
-//                taking the sub-tiles in turn: d^2 = |x|^2 + |y|^2 - 2 x.y,
+//   warps 5-8    the epilogue group of 4 warps (the 128 TMEM lanes):
+//                d^2 = |x|^2 + |y|^2 - 2 x.y,
 //                q1 / q2 by (d^2, index) across the K lanes of a query, the
 //                exact ratio test, outputs.
 //   BF16: the dot is an exact integer in FP32, so d^2 is exact.
@@ -43,10 +45,11 @@ namespace cm {
 
 namespace {
 
-constexpr int kProdWarps = 8;
+constexpr int kRrCtasPerSm = 2;
+constexpr int kProdWarps = 4;
 constexpr int kProd = kProdWarps * 32;            // producer threads
 constexpr int kMmaWarp = kProdWarps;              // the MMA warp
-constexpr int kEpiGroups = 2;                     // epilogue groups of 4 warps
+constexpr int kEpiGroups = 1;                     // epilogue groups of 4 warps (taking sub-tiles in turn)
 constexpr int kEpiWarp0 = kProdWarps + 1;
 constexpr int kRrThreads = (kProdWarps + 1 + 4 * kEpiGroups) * 32;
 constexpr int kRrSleeps = 1 << 20;
@@ -60,7 +63,7 @@ struct RR {
     static constexpr uint32_t A_HALF = 128u * 128u;       // 128 rows x 128 bytes
     static constexpr uint32_t B_HALF = (uint32_t)NB * 128u;
     static constexpr uint32_t STAGE = HALVES * (A_HALF + B_HALF);
-    static constexpr int STAGES_FIT = (int)((216u * 1024u) / STAGE);
+    static constexpr int STAGES_FIT = (int)((216u * 1024u / kRrCtasPerSm) / STAGE);
     static constexpr int STAGES = STAGES_FIT < 8 ? STAGES_FIT : 8;
     static constexpr int ACC_FIT = 256 / NB;
     static constexpr int ACC = ACC_FIT < 8 ? ACC_FIT : 8;  // a multiple of the epilogue groups, which take turns
@@ -73,6 +76,7 @@ struct RR {
     static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 8 * (2 * STAGES + 2 * ACC) + 64;
     static_assert(ACC % kEpiGroups == 0, "accumulators are dealt to the epilogue groups in turn");
     static_assert(STAGES >= 2, "stage ring");
+    static_assert(256 * kRrCtasPerSm <= 512, "each CTA allocates 256 TMEM columns");
     static_assert(B_HALF % 1024 == 0, "B tile keeps 1024-byte alignment");
 };
 
@@ -174,7 +178,7 @@ __device__ __forceinline__ uint32_t exact_d2(const uint8_t* x, const uint8_t* y,
 }
 
 template <int K, bool FP8>
-__global__ void __launch_bounds__(kRrThreads, 1) k_rerank_tc(MatchLaunch ml) {
+__global__ void __launch_bounds__(kRrThreads, kRrCtasPerSm) k_rerank_tc(MatchLaunch ml) {
     using C = RR<K, FP8>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -378,7 +382,7 @@ __global__ void __launch_bounds__(kRrThreads, 1) k_rerank_tc(MatchLaunch ml) {
             tc::fence_after();
             uint32_t vv[W];
             tc::tmem_ld_cols<W>(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(a * C::NB + col0), vv);
-            tc::tmem_wait_ld();
+            tc::tmem_wait_ld(vv);
             // column c = col0 + lane / K, picked by a binary tree of selects on the
             // bits of lane / K (the values stay in registers)
             const int sel = lane / K;
@@ -550,7 +554,8 @@ cudaError_t launch_rr(const MatchLaunch& m, int sms, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_rerank_tc<K, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
     const int n_sub = m.n_items * (m.S / C::QS);
-    const int grid = n_sub < sms ? (n_sub ? n_sub : 1) : sms;
+    const int slots = kRrCtasPerSm * sms;
+    const int grid = n_sub < slots ? (n_sub ? n_sub : 1) : slots;
     k_rerank_tc<K, FP8><<<grid, kRrThreads, C::SMEM, s>>>(m);
     return cudaGetLastError();
 }

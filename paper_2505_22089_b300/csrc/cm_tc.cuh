@@ -161,7 +161,16 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&v)[W]) {
     else tmem_ld16(taddr, v);
 }
 
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;"); }
+// tcgen05.wait::ld for the registers v of the loads before it.  The loaded
+// registers are valid only after the wait, but the compiler sees them defined
+// by the load; tying each one to an empty volatile statement after the wait
+// keeps every use of them below the wait.
+template <int W>
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[W]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < W; ++i) asm volatile("" : "+r"(v[i]));
+}
 
 }  // namespace tc
 }  // namespace cm
