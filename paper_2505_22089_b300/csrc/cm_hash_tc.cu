@@ -156,8 +156,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_hash_tc(HashLaunch h) {
 #pragma unroll
         for (int c = 0; c < NP / 16; ++c) {
             uint32_t v[16];
-            tc::tmem_ld16(lane_base + 16 * c, v);
-            tc::tmem_wait_ld(v);
+            tc::tmem_load16(lane_base + 16 * c, v);
             uint32_t bits = 0;
 #pragma unroll
             for (int j = 0; j < 16; ++j) bits |= (uint32_t)(__uint_as_float(v[j]) - bias[16 * c + j] > 0.f) << j;

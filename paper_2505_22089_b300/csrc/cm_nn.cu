@@ -314,8 +314,7 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
 #pragma unroll
                 for (int cc = part * H; cc < part * H + H; cc += 16) {
                     uint32_t acc[16];
-                    tc::tmem_ld16(lane_base + s * kNnChunk + cc, acc);
-                    tc::tmem_wait_ld(acc);
+                    tc::tmem_load16(lane_base + s * kNnChunk + cc, acc);
                     float tv[16];
 #pragma unroll
                     for (int u = 0; u < 16; ++u) tv[u] = __uint_as_float(acc[u]);

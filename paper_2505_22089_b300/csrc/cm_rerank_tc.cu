@@ -9,21 +9,20 @@
 // candidate rows each (M = 128), its B operand their QS query rows (N = NB >= 16,
 // padded).  One MMA chain (K = 128) gives every candidate's dot product with
 // every query of the sub-tile, of which candidate row r needs column r / K.
-// The kernel is persistent and warp-specialised, two CTAs per SM (two MMA
-// issuers: one issuing thread's 8 MMAs per sub-tile bounded a CTA), work items
-// dealt round-robin:
-//   warps 0-3    producers: 16-byte cp.async copies of the A and B rows from the
+// The kernel is persistent and warp-specialised, work items dealt
+// round-robin (the launch shape per form is in RR below):
+//   producers    16-byte cp.async copies of the A and B rows from the
 //                row copies into a ring of shared-memory stages, in the
 //                128-byte-swizzled K-major operand layout; each thread's copies
 //                arrive on the stage's mbarrier as they land
 //                (cp.async.mbarrier.arrive.noinc), so every stage of the ring
 //                can be in flight and no thread waits for its own copies;
-//   warp 4       MMA issuer: one thread, a proxy fence after each stage's
-//                wait (generic-proxy copies before async-proxy reads),
+//   MMA issuer   one thread, a proxy fence after each stage's wait
+//                (generic-proxy copies before async-proxy reads),
 //                tcgen05.mma into one of ACC TMEM accumulators, commits that
 //                free the stage and fill the accumulator;
-//   warps 5-8    the epilogue group of 4 warps (the 128 TMEM lanes):
-//                d^2 = |x|^2 + |y|^2 - 2 x.y,
+//   epilogue     groups of 4 warps (each the 128 TMEM lanes), taking the
+//                sub-tiles in turn: d^2 = |x|^2 + |y|^2 - 2 x.y,
 //                q1 / q2 by (d^2, index) across the K lanes of a query, the
 //                exact ratio test, outputs.
 //   BF16: the dot is an exact integer in FP32, so d^2 is exact.
@@ -45,25 +44,30 @@ namespace cm {
 
 namespace {
 
-constexpr int kRrCtasPerSm = 2;
-constexpr int kProdWarps = 4;
-constexpr int kProd = kProdWarps * 32;            // producer threads
-constexpr int kMmaWarp = kProdWarps;              // the MMA warp
-constexpr int kEpiGroups = 1;                     // epilogue groups of 4 warps (taking sub-tiles in turn)
-constexpr int kEpiWarp0 = kProdWarps + 1;
-constexpr int kRrThreads = (kProdWarps + 1 + 4 * kEpiGroups) * 32;
 constexpr int kRrSleeps = 1 << 20;
 constexpr uint16_t kNoCand = 0xFFFFu;
 
 template <int K, bool FP8>
 struct RR {
+    // Launch shape.  BF16: two CTAs per SM (two MMA issuers; one issuing
+    // thread's 8 MMAs per sub-tile bounded a CTA), 4 producer warps and one
+    // epilogue group each.  FP8: its exact re-score makes the epilogue the
+    // busier role, which wants two epilogue groups; those do not fit the
+    // register file twice, so FP8 keeps one CTA per SM with 8 producer warps.
+    static constexpr int CTAS = FP8 ? 1 : 2;              // CTAs per SM
+    static constexpr int PROD_WARPS = FP8 ? 8 : 4;
+    static constexpr int PROD = PROD_WARPS * 32;          // producer threads
+    static constexpr int MMA_WARP = PROD_WARPS;
+    static constexpr int EPI_WARP0 = PROD_WARPS + 1;
+    static constexpr int EPI = FP8 ? 2 : 1;               // epilogue groups of 4 warps, taking sub-tiles in turn
+    static constexpr int THREADS = (PROD_WARPS + 1 + 4 * EPI) * 32;
     static constexpr int QS = 128 / K;                    // queries per sub-tile
     static constexpr int NB = QS < 16 ? 16 : QS;          // B rows = MMA N
     static constexpr int HALVES = FP8 ? 1 : 2;            // 128-byte column blocks per row
     static constexpr uint32_t A_HALF = 128u * 128u;       // 128 rows x 128 bytes
     static constexpr uint32_t B_HALF = (uint32_t)NB * 128u;
     static constexpr uint32_t STAGE = HALVES * (A_HALF + B_HALF);
-    static constexpr int STAGES_FIT = (int)((216u * 1024u / kRrCtasPerSm) / STAGE);
+    static constexpr int STAGES_FIT = (int)((216u * 1024u / CTAS) / STAGE);
     static constexpr int STAGES = STAGES_FIT < 8 ? STAGES_FIT : 8;
     static constexpr int ACC_FIT = 256 / NB;
     static constexpr int ACC = ACC_FIT < 8 ? ACC_FIT : 8;  // a multiple of the epilogue groups, which take turns
@@ -71,12 +75,12 @@ struct RR {
     static constexpr int CPR = FP8 ? 8 : 16;               // 16-byte chunks per row copy
     static constexpr int ROWS = 128 + NB;                   // staged rows per sub-tile
     static constexpr int CHUNKS = ROWS * CPR;
-    static constexpr int PER_THREAD = (CHUNKS + kProd - 1) / kProd;
+    static constexpr int PER_THREAD = (CHUNKS + PROD - 1) / PROD;
     // stages (1024-aligned) + barriers: full/empty per stage, full/empty per accumulator
     static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 8 * (2 * STAGES + 2 * ACC) + 64;
-    static_assert(ACC % kEpiGroups == 0, "accumulators are dealt to the epilogue groups in turn");
+    static_assert(ACC % EPI == 0, "accumulators are dealt to the epilogue groups in turn");
     static_assert(STAGES >= 2, "stage ring");
-    static_assert(256 * kRrCtasPerSm <= 512, "each CTA allocates 256 TMEM columns");
+    static_assert(256 * CTAS <= 512, "each CTA allocates 256 TMEM columns");
     static_assert(B_HALF % 1024 == 0, "B tile keeps 1024-byte alignment");
 };
 
@@ -178,7 +182,7 @@ __device__ __forceinline__ uint32_t exact_d2(const uint8_t* x, const uint8_t* y,
 }
 
 template <int K, bool FP8>
-__global__ void __launch_bounds__(kRrThreads, kRrCtasPerSm) k_rerank_tc(MatchLaunch ml) {
+__global__ void __launch_bounds__(RR<K, FP8>::THREADS, RR<K, FP8>::CTAS) k_rerank_tc(MatchLaunch ml) {
     using C = RR<K, FP8>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(kRrThreads, kRrCtasPerSm) k_rerank_tc(MatchLau
 
     if (tid == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
-            tc::mbar_init(&full[s], kProd);
+            tc::mbar_init(&full[s], C::PROD);
             tc::mbar_init(&empty[s], 1);
         }
         for (int a = 0; a < C::ACC; ++a) {
@@ -203,7 +207,7 @@ __global__ void __launch_bounds__(kRrThreads, kRrCtasPerSm) k_rerank_tc(MatchLau
         s_abort = 0;
         s_stats[0] = s_stats[1] = s_stats[2] = 0;
     }
-    if (warp == kMmaWarp) tc::tmem_alloc(&s_tmem, 256);
+    if (warp == C::MMA_WARP) tc::tmem_alloc(&s_tmem, 256);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -219,8 +223,8 @@ __global__ void __launch_bounds__(kRrThreads, kRrCtasPerSm) k_rerank_tc(MatchLau
     // Every role walks the same sequence of non-empty sub-tiles, so the local
     // counter `it` (stage it % STAGES, accumulator it % ACC) agrees across roles.
 
-    if (warp < kProdWarps) {
-        // ---------------- producers: thread t copies chunks t, t + kProd, ... of each sub-tile
+    if (warp < C::PROD_WARPS) {
+        // ---------------- producers: thread t copies chunks t, t + PROD, ... of each sub-tile
         // (chunk e: staged row e / CPR, 16-byte chunk e % CPR; rows 0-127 = A, then B)
         const int rb = FP8 ? 128 : 256;   // bytes per row copy
         int it = 0;          // sub-tiles issued
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(kRrThreads, kRrCtasPerSm) k_rerank_tc(MatchLau
         auto idx_of = [&](const SubTile& t, uint32_t (&jr)[C::PER_THREAD]) {
 #pragma unroll
             for (int q = 0; q < C::PER_THREAD; ++q) {
-                const int r = (tid + q * kProd) / C::CPR;
+                const int r = (tid + q * C::PROD) / C::CPR;
                 jr[q] = (r < 128 && r / K < t.nq) ? (uint32_t)ml.topk16[t.row * K + r] : (uint32_t)kNoCand;
             }
         };
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(kRrThreads, kRrCtasPerSm) k_rerank_tc(MatchLau
             const unsigned char* qrow = t.ixq + (size_t)t.q0 * rb;   // a valid row for padding
 #pragma unroll
             for (int q = 0; q < C::PER_THREAD; ++q) {
-                const int e = tid + q * kProd;
+                const int e = tid + q * C::PROD;
                 if (e < C::CHUNKS) {
                     const int r = e / C::CPR, c = e % C::CPR;
                     const int h = c >> 3, c8 = c & 7;     // 128-byte column block, chunk in it
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(kRrThreads, kRrCtasPerSm) k_rerank_tc(MatchLau
         }
         if (!ok) give_up();
         asm volatile("cp.async.wait_all;" ::: "memory");
-    } else if (warp == kMmaWarp) {
+    } else if (warp == C::MMA_WARP) {
         // ---------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = FP8 ? tc::idesc_e4m3(128, C::NB) : tc::idesc_f16(128, C::NB, 1);
@@ -327,8 +331,8 @@ __global__ void __launch_bounds__(kRrThreads, kRrCtasPerSm) k_rerank_tc(MatchLau
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue: group g takes the sub-tiles with it % kEpiGroups == g
-        const int g = (warp - kEpiWarp0) >> 2;
+        // ---------------- epilogue: group g takes the sub-tiles with it % EPI == g
+        const int g = (warp - C::EPI_WARP0) >> 2;
         const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31
         const int r = 32 * quarter + lane;          // candidate row of the A tile
         const int c = r / K, k = r % K;             // its query column and slot
@@ -358,13 +362,13 @@ __global__ void __launch_bounds__(kRrThreads, kRrCtasPerSm) k_rerank_tc(MatchLau
         int it = 0;          // position in the CTA's sequence of non-empty sub-tiles
         Cursor<true> cursor;
         int u = blockIdx.x - (int)gridDim.x;
-        // advances to this group's next sub-tile (every kEpiGroups-th of the sequence)
+        // advances to this group's next sub-tile (every EPI-th of the sequence)
         auto next = [&](SubTile& t, int& myit) -> bool {
             for (u += gridDim.x; u < n_sub; u += gridDim.x) {
                 t = cursor.at(ml, u, per_item, C::QS);
                 if (t.nq <= 0) continue;
                 const int pos = it++;
-                if (pos % kEpiGroups == g) {
+                if (pos % C::EPI == g) {
                     myit = pos;
                     return true;
                 }
@@ -381,8 +385,7 @@ __global__ void __launch_bounds__(kRrThreads, kRrCtasPerSm) k_rerank_tc(MatchLau
             if (!warp_wait(&tfull[a], aph, abort_flag)) return false;
             tc::fence_after();
             uint32_t vv[W];
-            tc::tmem_ld_cols<W>(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(a * C::NB + col0), vv);
-            tc::tmem_wait_ld(vv);
+            tc::tmem_load<W>(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(a * C::NB + col0), vv);
             // column c = col0 + lane / K, picked by a binary tree of selects on the
             // bits of lane / K (the values stay in registers)
             const int sel = lane / K;
@@ -480,7 +483,7 @@ __global__ void __launch_bounds__(kRrThreads, kRrCtasPerSm) k_rerank_tc(MatchLau
         if (s_stats[1]) atomicAdd(&ml.out.stats[1], s_stats[1]);
         if (s_stats[2]) atomicAdd(&ml.out.stats[2], s_stats[2]);
     }
-    if (warp == kMmaWarp) {
+    if (warp == C::MMA_WARP) {
         tc::fence_after();
         tc::tmem_dealloc(tmem, 256);
     }
@@ -554,9 +557,9 @@ cudaError_t launch_rr(const MatchLaunch& m, int sms, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_rerank_tc<K, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
     const int n_sub = m.n_items * (m.S / C::QS);
-    const int slots = kRrCtasPerSm * sms;
+    const int slots = C::CTAS * sms;
     const int grid = n_sub < slots ? (n_sub ? n_sub : 1) : slots;
-    k_rerank_tc<K, FP8><<<grid, kRrThreads, C::SMEM, s>>>(m);
+    k_rerank_tc<K, FP8><<<grid, C::THREADS, C::SMEM, s>>>(m);
     return cudaGetLastError();
 }
 

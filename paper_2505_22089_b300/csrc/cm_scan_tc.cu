@@ -387,8 +387,7 @@ __global__ void __launch_bounds__(kScThreads, 1) k_scan_tc(MatchLaunch ml) {
                 const int N = (be.nb + 15) & ~15;
                 for (int c0 = 0; c0 < N && ok; c0 += 16) {
                     uint32_t v[16];
-                    tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(a * 128 + c0), v);
-                    tc::tmem_wait_ld(v);
+                    tc::tmem_load16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(a * 128 + c0), v);
                     if (!valid) continue;
                     // h < h_K  <=>  dot > 128 - 2 h_K; equality is decided by the index, below
                     const float thr = 128.f - 2.f * (float)(s[K - 1] >> 16);

@@ -129,47 +129,44 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;"); }
 
-// 16 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes 32w..32w+31).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+// TMEM loads.  Each helper issues tcgen05.ld and tcgen05.wait::ld in ONE asm
+// statement, so the destination registers are defined only after the wait:
+// with separate statements the compiler sees them defined at the load and
+// may use them, or spill them to local memory, before the data has arrived.
+// Warp w reads lanes 32 (w % 4) .. +31; each thread gets W consecutive FP32
+// columns of its lane.
+__device__ __forceinline__ void tmem_load16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                 "tcgen05.wait::ld.sync.aligned;"
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
                    "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                 : "r"(taddr));
+                 : "r"(taddr) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t (&v)[2]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(v[0]), "=r"(v[1]) : "r"(taddr));
+__device__ __forceinline__ void tmem_load2(uint32_t taddr, uint32_t (&v)[2]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];\ntcgen05.wait::ld.sync.aligned;"
+                 : "=r"(v[0]), "=r"(v[1]) : "r"(taddr) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(taddr));
+__device__ __forceinline__ void tmem_load4(uint32_t taddr, uint32_t (&v)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\ntcgen05.wait::ld.sync.aligned;"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(taddr) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+__device__ __forceinline__ void tmem_load8(uint32_t taddr, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 "tcgen05.wait::ld.sync.aligned;"
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                 : "r"(taddr));
+                 : "r"(taddr) : "memory");
 }
 
-// W consecutive columns (W = 2, 4, 8 or 16) of the warp's 32 lanes.
+// W consecutive columns (W = 2, 4, 8 or 16).
 template <int W>
-__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&v)[W]) {
-    if constexpr (W == 2) tmem_ld2(taddr, v);
-    else if constexpr (W == 4) tmem_ld4(taddr, v);
-    else if constexpr (W == 8) tmem_ld8(taddr, v);
-    else tmem_ld16(taddr, v);
-}
-
-// tcgen05.wait::ld for the registers v of the loads before it.  The loaded
-// registers are valid only after the wait, but the compiler sees them defined
-// by the load; tying each one to an empty volatile statement after the wait
-// keeps every use of them below the wait.
-template <int W>
-__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[W]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < W; ++i) asm volatile("" : "+r"(v[i]));
+__device__ __forceinline__ void tmem_load(uint32_t taddr, uint32_t (&v)[W]) {
+    if constexpr (W == 2) tmem_load2(taddr, v);
+    else if constexpr (W == 4) tmem_load4(taddr, v);
+    else if constexpr (W == 8) tmem_load8(taddr, v);
+    else tmem_load16(taddr, v);
 }
 
 }  // namespace tc

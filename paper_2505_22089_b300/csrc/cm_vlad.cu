@@ -100,8 +100,7 @@ k_vlad_assign(const uint8_t* __restrict__ desc, int64_t n_rows, const uint8_t* _
         int bc = 0;
         for (int c0 = 0; c0 < NC; c0 += 16) {
             uint32_t v[16];
-            tc::tmem_ld16(lane + c0, v);
-            tc::tmem_wait_ld(v);
+            tc::tmem_load16(lane + c0, v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const float d = fmaf(-2.f, __uint_as_float(v[j]), cn[c0 + j]);   // exact: integers below 2^24

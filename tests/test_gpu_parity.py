@@ -199,6 +199,31 @@ def test_bf16_tensor_core_rerank_full_strip():
     _run(synth.strip30(), cm.Params.make(rerank="bf16"), threads=16)
 
 
+def test_bf16_form_equals_fp32_form_on_a_grid():
+    # BF16 products of uint8 and their FP32 sums are exact, so the tensor-core
+    # rerank must decide every query as the CUDA-core FP32 form does.  A grid
+    # of 20,000-descriptor images gives every CTA hundreds of sub-tiles, so the
+    # stage and accumulator rings wrap many times (the small cases above give
+    # a CTA one sub-tile or none)
+    wl = synth.scaled("grid5000", gx=8, gy=5)
+    desc = torch.from_numpy(wl.generate()).cuda()
+    res = {}
+    for form in ("fp32", "bf16", "bf16"):
+        index = cm.Index.build(cm.Params.make(rerank=form), wl.n_desc, desc)
+        plan = cm.MatchPlan(index, wl.pairs)
+        out = plan.alloc_out()
+        plan.run(out)
+        torch.cuda.synchronize()
+        got = tuple(out[k].cpu().numpy() for k in ("best_j", "d1sq", "d2sq"))
+        if form in res:   # a rerun gives the same bits
+            assert all(np.array_equal(a, b) for a, b in zip(got, res[form]))
+        res[form] = got
+        del plan, index, out
+    for a, b in zip(res["bf16"], res["fp32"]):
+        assert np.array_equal(a, b)
+    assert (res["bf16"][0] >= 0).sum() > 0.1 * len(res["bf16"][0])
+
+
 @pytest.mark.parametrize("K", [2, 4, 8, 16])
 def test_fp8_tensor_core_rerank(K):
     # E4M3 distances pick q1, q2, which are re-scored exactly: top-K lists are
