@@ -403,7 +403,12 @@ __global__ void __launch_bounds__(RR<K, FP8>::THREADS, RR<K, FP8>::CTAS) k_reran
                     const uint32_t d2 = (uint32_t)((float)v.nx + (float)v.ny - 2.f * dot);   // exact: integers < 2^24
                     mine = ((uint64_t)d2 << 32) | (uint32_t)j;
                 } else {
-                    const float d2a = fmaxf((float)v.nx + (float)v.ny - 2.f * dot * v.sx * v.sy, 0.f);
+                    // each step rounded on its own (no contraction into an FMA), so the
+                    // approximate distance, and with it the pick of q1 and q2 among near
+                    // ties, does not depend on how a build schedules the expression
+                    const float d2a = fmaxf(__fsub_rn(__fadd_rn((float)v.nx, (float)v.ny),
+                                                      __fmul_rn(__fmul_rn(__fmul_rn(2.f, dot), v.sx), v.sy)),
+                                            0.f);
                     mine = ((uint64_t)__float_as_uint(d2a) << 32) | (uint32_t)j;
                 }
             }
