@@ -253,6 +253,13 @@ int64_t cm_match_plan_rows(const cm_match_plan* pl);
  * reranks the rerank and ratio test run in a second, tensor-core launch that
  * reads the first one's top-K lists. */
 cm_status cm_match_plan_run(cm_match_plan* pl, const cm_match_out* out, cm_stream stream);
+/* cm_match_plan_run that also records scan_done (a cudaEvent_t created by the
+ * caller, or NULL) on the stream right after the lookup / Hamming / top-K
+ * launch, before the rerank launch of the BF16 / FP8 / TC-scan forms (after
+ * the single launch of the fused forms).  Events around the call then time
+ * the two launches apart.  The event stays owned by the caller; errors as for
+ * cm_match_plan_run, plus CM_ERR_CUDA when the record fails. */
+cm_status cm_match_plan_run_marked(cm_match_plan* pl, const cm_match_out* out, void* scan_done, cm_stream stream);
 /* Compaction of the plan's decisions into per-pair match lists, the initial
  * matches handed to outlier removal (Algorithm 1).  From d_best_j (a
  * cm_match_plan_run output) writes, all device memory: d_counts [n_pairs]

@@ -49,6 +49,7 @@ EXPORTS = [
     "cm_schedule_get_row", "cm_free_schedule", "cm_gps_order", "cm_index_create", "cm_index_set_mean",
     "cm_index_mean_device", "cm_index_col_sums", "cm_index_check", "cm_index_load", "cm_index_rehash", "cm_index_evict", "cm_build_index",
     "cm_index_image_view", "cm_index_destroy", "cm_match_plan_create", "cm_match_plan_rows", "cm_match_plan_run",
+    "cm_match_plan_run_marked",
     "cm_match_plan_compact", "cm_match_plan_mutual", "cm_match_plan_destroy", "cm_match_pairs", "cm_sequence_create", "cm_sequence_launch",
     "cm_sequence_kernels", "cm_sequence_destroy", "cm_schedule_arena_bytes", "cm_pipeline_workspace_bytes", "cm_run_schedule",
     "cm_verify_affine", "cm_affine_verify_cb", "cm_sao_filter", "cm_schedule_from_rows", "cm_vlad_workspace_bytes", "cm_vlad_encode",
@@ -169,6 +170,7 @@ def lib():
             "cm_match_plan_create": (i32, [vp, vp, i64, vp, ctypes.POINTER(vp)]),
             "cm_match_plan_rows": (i64, [vp]),
             "cm_match_plan_run": (i32, [vp, ctypes.POINTER(MatchOut), vp]),
+            "cm_match_plan_run_marked": (i32, [vp, ctypes.POINTER(MatchOut), vp, vp]),
             "cm_match_plan_destroy": (None, [vp]),
             "cm_match_plan_compact": (i32, [vp, vp, vp, vp, vp, vp, u64, vp]),
             "cm_match_plan_mutual": (i32, [vp, vp, vp, vp]),
@@ -598,10 +600,18 @@ class MatchPlan:
             out["stats"] = torch.zeros(4, dtype=torch.int32, device="cuda")
         return out
 
-    def run(self, out: dict, stream=None):
+    def run(self, out: dict, stream=None, scan_done=None):
+        """scan_done: an optional torch.cuda.Event, recorded on the stream after
+        the lookup launch (before the rerank launch of the tensor-core forms)."""
         mo = MatchOut(*[ctypes.c_void_p(out[k].data_ptr()) if out.get(k) is not None else None
                         for k in ("best_j", "d1sq", "d2sq", "topk", "stats")])
-        check(lib().cm_match_plan_run(self.h, ctypes.byref(mo), _stream(stream)))
+        if scan_done is None:
+            check(lib().cm_match_plan_run(self.h, ctypes.byref(mo), _stream(stream)))
+            return
+        if not scan_done.cuda_event:   # torch creates the event at its first record
+            scan_done.record(stream)
+        check(lib().cm_match_plan_run_marked(self.h, ctypes.byref(mo), ctypes.c_void_p(scan_done.cuda_event),
+                                             _stream(stream)))
 
     def compact(self, best_j, capacity: int | None = None, stream=None):
         """Per-pair match lists from a run's best_j: returns CUDA tensors

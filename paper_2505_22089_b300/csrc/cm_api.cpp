@@ -662,11 +662,20 @@ extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, in
 extern "C" int64_t cm_match_plan_rows(const cm_match_plan* pl) { return pl ? pl->rows : -1; }
 
 extern "C" cm_status cm_match_plan_run(cm_match_plan* pl, const cm_match_out* out, cm_stream stream) {
+    return cm_match_plan_run_marked(pl, out, nullptr, stream);
+}
+
+extern "C" cm_status cm_match_plan_run_marked(cm_match_plan* pl, const cm_match_out* out, void* scan_done,
+                                              cm_stream stream) {
     if (!pl || !out || (!out->best_j && pl->rows)) return fail(CM_ERR_INVALID, "plan_run: bad argument");
     cm_index* ix = pl->ix;
     if (!ix) return fail(CM_ERR_STATE, "plan_run: the plan's index was destroyed");
-    if (!pl->n_items) return CM_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t mark = reinterpret_cast<cudaEvent_t>(scan_done);
+    if (!pl->n_items) {
+        if (mark) CM_CUDA(cudaEventRecord(mark, s));
+        return CM_OK;
+    }
     const uint64_t counter_at = pl->table_at + align_up((uint64_t)pl->n_pairs * sizeof(DevPair));
     unsigned* counter = reinterpret_cast<unsigned*>(ix->arena + counter_at);
     CM_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
@@ -704,10 +713,12 @@ extern "C" cm_status cm_match_plan_run(cm_match_plan* pl, const cm_match_out* ou
             m.algo = CM_ALGO_TILE;
             CM_CUDA(launch_match(m, ix->sms, s));
         }
+        if (mark) CM_CUDA(cudaEventRecord(mark, s));
         CM_CUDA(tc_rerank(&pp) ? launch_rerank_tc(m, ix->sms, s) : launch_rerank_cc(m, ix->sms, s));
         return CM_OK;
     }
     CM_CUDA(m.algo == CM_ALGO_TILE ? launch_match(m, ix->sms, s) : launch_match_wq(m, ix->sms, s));
+    if (mark) CM_CUDA(cudaEventRecord(mark, s));
     return CM_OK;
 }
 

@@ -188,6 +188,26 @@ def test_plan_rerun_is_deterministic():
             assert np.array_equal(o[k], outs[0][k])
 
 
+@pytest.mark.parametrize("rerank", ["fp32", "bf16"])
+def test_marked_run_times_the_lookup_launch(rerank):
+    # cm_match_plan_run_marked records the caller's event between the lookup
+    # and the rerank launch; the results are those of cm_match_plan_run
+    wl = synth.strip30(n_images=4, n=3000)
+    index = cm.Index.build(cm.Params.make(rerank=rerank), wl.n_desc, torch.from_numpy(wl.generate()).cuda())
+    plan = cm.MatchPlan(index, wl.pairs)
+    a, b = plan.alloc_out(), plan.alloc_out()
+    plan.run(a)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    plan.run(b, scan_done=ev[1])
+    ev[2].record()
+    torch.cuda.synchronize()
+    for k in ("best_j", "d1sq", "d2sq"):
+        assert torch.equal(a[k], b[k])
+    t_scan, t_all = ev[0].elapsed_time(ev[1]), ev[0].elapsed_time(ev[2])
+    assert 0 < t_scan <= t_all
+
+
 @pytest.mark.parametrize("K", [2, 4, 8, 16])
 def test_bf16_tensor_core_rerank_is_exact(K):
     # BF16 holds uint8 exactly and the FP32 accumulation of integer products is
