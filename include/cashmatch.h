@@ -504,8 +504,8 @@ cm_status cm_selftest_wait(int32_t polls, cm_stream stream);
 
 /* ---- exhaustive nearest neighbours (quality ceiling) --------------------- */
 /* Device workspace of cm_nn_pairs for these images and pairs (it holds a BF16
- * operand copy of every database image the pairs name: 128 KB per 256 rows,
- * 64 KB of it the tile). */
+ * operand copy of every database image the pairs name: 72 KB per 256 rows,
+ * -2y and the base-256 digits of |y|^2 in the tensor-core tile layout). */
 cm_status cm_nn_workspace_bytes(const int64_t* img_off, int32_t n_images, const cm_pair* pairs, int64_t n_pairs,
                                 uint64_t* bytes);
 /* Exhaustive nearest neighbours with the exact ratio test for each pair: for
@@ -514,8 +514,9 @@ cm_status cm_nn_workspace_bytes(const int64_t* img_off, int32_t n_images, const 
  * ties to the smaller j), and best_j = j1 when den^2 d1^2 < num^2 d2^2 (no
  * match with fewer than 2 rows in j).  These are the matches cascade hashing
  * gives with every database point a candidate (Sec. 2.3.1 with K = N_J): the
- * ceiling its recall is measured against.  d^2 = |x|^2 + |y|^2 - 2 x.y with
- * x.y from BF16 tensor-core products, exact on integers.
+ * ceiling its recall is measured against.  d^2 = |x|^2 + t with
+ * t = |y|^2 - 2 x.y from one BF16 tensor-core product (|y|^2 enters as an
+ * extra K block of digits), exact on integers.
  *  - desc: device uint8 [rows][128], all images concatenated; img_off: host
  *    int64 [n_images + 1], img_off[0] = 0, ascending, <= 65535 rows per image.
  *  - pairs: host, n_pairs entries; output rows: pair k owns rows
