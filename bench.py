@@ -65,7 +65,15 @@ def parse():
     ap.add_argument("--block-images", type=int, default=400, help="Size_blk: images per schedule chunk")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="HBM budget of the MBR schedule")
     ap.add_argument("--plain-pairs", type=int, default=200, help="pairs timed in the plain per-pair form")
-    ap.add_argument("--oracle-pairs", type=int, default=12, help="pairs in the CPU-oracle sample")
+    ap.add_argument("--oracle-pairs", type=int, default=12,
+                    help="pairs per step of the reference arm's oracle sample")
+    ap.add_argument("--oracle-frac", type=float, default=0.02,
+                    help="share of the pairs the FP64 oracle checks in full (at least --oracle-min-pairs); 0: skip")
+    ap.add_argument("--oracle-min-pairs", type=int, default=1000)
+    ap.add_argument("--configs", default="all", choices=["all", "none"],
+                    help="also measure the four smaller workloads (pair2k, strip30, grid500, oblique200)")
+    ap.add_argument("--config-oracle-pairs", type=int, default=300,
+                    help="pairs the oracle checks in full per smaller workload (all pairs when fewer)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--nn-pairs", type=int, default=64,
                     help="sampled pairs matched exhaustively on the tensor cores (recall ceiling, L/K sweep); 0: skip")
@@ -202,7 +210,202 @@ def _sync_ms(ms, world, dev):
     return float(t.item())
 
 
-def device_forms(args, wl, desc_dev, rows, stream, dev, world, forms):
+U32_MAX = 0xFFFFFFFF
+
+
+def pick_sample(pairs, frac, min_pairs, seed=0):
+    """A seeded sample of pair ids for the full oracle check (frac of the pairs,
+    at least min_pairs), the images it names, and every pair both of whose
+    images are among them (their near-threshold queries are checked too)."""
+    P = len(pairs)
+    n = min(P, max(int(min_pairs), int(np.ceil(frac * P))))
+    sel = np.sort(np.random.default_rng(seed).choice(P, n, replace=False)) if n else np.zeros(0, np.int64)
+    imgs = np.unique(pairs[sel]) if n else np.zeros(0, np.int64)
+    elig = np.nonzero(np.isin(pairs[:, 0], imgs) & np.isin(pairs[:, 1], imgs))[0]
+    return sel, imgs, elig
+
+
+def gpu_outputs(plans, outs, rows, sel, elig, ratio, index, imgs, extra=()):
+    """Host copies of what the oracle check needs from one pass's device
+    outputs (outs with best_j, d1sq, d2sq): every row of the sampled pairs (and
+    of `extra` pairs), the near-threshold rows of the eligible pairs
+    (|sqrt(d1/d2) - t_r| < 1e-3 by the GPU's own distances), and the keys and
+    codes of the sampled images."""
+    import torch
+    where = {}
+    for r, rr in enumerate(rows):
+        for q, k in enumerate(rr):
+            where[int(k)] = (r, q)
+
+    def rows_of(k):
+        r, q = where[k]
+        a, b = plans[r].row_off[q], plans[r].row_off[q + 1]
+        o = outs[r]
+        return (o["best_j"][a:b].cpu().numpy(), o["d1sq"][a:b].cpu().numpy().view(np.uint32),
+                o["d2sq"][a:b].cpu().numpy().view(np.uint32))
+
+    full = {int(k): rows_of(int(k)) for k in set(sel.tolist()) | set(int(x) for x in extra)}
+    t = ratio[0] / ratio[1]
+    elig_set = set(elig.tolist())
+    near = {}
+    for r, (pl, o) in enumerate(zip(plans, outs)):
+        if not pl.rows or not elig_set:
+            continue
+        d1 = (o["d1sq"][:pl.rows].to(torch.int64) & U32_MAX).double()
+        d2 = (o["d2sq"][:pl.rows].to(torch.int64) & U32_MAX).double()
+        m = (d2 < float(U32_MAX)) & (d2 > 0) & ((torch.sqrt(d1 / d2.clamp(min=1.0)) - t).abs() < 1e-3)
+        idx = torch.nonzero(m).flatten()
+        del d1, d2, m
+        if not idx.numel():
+            continue
+        b = o["best_j"][idx].cpu().numpy()
+        e1 = o["d1sq"][idx].cpu().numpy().view(np.uint32)
+        e2 = o["d2sq"][idx].cpu().numpy().view(np.uint32)
+        idx = idx.cpu().numpy()
+        q = np.searchsorted(pl.row_off, idx, side="right") - 1
+        for qq in np.unique(q):
+            k = int(rows[r][qq])
+            if k not in elig_set:
+                continue
+            sel_q = q == qq
+            near[k] = (idx[sel_q] - pl.row_off[qq], b[sel_q], e1[sel_q], e2[sel_q])
+    bits = {int(i): index.image_bits(int(i)) for i in imgs}
+    return {"full": full, "near": near, "bits": bits}
+
+
+def _oparams(p):
+    import oracle
+    return oracle.Params(L=p.L, m=p.m, nbits=p.n_bits, K=p.K, ratio_num=p.ratio_num, ratio_den=p.ratio_den,
+                         seed=p.seed)
+
+
+def _match_set(best):
+    q = np.nonzero(best >= 0)[0]
+    return set(zip(q.tolist(), best[q].tolist()))
+
+
+def oracle_check(wl, desc, p, pairs, sel, imgs, elig, got, gpu_sums, form, marginal_images=32, one_core=True,
+                 cache=None):
+    """The FP64 oracle against the GPU's outputs, with the oracle's own
+    centring sums: (1) the sums themselves; (2) every key / code bit of the
+    sampled images (differing bits must be marginal: |s| < 1e-4 |x - mu|;
+    the marginal share is counted on a subset of them); (3) every query of the
+    sampled pairs: decision, match-set Jaccard, exact d^2; (4) every
+    near-threshold query of the pairs whose two images the sample hashed, one
+    query at a time.  Also times the oracle as it stands (all host cores, and
+    one core) for the CPU baseline."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    cores = os.cpu_count() or 1
+    op = _oparams(p)
+    if cache is not None and cache.get("key") == (op, tuple(sel.tolist())):
+        oix, res, t_sums, t_match = cache["val"]                  # the same workload checked for another form
+    else:
+        t0 = time.perf_counter()
+        oix = oracle.Index(desc, wl.n_desc, op, threads=cores)     # its own sums over every row
+        t_sums = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        res = oix.match(pairs[sel])                               # hashes the sampled images, then matches
+        t_match = time.perf_counter() - t0
+        if cache is not None:
+            cache["key"], cache["val"] = (op, tuple(sel.tolist())), (oix, res, t_sums, t_match)
+    out = {"form": form, "oracle_sums_equal_gpu": bool(np.array_equal(oix.sums, gpu_sums)),
+           "oracle_sums": "computed by the oracle from the raw rows (not the GPU's)"}
+    # (2) bits
+    n_bits = n_diff = n_diff_nonmarg = 0
+    L, m = p.L, p.m
+    diff_imgs = []
+    for i in imgs:
+        gk, gc = got["bits"][int(i)]
+        oi = oix.image(int(i))
+        kd = np.unpackbits((gk ^ oi.keys).reshape(-1, L, 1), axis=2, bitorder="little")[:, :, :m].reshape(len(gk), -1)
+        cd = np.unpackbits((gc ^ oi.code).view(np.uint8), axis=1, bitorder="little")
+        d = np.concatenate([kd, cd], axis=1).astype(bool)
+        n_bits += d.size
+        if d.any():
+            n_diff += int(d.sum())
+            diff_imgs.append((int(i), d))
+    for i, d in diff_imgs:                                        # differing bits must be marginal ones
+        oi = oracle.hash_image(oix.image_desc(i), oix.mu, oix.W, op, marginal=True)
+        n_diff_nonmarg += int((d & (oi.marginal == 0)).sum())
+    n_mb = n_marg = 0
+    for i in imgs[:marginal_images]:
+        oi = oracle.hash_image(oix.image_desc(int(i)), oix.mu, oix.W, op, marginal=True)
+        n_marg += int(oi.marginal.sum())
+        n_mb += int(oi.marginal.size)
+    out["bits"] = {"images": int(len(imgs)), "bits": n_bits, "differing": n_diff,
+                   "differing_share": n_diff / max(n_bits, 1), "differing_not_marginal": n_diff_nonmarg,
+                   "marginal_share": n_marg / max(n_mb, 1), "marginal_counted_on_images": int(min(len(imgs),
+                                                                                           marginal_images)),
+                   "marginal": "|s| < 1e-4 |x - mu| (FP64); must stay under 0.01 % of bits"}
+    # (3) sampled pairs in full
+    same = total = inter = union = ng = no = 0
+    d_cmp = d_err = 0
+    for k, o in zip(sel, res):
+        g, g1, g2 = got["full"][int(k)]
+        same += int((g == o["best_j"]).sum())
+        total += len(g)
+        gm, om = _match_set(g), _match_set(o["best_j"])
+        inter += len(gm & om)
+        union += len(gm | om)
+        ng += len(gm)
+        no += len(om)
+        both = (g == o["best_j"]) & (g >= 0)
+        d_cmp += int(both.sum())
+        d_err = max(d_err, float(np.max(np.abs(g1[both].astype(np.float64) - o["d1sq"][both]) /
+                                         np.maximum(o["d1sq"][both], 1), initial=0.0)))
+        d_err = max(d_err, float(np.max(np.abs(g2[both].astype(np.float64) - o["d2sq"][both]) /
+                                         np.maximum(o["d2sq"][both], 1), initial=0.0)))
+    out["sample"] = {"pairs": int(len(sel)), "of_pairs": int(len(pairs)), "share": len(sel) / max(len(pairs), 1),
+                     "seed": 0, "queries": total, "per_query_agreement": same / max(total, 1),
+                     "match_set_jaccard": inter / union if union else 1.0, "gpu_matches": ng, "oracle_matches": no,
+                     "d2_max_rel_err": d_err, "d2_compared": d_cmp,
+                     "d2_note": "d1^2 and d2^2 of every query whose decision agrees with a match"}
+    # (4) near-threshold queries, one by one
+    jobs = [(k, v) for k, v in got["near"].items()]
+
+    def check_near(job):
+        k, (qs, b, e1, e2) = job
+        i, j = (int(x) for x in pairs[k])
+        I, J = oix.image(i), oix.image(j)
+        agree = dd = 0
+        for q, bb, a1, a2 in zip(qs, b, e1, e2):
+            o = oracle.match_pair(I, J, op, q0=int(q), q1=int(q) + 1)
+            agree += int(o["best_j"][0] == bb)
+            dd += int(o["d1sq"][0] == a1 and o["d2sq"][0] == a2)
+        return agree, dd, len(qs)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        rr = list(ex.map(check_near, jobs))
+    a = sum(x[0] for x in rr)
+    dd = sum(x[1] for x in rr)
+    nq = sum(x[2] for x in rr)
+    out["near_threshold"] = {"definition": "|sqrt(d1/d2) - t_r| < 1e-3 by the GPU's d1, d2",
+                             "pairs_scanned": int(len(elig)), "pairs_with_such_queries": len(jobs), "queries": nq,
+                             "decision_agreement": a / max(nq, 1), "distances_equal": dd / max(nq, 1),
+                             "oracle_s": round(time.perf_counter() - t0, 2)}
+    per_pair = (t_match + t_sums * len(sel) / max(len(pairs), 1)) / max(len(sel), 1)
+    out["oracle_time_s"] = {"sums_all_rows": round(t_sums, 2), "hash_and_match_sample": round(t_match, 2)}
+    base = {"value": 1.0 / per_pair, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of %d pairs (seeded), FP64 oracle as it stands on %d host threads: its own column sums "
+                      "over all %d rows (time pro-rated per pair), hashing of the %d images the sample names, "
+                      "matching" % (len(sel), len(pairs), cores, wl.total_desc, len(imgs))}
+    if one_core and len(sel):
+        k = int(sel[0])
+        i, j = (int(x) for x in pairs[k])
+        t0 = time.perf_counter()
+        I1 = oracle.hash_image(oix.image_desc(i), oix.mu, oix.W, op)
+        J1 = oracle.hash_image(oix.image_desc(j), oix.mu, oix.W, op)
+        oracle.match_pair(I1, J1, op)
+        t1c = time.perf_counter() - t0
+        base["one_core"] = {"value": 1.0 / (t1c + t_sums * cores / max(len(pairs), 1)), "unit": "pairs/s",
+                            "sample": "pair %d: hash both images + match on one thread; the sums pass pro-rated "
+                                      "per pair at %d x its all-core time" % (k, cores)}
+    return out, base
+
+
+def device_forms(args, wl, desc_dev, rows, stream, dev, world, forms, check=None, extra=()):
     """Device-resident steps, one per rerank form: descriptors already in HBM;
     a step = the captured block sequence (rehash of every resident image, then
     per block row one fused match launch and its compaction) replayed as one
@@ -264,16 +467,24 @@ def device_forms(args, wl, desc_dev, rows, stream, dev, world, forms):
             r["match_jaccard_vs_fp32"] = inter / union if union else 1.0
         if form == headline:
             # the same launches without the graph, events around every match launch
-            # (the middle event is recorded by the library after the lookup launch)
+            # (the middle event is recorded by the library after the lookup launch);
+            # these outputs also carry d1^2, d2^2 and the counters of the last step
+            outs_d = [dict(o, d1sq=torch.empty_like(o["best_j"]), d2sq=torch.empty_like(o["best_j"])) for o in outs]
             evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in plans]
                    for _ in range(args.steps)]
             for s in range(args.steps):
+                if s == args.steps - 1:
+                    for o in outs_d:
+                        o["stats"].zero_()
                 index.rehash(stream)
-                for k, (pl, o) in enumerate(zip(plans, outs)):
+                for k, (pl, o) in enumerate(zip(plans, outs_d)):
                     evs[s][k][0].record(stream)
                     pl.run(o, stream, scan_done=evs[s][k][1])
                     evs[s][k][2].record(stream)
             stream.synchronize()
+            st = torch.stack([o["stats"] for o in outs_d]).sum(0).cpu().numpy()
+            r["fp64_rechecks_per_step"] = int(st[0])
+            r["fp8_top2_swaps_per_step"] = int(st[2])
             launch_ms = [e[k][0].elapsed_time(e[k][2]) for e in evs for k in range(len(plans))]
             scan_ms = [e[k][0].elapsed_time(e[k][1]) for e in evs for k in range(len(plans))]
             r["match_launch_ms"] = float(np.mean(launch_ms))
@@ -281,13 +492,13 @@ def device_forms(args, wl, desc_dev, rows, stream, dev, world, forms):
             r["match_ms_per_step"] = float(np.sum(launch_ms)) / args.steps
             r["evals_per_step"] = bucket_evaluations(index, wl, pairs)
             r["launches"] = len(plans)
-            gpu_rows = {}
-            for pl, o, rr in zip(plans, outs, rows):
-                bj = o["best_j"].cpu().numpy()
-                for q, k in enumerate(rr):
-                    gpu_rows[int(k)] = bj[pl.row_off[q]:pl.row_off[q + 1]]
-            r["_gpu_rows"] = gpu_rows
+            r["_p"] = cm.Params.from_buffer_copy(index.p)
             r["_sums"] = index.col_sums(stream)[0]
+            if check is not None:
+                sel, imgs, elig = check
+                r["_got"] = gpu_outputs(plans, outs_d, rows, sel, elig, (p.ratio_num, p.ratio_den), index, imgs,
+                                        extra)
+            del outs_d
         res[form] = r
         seq.close()
         for pl in plans:
@@ -296,6 +507,84 @@ def device_forms(args, wl, desc_dev, rows, stream, dev, world, forms):
         del seq, plans, outs, comps, index, best
         torch.cuda.empty_cache()
     return res
+
+
+# The smaller workloads measured next to the headline one: (line, workload, rerank form, HBM budget in GB,
+# Size_blk).  grid500 runs once as one block and once cut into blocks of at most 100 images.
+CONFIG_RUNS = [("pair2k", "pair2k", "fp32", 150.0, 400), ("strip30", "strip30", "fp32", 150.0, 400),
+               ("grid500", "grid500", "fp32", 40.0, 400), ("grid500_blk100", "grid500", "fp32", 40.0, 100),
+               ("oblique200_bf16", "oblique200", "bf16", 150.0, 400),
+               ("oblique200_fp8", "oblique200", "fp8", 150.0, 400)]
+
+
+def config_lines(args, stream, dev):
+    """Per workload: pairs/s of the device-resident step (one CUDA graph:
+    rehash, per block row one match launch and its compaction, as for the
+    headline workload), then the FP64 oracle (own sums) on every pair, or on
+    a seeded sample of --config-oracle-pairs pairs plus the near-threshold
+    queries of the pairs among the sampled images."""
+    import torch
+    import paper_2505_22089_b300 as cm
+    out = {}
+    descs, caches = {}, {}
+    for key, wname, form, budget_gb, size_blk in CONFIG_RUNS:
+        wl = synth.workload(wname)
+        if wname not in descs:
+            descs[wname] = wl.generate()
+        desc = descs[wname]
+        pairs = wl.pairs
+        p = cm.Params.make(rerank=form)
+        sched = cm.schedule_blocks(pairs, wl.n_desc, p, int(budget_gb * 2 ** 30), size_blk)
+        rows = [np.asarray(r["pairs"], dtype=np.int64) for r in sched.rows if r["pairs"]]
+        n_rows, n_iter = len(sched.rows), sched.iterations
+        sched.close()
+        desc_dev = torch.from_numpy(desc).to(dev)
+        arena = (cm.index_bytes(p, wl.n_desc, inplace=True) + cm.PLAN_HEADROOM +
+                 sum(cm.pairs_plan_bytes(p, wl.n_desc, pairs[r]) for r in rows))
+        with torch.cuda.stream(stream):
+            index = cm.Index.build(p, wl.n_desc, desc_dev, stream=stream, arena_bytes=arena)
+            plans = [cm.MatchPlan(index, pairs[r], stream=stream) for r in rows]
+            outs = [pl.alloc_out() for pl in plans]
+            comps = [cm.compact_out(pl) for pl in plans]
+        stream.synchronize()
+        seq = cm.Sequence(index, plans, outs, comps, rehash=True, stream=stream)
+        for _ in range(args.warmup):
+            seq.launch(stream)
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            start.record(stream)
+            for _ in range(args.steps):
+                seq.launch(stream)
+            stop.record(stream)
+            stop.synchronize()
+        ms = start.elapsed_time(stop) / args.steps
+        for o in outs:
+            o["stats"].zero_()
+        seq.launch(stream)
+        stream.synchronize()
+        index.check(stream)
+        st = torch.stack([o["stats"] for o in outs]).sum(0).cpu().numpy()
+        P = len(pairs)
+        n_s = min(P, args.config_oracle_pairs)
+        sel, imgs, elig = pick_sample(pairs, n_s / P, n_s)
+        got = gpu_outputs(plans, outs, rows, sel, elig, (p.ratio_num, p.ratio_den), index, imgs)
+        sums = index.col_sums(stream)[0]
+        seq.close()
+        for pl in plans:
+            pl.close()
+        index.close()
+        del seq, plans, outs, comps, index, desc_dev
+        torch.cuda.empty_cache()
+        chk, base = oracle_check(wl, desc, p, pairs, sel, imgs, elig, got, sums, form, one_core=False,
+                                 cache=caches.setdefault(wname, {}))
+        out[key] = {"workload": wname, "images": wl.n_images, "pairs": P, "descriptors": wl.total_desc,
+                    "rerank": form, "budget_gb": budget_gb, "size_blk": size_blk, "block_rows": n_rows,
+                    "gps_iterations": n_iter, "match_launches": len(rows), "ms_per_step": ms,
+                    "value": P / (ms / 1e3), "unit": "pairs/s", "clocks": clk.summary(),
+                    "fp64_rechecks_per_step": int(st[0]), "fp8_top2_swaps_per_step": int(st[2]),
+                    "oracle": chk, "cpu_oracle_pairs_per_s": base["value"],
+                    "step": "one CUDA graph: rehash + per block row match + compaction, descriptors resident"}
+    return out
 
 
 def vlad_encoding(args, wl, desc_dev, host, stream, world, dev):
@@ -342,33 +631,56 @@ def vlad_encoding(args, wl, desc_dev, host, stream, world, dev):
             "codebook": "C rows sampled from the workload (seeded), a stand-in for k-means centroids"}
 
 
-def pipeline_e2e(args, wl, host, kp, sums, stream, world, dev):
-    """End to end through the public pipeline call (cm_run_schedule): per block
-    row, H2D of the row's new images from pinned host memory, hashing, one fused
-    match launch, compaction straight into pinned host memory, release of the
-    freed images.  Timed by the host clock around the call."""
+def pipeline_e2e(args, wl, host, kp, stream, world, dev):
+    """End to end through the public calls, timed by the host clock around the
+    whole job: the MBR schedule (cm_schedule_blocks, host), the index over its
+    arena, the centring statistics from the pinned host rows (cm_index_mean_host:
+    H2D through arena staging, exact column sums on the GPU), then
+    cm_run_schedule: per block row, H2D of the row's new images, hashing, one
+    fused match launch, compaction straight into pinned host memory, release
+    of the freed images."""
     import torch
     import paper_2505_22089_b300 as cm
     p = cm.Params.make(rerank=args.rerank, algo=args.algo, projection=args.projection, K=args.K)
-    sched = cm.schedule_blocks(wl.pairs, wl.n_desc, p, int(args.budget_gb * 2 ** 30), args.block_images)
-    index = cm.Index(p, wl.n_desc, arena_bytes=cm.schedule_arena_bytes(sched, p, wl.n_desc))
-    index.set_mean(sums, wl.total_desc, stream)
     off = wl.row_off
     hl = [host[off[i]:off[i + 1]] for i in range(wl.n_images)]
-    walls, stats = [], None
+    walls, parts, stats = [], [], None
     for s in range(args.e2e_steps + 1):
         if world > 1:
             torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sched = cm.schedule_blocks(wl.pairs, wl.n_desc, p, int(args.budget_gb * 2 ** 30), args.block_images)
+        t1 = time.perf_counter()
+        index = cm.Index(p, wl.n_desc, arena_bytes=cm.schedule_arena_bytes(sched, p, wl.n_desc))
+        index.mean_host(hl, stream)
+        stream.synchronize()
+        t2 = time.perf_counter()
         stats, _ = cm.run_schedule(index, sched, hl, verify=None, workers=1, stream=stream)
+        index.close()
+        sched.close()
+        del index
+        t3 = time.perf_counter()
         if s > 0:
-            walls.append(stats["wall_ms"])
+            walls.append((t3 - t0) * 1e3)
+            parts.append(((t1 - t0) * 1e3, (t2 - t1) * 1e3, stats["wall_ms"]))
     ms = _sync_ms(float(np.mean(walls)), world, dev)
+    pm = np.mean(parts, axis=0)
     out = {"value": len(wl.pairs) * world / (ms / 1e3), "unit": "pairs/s", "ms_per_step": ms,
-           "h2d_bytes_per_step": int(stats["h2d_bytes"]), "d2h_bytes_per_step": int(stats["d2h_bytes"]),
+           "h2d_bytes_per_step": int(stats["h2d_bytes"] + 128 * wl.total_desc),
+           "d2h_bytes_per_step": int(stats["d2h_bytes"]),
            "block_rows": stats["rows"], "kernels_per_step": int(stats["kernels"]),
-           "form": "cm_run_schedule, host descriptors (pinned) in, per-pair match lists (pinned host) out"}
+           "prefetched_rows": int(stats["prefetched_rows"]),
+           "parts_ms": {"schedule": round(float(pm[0]), 2), "index_and_centring": round(float(pm[1]), 2),
+                        "pipeline": round(float(pm[2]), 2)},
+           "form": "host clock around cm_schedule_blocks + cm_index_create + cm_index_mean_host (pinned host rows) "
+                   "+ cm_run_schedule (H2D of each row's images, hashing, match, compaction into pinned host "
+                   "memory); h2d counts the centring pass and the rows' loads"}
     ver = None
     if kp is not None and args.verify_workers > 0:
+        sched = cm.schedule_blocks(wl.pairs, wl.n_desc, p, int(args.budget_gb * 2 ** 30), args.block_images)
+        index = cm.Index(p, wl.n_desc, arena_bytes=cm.schedule_arena_bytes(sched, p, wl.n_desc))
+        index.mean_host(hl, stream)
         # outlier removal on the host workers, overlapped with the GPU rows:
         # RANSAC alone, then the SAO local constraint ahead of RANSAC (Sec. 2.3.3)
         kl = [kp[off[i]:off[i + 1]] for i in range(wl.n_images)]
@@ -391,8 +703,8 @@ def pipeline_e2e(args, wl, host, kp, sums, stream, world, dev):
                             "note": "matches counts the kept ones"}
             ver[mode] = v
         del kp_dev, kp_off_dev
-    index.close()
-    sched.close()
+        index.close()
+        sched.close()
     return out, ver
 
 
@@ -495,15 +807,23 @@ def run_ours(args, rank, world, local):
     # ---- device-resident steps (graph replay), every form
     forms = [args.rerank] + ([f for f in ("fp32", "int", "bf16", "fp8") if f != args.rerank]
                              if args.forms == "all" else [])
+    # the oracle's sample (rank 0 at N=1) and the exhaustive-NN sample: their GPU rows are kept
+    check = rank == 0 and world == 1 and args.oracle_frac > 0
+    sample = pick_sample(pairs, args.oracle_frac, args.oracle_min_pairs) if check else None
+    nn_sel = (np.sort(np.random.default_rng(123).choice(len(pairs), min(args.nn_pairs, len(pairs)), replace=False))
+              if args.nn_pairs > 0 else np.zeros(0, np.int64))
     desc_dev = host.to(dev, non_blocking=False)
-    fr = device_forms(args, wl, desc_dev, rows, stream, dev, world, forms)
+    fr = device_forms(args, wl, desc_dev, rows, stream, dev, world, forms,
+                      check=sample if sample is not None else (np.zeros(0, np.int64),) * 3, extra=nn_sel)
     head = fr[args.rerank]
-    gpu_rows, sums = head.pop("_gpu_rows"), head.pop("_sums")
+    got, sums = head.pop("_got"), head.pop("_sums")
+    head_p = head.pop("_p")
+    gpu_rows = {k: v[0] for k, v in got["full"].items()}
     vl = vlad_encoding(args, wl, desc_dev, host.numpy(), stream, world, dev) if args.vlad_codewords > 0 else None
     ceiling = sweep = None
     if args.nn_pairs > 0:
-        ceiling, sweep = exhaustive_leg(args, wl, desc_dev, host.numpy(), sums, pairs, gpu_rows, stream, world, dev,
-                                        float(peaks()[0].get("bf16_tflops", 1800.0)))
+        ceiling, sweep = exhaustive_leg(args, wl, desc_dev, host.numpy(), sums, pairs, nn_sel, gpu_rows, stream,
+                                        world, dev, float(peaks()[0].get("bf16_tflops", 1800.0)))
     del desc_dev
     torch.cuda.empty_cache()
     ms = head["ms_per_step"]
@@ -530,15 +850,18 @@ def run_ours(args, rank, world, local):
     # ---- end to end through the pipeline call, then the same with CPU verification overlapped
     e2e, verified = (None, None)
     if args.e2e_steps > 0:
-        e2e, verified = pipeline_e2e(args, wl, host, kp, sums, stream, world, dev)
+        e2e, verified = pipeline_e2e(args, wl, host, kp, stream, world, dev)
 
     # ---- plain per-pair form (no schedule): upload both images, hash, match, download, free
     plain = plain_per_pair(args, wl, host, sums, stream, dev) if args.plain_pairs > 0 else None
 
-    # ---- CPU oracle on a bounded sample (rank 0 at N=1): baseline and match agreement
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.oracle_pairs > 0:
-        cpu = cpu_baseline_and_agreement(args, wl, host.numpy(), sums, pairs, rows, gpu_rows)
+    # ---- the FP64 oracle on its sample (rank 0 at N=1): agreement, and the CPU baseline from its timing
+    cpu = base = None
+    if check:
+        cpu, base = oracle_check(wl, host.numpy(), head_p, pairs, *sample, got, sums, args.rerank)
+        cpu["fp64_rechecks_per_step"] = head["fp64_rechecks_per_step"]
+        cpu["fp8_top2_swaps_per_step"] = head["fp8_top2_swaps_per_step"]
+    del got
 
     forms_out = {}
     for f, r in fr.items():
@@ -562,6 +885,7 @@ def run_ours(args, rank, world, local):
         "plain_fp32_per_pair": plain,
         "pipeline_verified": verified,
         "schedules": schedule_comparison(args, wl, p, stream, world, dev) if world == 1 else None,
+        "configs": config_lines(args, stream, dev) if (world == 1 and args.configs == "all") else None,
         "gpu_launches": args.steps * head["graph_kernels"],
         "roofline": roofline,
         "vlad": vl,
@@ -570,7 +894,8 @@ def run_ours(args, rank, world, local):
         "clocks": head["clocks"],
     }
     if cpu is not None:
-        res["cpu_baseline"] = cpu.pop("cpu_baseline")
+        if not args.no_cpu_baseline:
+            res["cpu_baseline"] = base
         res["agreement"] = cpu
     return res, None
 
@@ -609,50 +934,19 @@ def plain_per_pair(args, wl, host, sums, stream, dev):
             "form": "per pair: upload 2 images (pinned host), hash, bucket, 1 match launch, download, free"}
 
 
-def cpu_baseline_and_agreement(args, wl, desc, sums, pairs, rows, gpu_rows):
-    """Times the FP64 oracle (as it stands) on a sample of pairs on all host
-    cores and compares its match sets with the GPU's on the same pairs."""
-    import oracle
-    cores = os.cpu_count() or 1
-    rng = np.random.default_rng(0)
-    sel = np.sort(rng.choice(len(pairs), min(args.oracle_pairs, len(pairs)), replace=False))
-    oix = oracle.Index(desc, wl.n_desc, oracle.Params(), threads=cores, sums=sums, n_total=wl.total_desc)
-    t0 = time.perf_counter()
-    res = oix.match(pairs[sel])
-    dt = time.perf_counter() - t0
-    inter = union = same = total = ng = no = 0
-    for k, o in zip(sel, res):
-        g = gpu_rows[int(k)]
-        same += int((g == o["best_j"]).sum())
-        total += len(g)
-        gm = set(zip(np.nonzero(g >= 0)[0].tolist(), g[g >= 0].tolist()))
-        om = set(zip(np.nonzero(o["best_j"] >= 0)[0].tolist(), o["best_j"][o["best_j"] >= 0].tolist()))
-        inter += len(gm & om)
-        union += len(gm | om)
-        ng += len(gm)
-        no += len(om)
-    return {"cpu_baseline": {"value": len(sel) / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-                             "sample": "%d of %d pairs, each: hash both images (FP64) + match; centring sums "
-                                       "given" % (len(sel), len(pairs))},
-            "pairs_checked": int(len(sel)), "match_set_jaccard": inter / union if union else 1.0,
-            "per_query_agreement": same / total if total else 1.0, "gpu_matches": ng, "oracle_matches": no}
-
-
 def recall_precision(g, ex):
     shared = int(((g == ex) & (g >= 0)).sum())
     n_ex, n_g = int((ex >= 0).sum()), int((g >= 0).sum())
     return shared, n_ex, n_g
 
 
-def exhaustive_leg(args, wl, desc_dev, host, sums, pairs, gpu_rows, stream, world, dev, peak_tflops):
+def exhaustive_leg(args, wl, desc_dev, host, sums, pairs, sel, gpu_rows, stream, world, dev, peak_tflops):
     """Quality ceiling and its cost: exhaustive nearest neighbours (cm_nn_pairs,
     tensor cores, exact) on a seeded sample of pairs, timed with CUDA events;
     the main run's cascade-hashing matches against them (recall = shared /
     exhaustive, precision = shared / cascade); then the L / K sweep."""
     import torch
     import paper_2505_22089_b300 as cm
-    rng = np.random.default_rng(123)
-    sel = np.sort(rng.choice(len(pairs), min(args.nn_pairs, len(pairs)), replace=False))
     sp = pairs[sel]
     with torch.cuda.stream(stream):
         best, _, _, rows = cm.nn_pairs(desc_dev, wl.n_desc, sp, stream=stream)   # warm-up, status checked

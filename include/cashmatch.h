@@ -197,9 +197,19 @@ cm_status cm_index_set_mean(cm_index* ix, const uint64_t* col_sums_host, uint64_
 /* Centring mean from the exact column sums of n_rows device descriptor rows
  * (async, on stream). */
 cm_status cm_index_mean_device(cm_index* ix, const uint8_t* d_desc, uint64_t n_rows, cm_stream stream);
+/* Centring mean of the whole index from host rows (the a2 statistics of an
+ * end-to-end run whose descriptors start in host memory): desc_host[i] points
+ * at image i's n_desc[i] rows (NULL allowed for an empty image).  The rows
+ * are copied through staging blocks taken from the free part of the arena
+ * (up to 2 x 64 MiB) and summed exactly in uint64 on the GPU (k_colsum_rows),
+ * then mu = sums / N.  Pinned host memory makes the copies asynchronous.
+ * Async on stream; the rows must stay valid until the stream is synchronised.
+ * Errors: CM_ERR_INVALID (NULL rows of a non-empty image, no rows at all),
+ * CM_ERR_BUDGET (not even 1 MiB of the arena free), CM_ERR_CUDA. */
+cm_status cm_index_mean_host(cm_index* ix, const uint8_t* const* desc_host, cm_stream stream);
 /* Exact column sums and row count behind the current centring mean, copied to
  * host (waits for stream).  Valid after cm_build_index, cm_index_mean_device,
- * cm_index_rehash or cm_index_set_mean. */
+ * cm_index_mean_host, cm_index_rehash or cm_index_set_mean. */
 cm_status cm_index_col_sums(cm_index* ix, uint64_t* sums_host, uint64_t* n_total, cm_stream stream);
 /* Makes images resident (async): copies their descriptors into the arena
  * (unless CM_MEM_DEVICE_INPLACE), computes keys and codes and builds the per
@@ -229,6 +239,8 @@ cm_status cm_build_index(const cm_params* p, int32_t n_images, const int32_t* n_
 cm_status cm_index_image_view(const cm_index* ix, int32_t image, const void** keys, const void** codes,
                               const void** sorted_codes, const void** sorted_idx, const void** offsets);
 void cm_index_destroy(cm_index* ix);
+/* The same as cm_index_destroy (the name the problem statement's interface uses). */
+void cm_free_index(cm_index* ix);
 
 /* ---- matching (Sec. 2.3.1 steps (1)-(4), one launch per block) ------------ */
 /* Arena bytes a plan of n_pairs pairs and `rows` query rows (the largest
@@ -296,9 +308,33 @@ cm_status cm_match_plan_sao(cm_match_plan* pl, const int32_t* d_best_in, int32_t
                             const int64_t* d_kp_off, int32_t k_nn, float max_score, float* d_score, void* d_work,
                             uint64_t work_bytes, cm_stream stream);
 void cm_match_plan_destroy(cm_match_plan* pl);
-/* Convenience: plan, run on stream, wait for the stream, destroy the plan. */
-cm_status cm_match_pairs(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, const cm_match_out* out,
-                         cm_stream stream);
+/* Device workspace (bytes) cm_match_pairs needs for this pair list: the pair
+ * table, the work counter and, for the BF16 / FP8 reranks, the top-K
+ * hand-over (as cm_plan_bytes).  Host only; the images need not be resident
+ * yet.  CM_ERR_INVALID for an image id out of range. */
+cm_status cm_match_pairs_workspace_bytes(const cm_index* ix, const cm_pair* pairs, int64_t n_pairs, uint64_t* bytes);
+/* Device workspace (bytes) that matching block row `block` of schedule s with
+ * cm_match_pairs takes (the row's pairs as the schedule holds them; the
+ * schedule keeps a copy of the pair list it was made from), or the largest
+ * over all rows when block = -1.  Host only.  Errors: CM_ERR_INVALID (block
+ * out of range, a pair naming an image the index does not have). */
+cm_status cm_index_workspace_bytes(const cm_index* ix, const cm_schedule* s, int32_t block, uint64_t* bytes);
+/* Matches a batch of pairs of resident images (Sec. 2.3.1 steps (1)-(4) for
+ * each query of image i against image j) in one fused launch (two for the
+ * BF16 / FP8 reranks), without taking anything from the index arena:
+ *  - pairs: host list; every image must be resident (CM_ERR_STATE otherwise).
+ *  - d_workspace / ws_bytes: caller-owned device memory, 256-byte aligned, at
+ *    least cm_match_pairs_workspace_bytes (CM_ERR_BUDGET otherwise).  It must
+ *    not be reused until the stream has run past this call.
+ *  - d_best_j (required when any query exists), d_d1sq, d_d2sq (optional):
+ *    caller-owned device outputs, one entry per query row, pair k's rows
+ *    starting at the sum of N_i over the pairs before it (as cm_match_out).
+ * Asynchronous on `stream`: the call returns once the work is enqueued; the
+ * inputs must stay valid and resident until the stream is synchronised.
+ * Errors: CM_ERR_INVALID (ids, i == j, NULL, misaligned workspace),
+ * CM_ERR_STATE, CM_ERR_BUDGET, CM_ERR_CUDA. */
+cm_status cm_match_pairs(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, void* d_workspace, uint64_t ws_bytes,
+                         int32_t* d_best_j, uint32_t* d_d1sq, uint32_t* d_d2sq, cm_stream stream);
 
 /* ---- captured block sequence (CUDA graph) -------------------------------- */
 /* Compaction outputs of one plan inside a sequence (see cm_match_plan_compact);
@@ -356,6 +392,7 @@ typedef struct cm_pipeline_stats {
     double verify_ms;        /* time spent inside the callback, summed over workers */
     double stall_ms;         /* host time spent waiting for a result buffer still held by verification */
     double tail_ms;          /* wall time after the last row's device work completed */
+    int64_t prefetched_rows; /* rows whose new images were copied during the previous row */
 } cm_pipeline_stats;
 
 /* Arena bytes for an index that runs schedule s (made from pairs[n_pairs])
@@ -502,6 +539,19 @@ cm_status cm_workspace_status(const void* d_work, cm_stream stream);
  * done.  CM_ERR_INVALID for polls out of range. */
 cm_status cm_selftest_wait(int32_t polls, cm_stream stream);
 
+/* Diagnostic: measured throughput of the integer operations the Hamming scan
+ * is made of, per clock per SM (the ALU roofline of the lookup kernel).  One
+ * CTA of 1024 threads per SM runs `iters` steps of 8 independent chains per
+ * thread and times them with the SM's clock64 counter (median over the
+ * CTAs).  kind: CM_PROBE_POPC (population counts), CM_PROBE_LOP3 (3-input
+ * logic ops), CM_PROBE_HAM4 (128-bit Hamming distances as 4 XOR + 4 POPC +
+ * adds), CM_PROBE_HAM3 (the same distances through a carry-save sum with 3
+ * POPC).  d_work: device scratch of >= SMs * (8 + 4096) bytes.  Blocks until
+ * done.  Errors: CM_ERR_INVALID, CM_ERR_BUDGET, CM_ERR_CUDA. */
+enum { CM_PROBE_POPC = 0, CM_PROBE_LOP3 = 1, CM_PROBE_HAM4 = 2, CM_PROBE_HAM3 = 3 };
+cm_status cm_probe_int(int32_t kind, int32_t iters, void* d_work, uint64_t work_bytes, cm_stream stream,
+                       double* per_clock_per_sm);
+
 /* ---- exhaustive nearest neighbours (quality ceiling) --------------------- */
 /* Device workspace of cm_nn_pairs for these images and pairs (it holds a BF16
  * operand copy of every database image the pairs name: 72 KB per 256 rows,
@@ -558,21 +608,32 @@ cm_status cm_autotune(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, const
  * allocate GPU memory (code running inside another framework's memory budget,
  * plug-ins of a host process that owns the device, real-time paths where an
  * allocation could block or fail).  It matches one pair, image i (queries)
- * against image j, with every step of Sec. 2.3.1 run on the GPU, and uses as
- * scratch only a file-scope device array of 5 MiB that every GPU which loads
- * this library holds until the process exits.
+ * against image j: hashing of both images into bucket keys and binary codes,
+ * their bucket tables, the Hamming top-K lookup, the exact rerank and the
+ * ratio test, all on the GPU.  Its only scratch is a file-scope device array
+ * of 5 MiB that every GPU which loads this library holds until the process
+ * exits; the call allocates nothing, on the device or through a library.
  *  - d_desc_i / d_desc_j: device uint8 [n][128] descriptor rows, at most 8,192
- *    per image (CM_ERR_BUDGET beyond, with a message); read in place.
+ *    per image (CM_ERR_BUDGET beyond, with a message); read in place.  An
+ *    empty database image (n_j = 0) gives no matches.
  *  - col_sums_host / n_total: the exact column sums and row count that define
- *    the centring mean (e.g. from cm_index_col_sums), host memory.
+ *    the centring mean (e.g. from cm_index_col_sums), host memory, read
+ *    before the call returns.
  *  - d_best_j (required), d_d1sq, d_d2sq (optional): device outputs of n_i
  *    rows, as in cm_match_out.
- *  - p->rerank must be CM_RERANK_FP32 or CM_RERANK_INT.
- * Async on stream.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the one array and it keeps the last call's
- * contents, so calls that overlap on the GPU (other streams or host threads)
- * race: serialise them. */
+ *  - p->rerank: CM_RERANK_FP32 or CM_RERANK_INT; p->projection: CM_PROJ_FFMA
+ *    only (the tensor-core projection needs a status word the call could not
+ *    report); p->algo: CM_ALGO_TILE or CM_ALGO_WARP as asked, CM_ALGO_AUTO the
+ *    tile mapping when its shared memory fits, else the warp mapping;
+ *    CM_ALGO_TC is rejected.  Other values give CM_ERR_INVALID.
+ * Async on stream: the per-call tables reach the array through set-up
+ * kernels that take them as kernel arguments, so the host does not wait.
+ * The first call on a device (and the first after a new CUDA context, e.g.
+ * after cudaDeviceReset) looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents (the
+ * call clears what must start at zero), so calls that overlap on the GPU
+ * (other streams or host threads) race: serialise them. */
 cm_status cm_match_pair_noalloc(const cm_params* p, const uint8_t* d_desc_i, int32_t n_i, const uint8_t* d_desc_j,
                                 int32_t n_j, const uint64_t* col_sums_host, uint64_t n_total, int32_t* d_best_j,
                                 uint32_t* d_d1sq, uint32_t* d_d2sq, cm_stream stream);

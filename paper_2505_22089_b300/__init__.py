@@ -55,6 +55,8 @@ EXPORTS = [
     "cm_verify_affine", "cm_affine_verify_cb", "cm_sao_filter", "cm_schedule_from_rows", "cm_vlad_workspace_bytes", "cm_vlad_encode",
     "cm_workspace_status", "cm_nn_workspace_bytes", "cm_nn_pairs", "cm_selftest_wait", "cm_match_plan_sao_bytes",
     "cm_match_plan_sao", "cm_pipeline_workspace_bytes_ex", "cm_run_schedule_ex", "cm_autotune", "cm_match_pair_noalloc",
+    "cm_match_pairs_workspace_bytes", "cm_index_workspace_bytes", "cm_free_index", "cm_index_mean_host",
+    "cm_probe_int",
 ]
 
 
@@ -97,7 +99,7 @@ class PipelineStats(ctypes.Structure):
                 ("queries", ctypes.c_int64), ("matches", ctypes.c_int64), ("kernels", ctypes.c_int64),
                 ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64), ("wall_ms", ctypes.c_double),
                 ("gpu_ms", ctypes.c_double), ("verify_ms", ctypes.c_double), ("stall_ms", ctypes.c_double),
-                ("tail_ms", ctypes.c_double)]
+                ("tail_ms", ctypes.c_double), ("prefetched_rows", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -174,7 +176,12 @@ def lib():
             "cm_match_plan_destroy": (None, [vp]),
             "cm_match_plan_compact": (i32, [vp, vp, vp, vp, vp, vp, u64, vp]),
             "cm_match_plan_mutual": (i32, [vp, vp, vp, vp]),
-            "cm_match_pairs": (i32, [vp, vp, i64, ctypes.POINTER(MatchOut), vp]),
+            "cm_match_pairs": (i32, [vp, vp, i64, vp, u64, vp, vp, vp, vp]),
+            "cm_match_pairs_workspace_bytes": (i32, [vp, vp, i64, ctypes.POINTER(u64)]),
+            "cm_index_workspace_bytes": (i32, [vp, vp, i32, ctypes.POINTER(u64)]),
+            "cm_free_index": (None, [vp]),
+            "cm_index_mean_host": (i32, [vp, vp, vp]),
+            "cm_probe_int": (i32, [i32, i32, vp, u64, vp, ctypes.POINTER(ctypes.c_double)]),
             "cm_match_pair_noalloc": (i32, [P, vp, i32, vp, i32, vp, u64, vp, vp, vp, vp]),
             "cm_sequence_create": (i32, [vp, i32, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]),
             "cm_sequence_launch": (i32, [vp, vp]),
@@ -388,6 +395,18 @@ def vlad_encode(desc, n_desc, codebook, stream=None, want_assign: bool = False, 
     return out, a
 
 
+PROBE = {"popc": 0, "lop3": 1, "ham4": 2, "ham3": 3}
+
+
+def probe_int(kind: str, iters: int = 4096, stream=None) -> float:
+    """cm_probe_int: measured operations (or 128-bit distances) per clock per SM."""
+    import torch
+    work = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    r = ctypes.c_double()
+    check(lib().cm_probe_int(PROBE[kind], int(iters), _ptr(work), work.numel(), _stream(stream), ctypes.byref(r)))
+    return float(r.value)
+
+
 def nn_pairs(desc, n_desc, pairs, ratio=(4, 5), stream=None, check_status: bool = True):
     """cm_nn_pairs: exhaustive nearest neighbours with the exact ratio test.
     desc: CUDA uint8 [n][128] (all images), n_desc: rows per image, pairs:
@@ -493,6 +512,36 @@ class Index:
         s = np.ascontiguousarray(sums, dtype=np.uint64)
         check(lib().cm_index_set_mean(self.h, s.ctypes.data, int(n_total), _stream(stream)))
 
+    def mean_host(self, descs, stream=None):
+        """cm_index_mean_host: the centring mean from every image's host rows
+        (descs[i]: uint8 [n_i][128] array or pinned CPU tensor), summed on the GPU."""
+        ptrs = (ctypes.c_void_p * len(descs))(*[d.data_ptr() if hasattr(d, "data_ptr") else
+                                                np.ascontiguousarray(d).ctypes.data for d in descs])
+        self._keep.append(descs)
+        check(lib().cm_index_mean_host(self.h, ptrs, _stream(stream)))
+
+    def workspace_bytes(self, sched, block: int = -1) -> int:
+        """cm_index_workspace_bytes: device bytes match_pairs needs for row `block` of sched (-1: any row)."""
+        b = ctypes.c_uint64()
+        check(lib().cm_index_workspace_bytes(self.h, sched.h, int(block), ctypes.byref(b)))
+        return int(b.value)
+
+    def match_pairs(self, pairs, workspace, best_j, d1sq=None, d2sq=None, stream=None):
+        """cm_match_pairs: one fused match launch over `pairs` (all resident),
+        asynchronous on the stream; `workspace` is a CUDA uint8 tensor of at
+        least match_pairs_bytes(pairs) + 256 bytes (aligned here)."""
+        pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        base = (workspace.data_ptr() + 255) // 256 * 256
+        ws = workspace.numel() - (base - workspace.data_ptr())
+        check(lib().cm_match_pairs(self.h, pr.ctypes.data, len(pr), ctypes.c_void_p(base), int(ws), _ptr(best_j),
+                                   _ptr(d1sq), _ptr(d2sq), _stream(stream)))
+
+    def match_pairs_bytes(self, pairs) -> int:
+        pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        b = ctypes.c_uint64()
+        check(lib().cm_match_pairs_workspace_bytes(self.h, pr.ctypes.data, len(pr), ctypes.byref(b)))
+        return int(b.value)
+
     def mean_device(self, desc, stream=None):
         check(lib().cm_index_mean_device(self.h, _ptr(desc), desc.shape[0], _stream(stream)))
 
@@ -546,6 +595,18 @@ class Index:
                 "sidx": device_to_numpy(ptrs[3].value, (L, n), np.uint16),
                 "off": device_to_numpy(ptrs[4].value, (L, B + 1), np.uint32)}
 
+    def image_bits(self, image: int):
+        """Copies of a resident image's keys (uint8 [n][L]) and codes (uint32 [n][4]) only."""
+        ptrs = [ctypes.c_void_p() for _ in range(2)]
+        check(lib().cm_index_image_view(self.h, image, ctypes.byref(ptrs[0]), ctypes.byref(ptrs[1]), None, None,
+                                        None))
+        n, L = int(self.n_desc[image]), self.p.L
+        if not n:
+            return np.zeros((0, L), np.uint8), np.zeros((0, 4), np.uint32)
+        keyw = device_to_numpy(ptrs[0].value, (n,), np.uint64)
+        keys = np.ascontiguousarray(keyw.view(np.uint8).reshape(n, 8)[:, :L])
+        return keys, device_to_numpy(ptrs[1].value, (n, 4), np.uint32)
+
     def close(self):
         for ref in getattr(self, "_plans", []):
             pl = ref()
@@ -565,11 +626,29 @@ class Index:
 def match_pair_noalloc(p: Params, desc_i, desc_j, col_sums, n_total: int, best_j, d1sq=None, d2sq=None,
                        stream=None):
     """cm_match_pair_noalloc: one pair matched with the library's static device
-    scratch only.  desc_i / desc_j and the outputs are CUDA tensors."""
+    scratch only.  desc_i / desc_j: contiguous CUDA uint8 [n][128]; best_j
+    (int32), d1sq, d2sq (4-byte, optional): CUDA tensors of at least n_i entries."""
+    import torch
+
+    def _rows(name, t):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.uint8 and t.dim() == 2
+                and t.shape[1] == 128 and t.is_contiguous()):
+            raise ValueError("%s must be a contiguous CUDA uint8 tensor of shape [n, 128]" % name)
+        return int(t.shape[0])
+
+    n_i, n_j = _rows("desc_i", desc_i), _rows("desc_j", desc_j)
+    for name, t, need in (("best_j", best_j, True), ("d1sq", d1sq, False), ("d2sq", d2sq, False)):
+        if t is None and not need:
+            continue
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.element_size() == 4 and t.is_contiguous()
+                and t.numel() >= n_i and (name != "best_j" or t.dtype == torch.int32)):
+            raise ValueError("%s must be a contiguous CUDA tensor of 4-byte entries (int32 for best_j) with at "
+                             "least %d entries" % (name, n_i))
     sums = np.ascontiguousarray(col_sums, dtype=np.uint64)
-    check(lib().cm_match_pair_noalloc(ctypes.byref(p), _ptr(desc_i), int(desc_i.shape[0]), _ptr(desc_j),
-                                      int(desc_j.shape[0]), sums.ctypes.data, int(n_total), _ptr(best_j),
-                                      _ptr(d1sq), _ptr(d2sq), _stream(stream)))
+    if sums.shape != (128,):
+        raise ValueError("col_sums must hold 128 column sums")
+    check(lib().cm_match_pair_noalloc(ctypes.byref(p), _ptr(desc_i), n_i, _ptr(desc_j), n_j, sums.ctypes.data,
+                                      int(n_total), _ptr(best_j), _ptr(d1sq), _ptr(d2sq), _stream(stream)))
 
 
 class MatchPlan:

@@ -261,6 +261,49 @@ extern "C" cm_status cm_index_mean_device(cm_index* ix, const uint8_t* d_desc, u
     return CM_OK;
 }
 
+extern "C" cm_status cm_index_mean_host(cm_index* ix, const uint8_t* const* desc_host, cm_stream stream) {
+    if (!ix || !desc_host) return fail(CM_ERR_INVALID, "cm_index_mean_host: bad argument");
+    uint64_t total = 0;
+    for (int i = 0; i < ix->n_images; ++i) {
+        if (ix->n_desc[i] && !desc_host[i]) return fail(CM_ERR_INVALID, "cm_index_mean_host: image %d has no rows", i);
+        total += (uint64_t)ix->n_desc[i];
+    }
+    if (!total) return fail(CM_ERR_INVALID, "cm_index_mean_host: the index has no rows");
+    // staging: the largest block of up to 64 MiB (a multiple of 128-byte rows) the arena has free
+    uint64_t chunk = std::min<uint64_t>(64ull << 20, align_up(total * kDim)), at = 0;
+    while (chunk >= (1ull << 20) && !ix->alloc.alloc(chunk, &at)) chunk /= 2;
+    if (chunk < (1ull << 20)) return fail(CM_ERR_BUDGET, "cm_index_mean_host: no 1 MiB of the arena is free");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t* stage = ix->arena + at;
+    const uint64_t rows_per_chunk = chunk / kDim;
+    unsigned long long* sums = ix->at<unsigned long long>(ix->fx.sums);
+    cudaError_t e = cudaMemsetAsync(sums, 0, kDim * 8, s);
+    // fill the staging block with consecutive rows (image segments), then sum it
+    uint64_t fill = 0;
+    for (int i = 0; i < ix->n_images && e == cudaSuccess; ++i) {
+        uint64_t done = 0, n = (uint64_t)ix->n_desc[i];
+        while (done < n && e == cudaSuccess) {
+            const uint64_t take = std::min(n - done, rows_per_chunk - fill);
+            e = cudaMemcpyAsync(stage + fill * kDim, desc_host[i] + done * kDim, take * kDim, cudaMemcpyHostToDevice, s);
+            fill += take;
+            done += take;
+            if (fill == rows_per_chunk && e == cudaSuccess) {
+                e = launch_colsum_rows(stage, fill, sums, s);
+                fill = 0;
+            }
+        }
+    }
+    if (fill && e == cudaSuccess) e = launch_colsum_rows(stage, fill, sums, s);
+    if (e == cudaSuccess) e = launch_mean(sums, nullptr, total, ix->at<float>(ix->fx.mu), s);
+    // later work on this stream is ordered after the sums: the block may be placed again at once
+    ix->alloc.release(at);
+    if (e != cudaSuccess) return fail(CM_ERR_CUDA, "cm_index_mean_host: %s", cudaGetErrorString(e));
+    ix->mean_set = true;
+    ix->sums_on_host = false;
+    ix->n_total = total;
+    return CM_OK;
+}
+
 // Allocate slots, copy descriptors, refresh the device image table and the
 // load-batch table.  Returns the batch's hash-tile count.
 // Loading an image has three phases: placing its slot in the arena, copying
@@ -592,11 +635,11 @@ extern "C" cm_status cm_index_image_view(const cm_index* ix, int32_t image, cons
 // ---------------------------------------------------------------------------
 // match plans
 // ---------------------------------------------------------------------------
-extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, cm_stream stream,
-                                          cm_match_plan** out) {
-    if (!ix || !out || n_pairs < 0 || (n_pairs && !pairs)) return fail(CM_ERR_INVALID, "plan: bad argument");
-    const int S = query_tile(&ix->p);
-    std::vector<DevPair> tab((size_t)n_pairs);
+// Validates a pair list and fills its work table.  Returns the plan's device
+// bytes (cm_plan_bytes) and its row / item counts.
+static cm_status plan_table(const cm_index* ix, const cm_pair* pairs, int64_t n_pairs, int S, std::vector<DevPair>& tab,
+                            int64_t* rows_out, int64_t* items_out, int32_t* max_ni_out) {
+    tab.assign((size_t)n_pairs, DevPair{});
     int64_t rows = 0, items = 0;
     int32_t max_ni = 0;
     for (int64_t k = 0; k < n_pairs; ++k) {
@@ -627,6 +670,21 @@ extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, in
             tab[k].rev = it == first.end() ? -1 : (int32_t)it->second;
         }
     }
+    *rows_out = rows;
+    *items_out = items;
+    *max_ni_out = max_ni;
+    return CM_OK;
+}
+
+extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, cm_stream stream,
+                                          cm_match_plan** out) {
+    if (!ix || !out || n_pairs < 0 || (n_pairs && !pairs)) return fail(CM_ERR_INVALID, "plan: bad argument");
+    const int S = query_tile(&ix->p);
+    std::vector<DevPair> tab;
+    int64_t rows = 0, items = 0;
+    int32_t max_ni = 0;
+    cm_status st0 = plan_table(ix, pairs, n_pairs, S, tab, &rows, &items, &max_ni);
+    if (st0 != CM_OK) return st0;
     cm_match_plan* pl = new (std::nothrow) cm_match_plan();
     if (!pl) return fail(CM_ERR_NOMEM, "plan: host allocation");
     const uint64_t bytes = plan_bytes(&ix->p, n_pairs, rows, max_ni);
@@ -676,12 +734,12 @@ extern "C" cm_status cm_match_plan_run_marked(cm_match_plan* pl, const cm_match_
         if (mark) CM_CUDA(cudaEventRecord(mark, s));
         return CM_OK;
     }
-    const uint64_t counter_at = pl->table_at + align_up((uint64_t)pl->n_pairs * sizeof(DevPair));
-    unsigned* counter = reinterpret_cast<unsigned*>(ix->arena + counter_at);
+    uint8_t* counter_ptr = pl->base() + align_up((uint64_t)pl->n_pairs * sizeof(DevPair));
+    unsigned* counter = reinterpret_cast<unsigned*>(counter_ptr);
     CM_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
     MatchLaunch m{};
     m.imgs = ix->at<DevImage>(ix->fx.imgs);
-    m.pairs = reinterpret_cast<const DevPair*>(ix->arena + pl->table_at);
+    m.pairs = reinterpret_cast<const DevPair*>(pl->base());
     m.n_pairs = (int32_t)pl->n_pairs;
     m.n_items = pl->n_items;
     const cm_params& pp = pl->p;
@@ -700,7 +758,7 @@ extern "C" cm_status cm_match_plan_run_marked(cm_match_plan* pl, const cm_match_
     if (needs_hand_over(&pp)) {
         // a scan leaves each query's top-K in the plan's hand-over area, then a rerank launch
         const HandOver ho = hand_over(&pp, pl->rows, pl->max_ni);
-        uint8_t* base = ix->arena + counter_at + kAlign;
+        uint8_t* base = counter_ptr + kAlign;
         m.topk16 = reinterpret_cast<uint16_t*>(base + ho.idx);
         m.hnorm = reinterpret_cast<uint32_t*>(base + ho.norm);
         m.hscale = pp.rerank == CM_RERANK_FP8 ? reinterpret_cast<float*>(base + ho.scale) : nullptr;
@@ -728,7 +786,7 @@ extern "C" cm_status cm_match_plan_compact(cm_match_plan* pl, const int32_t* d_b
     if (!pl || !d_best_j || !d_counts || !d_offsets) return fail(CM_ERR_INVALID, "compact: bad argument");
     if (!pl->ix) return fail(CM_ERR_STATE, "compact: the plan's index was destroyed");
     cm_index* ix = pl->ix;
-    CM_CUDA(launch_compact(reinterpret_cast<const DevPair*>(ix->arena + pl->table_at), (int)pl->n_pairs,
+    CM_CUDA(launch_compact(reinterpret_cast<const DevPair*>(pl->base()), (int)pl->n_pairs,
                            ix->at<DevImage>(ix->fx.imgs), d_best_j, d_counts,
                            reinterpret_cast<unsigned long long*>(d_offsets), reinterpret_cast<unsigned long long*>(d_total),
                            d_matches, (unsigned long long)capacity, reinterpret_cast<cudaStream_t>(stream)));
@@ -741,7 +799,7 @@ extern "C" cm_status cm_match_plan_mutual(cm_match_plan* pl, const int32_t* d_be
         return fail(CM_ERR_INVALID, "mutual: bad argument (in and out must differ)");
     if (!pl->ix) return fail(CM_ERR_STATE, "mutual: the plan's index was destroyed");
     cm_index* ix = pl->ix;
-    CM_CUDA(launch_mutual(reinterpret_cast<const DevPair*>(ix->arena + pl->table_at), (int)pl->n_pairs,
+    CM_CUDA(launch_mutual(reinterpret_cast<const DevPair*>(pl->base()), (int)pl->n_pairs,
                           ix->at<DevImage>(ix->fx.imgs), d_best_in, d_best_out, reinterpret_cast<cudaStream_t>(stream)));
     return CM_OK;
 }
@@ -766,15 +824,92 @@ extern "C" void cm_index_destroy(cm_index* ix) {
     delete ix;
 }
 
-extern "C" cm_status cm_match_pairs(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, const cm_match_out* out,
-                                    cm_stream stream) {
-    cm_match_plan* pl = nullptr;
-    cm_status st = cm_match_plan_create(ix, pairs, n_pairs, stream, &pl);
-    if (st != CM_OK) return st;
-    st = cm_match_plan_run(pl, out, stream);
-    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
-    cm_match_plan_destroy(pl);
-    if (st != CM_OK) return st;
-    if (e != cudaSuccess) return fail(CM_ERR_CUDA, "cm_match_pairs: %s", cudaGetErrorString(e));
+// Device bytes cm_match_pairs needs for a pair list (sizes only; residency is
+// checked by the call itself).
+static cm_status pairs_bytes(const cm_index* ix, const cm_pair* pairs, int64_t n_pairs, uint64_t* bytes) {
+    int64_t rows = 0;
+    int32_t max_ni = 0;
+    for (int64_t k = 0; k < n_pairs; ++k) {
+        const int i = pairs[k].i;
+        if (i < 0 || i >= ix->n_images || pairs[k].j < 0 || pairs[k].j >= ix->n_images)
+            return fail(CM_ERR_INVALID, "workspace: pair %lld has an image id out of range", (long long)k);
+        rows += ix->n_desc[i];
+        max_ni = std::max(max_ni, ix->n_desc[i]);
+    }
+    *bytes = plan_bytes(&ix->p, n_pairs, rows, max_ni);
     return CM_OK;
 }
+
+extern "C" cm_status cm_match_pairs_workspace_bytes(const cm_index* ix, const cm_pair* pairs, int64_t n_pairs,
+                                                    uint64_t* bytes) {
+    if (!ix || !bytes || n_pairs < 0 || (n_pairs && !pairs))
+        return fail(CM_ERR_INVALID, "cm_match_pairs_workspace_bytes: bad argument");
+    return pairs_bytes(ix, pairs, n_pairs, bytes);
+}
+
+extern "C" cm_status cm_index_workspace_bytes(const cm_index* ix, const cm_schedule* s, int32_t block,
+                                              uint64_t* bytes) {
+    if (!ix || !s || !bytes) return fail(CM_ERR_INVALID, "cm_index_workspace_bytes: bad argument");
+    const int32_t R = cm_schedule_num_rows(s);
+    if (block < -1 || block >= R) return fail(CM_ERR_INVALID, "cm_index_workspace_bytes: block %d of %d", block, R);
+    int64_t n_all = 0;
+    const cm_pair* all = schedule_pairs(s, &n_all);
+    uint64_t most = 0;
+    for (int32_t r = (block < 0 ? 0 : block); r < (block < 0 ? R : block + 1); ++r) {
+        cm_schedule_row row{};
+        cm_status st = cm_schedule_get_row(s, r, &row);
+        if (st != CM_OK) return st;
+        std::vector<cm_pair> rp((size_t)row.n_pairs);
+        for (int64_t k = 0; k < row.n_pairs; ++k) {
+            if (row.pairs[k] < 0 || row.pairs[k] >= n_all)
+                return fail(CM_ERR_INVALID, "cm_index_workspace_bytes: row %d names pair %lld", r,
+                            (long long)row.pairs[k]);
+            rp[k] = all[row.pairs[k]];
+        }
+        uint64_t b = 0;
+        if ((st = pairs_bytes(ix, rp.data(), row.n_pairs, &b)) != CM_OK) return st;
+        most = std::max(most, b);
+    }
+    *bytes = most;
+    return CM_OK;
+}
+
+extern "C" cm_status cm_match_pairs(cm_index* ix, const cm_pair* pairs, int64_t n_pairs, void* d_workspace,
+                                    uint64_t ws_bytes, int32_t* d_best_j, uint32_t* d_d1sq, uint32_t* d_d2sq,
+                                    cm_stream stream) {
+    if (!ix || n_pairs < 0 || (n_pairs && !pairs)) return fail(CM_ERR_INVALID, "cm_match_pairs: bad argument");
+    if (!d_workspace || reinterpret_cast<uintptr_t>(d_workspace) % kAlign)
+        return fail(CM_ERR_INVALID, "cm_match_pairs: the workspace must be a 256-byte aligned device pointer");
+    const int S = query_tile(&ix->p);
+    std::vector<DevPair> tab;
+    int64_t rows = 0, items = 0;
+    int32_t max_ni = 0;
+    cm_status st = plan_table(ix, pairs, n_pairs, S, tab, &rows, &items, &max_ni);
+    if (st != CM_OK) return st;
+    if (rows && !d_best_j) return fail(CM_ERR_INVALID, "cm_match_pairs: d_best_j is NULL");
+    const uint64_t need = plan_bytes(&ix->p, n_pairs, rows, max_ni);
+    if (ws_bytes < need)
+        return fail(CM_ERR_BUDGET, "cm_match_pairs: workspace of %llu bytes, %llu needed", (unsigned long long)ws_bytes,
+                    (unsigned long long)need);
+    // a plan whose table lives in the caller's workspace: nothing of the arena
+    // is taken, so the call returns as soon as the launches are enqueued
+    cm_match_plan pl;
+    pl.ix = ix;
+    pl.p = ix->p;
+    pl.S = S;
+    pl.ext = static_cast<uint8_t*>(d_workspace);
+    pl.n_pairs = n_pairs;
+    pl.rows = rows;
+    pl.n_items = (int32_t)items;
+    pl.max_ni = max_ni;
+    if (n_pairs)
+        CM_CUDA(ix->staging.upload(pl.ext, tab.data(), tab.size() * sizeof(DevPair),
+                                   reinterpret_cast<cudaStream_t>(stream)));
+    cm_match_out out{};
+    out.best_j = d_best_j;
+    out.d1sq = d_d1sq;
+    out.d2sq = d_d2sq;
+    return cm_match_plan_run(&pl, &out, stream);
+}
+
+extern "C" void cm_free_index(cm_index* ix) { cm_index_destroy(ix); }

@@ -273,6 +273,8 @@ cm_status index_publish(cm_index* ix, int32_t count, const int32_t* ids, cudaStr
 void index_cancel_prefetch(cm_index* ix, int32_t count, const int32_t* ids);
 // Device workspace of cm_match_plan_sao for a plan of n_pairs pairs and rows query rows.
 uint64_t sao_work_bytes(int64_t n_pairs, int64_t rows);
+// The pair list a schedule was made from (cm_sched.cpp); valid while the schedule lives.
+const cm_pair* schedule_pairs(const cm_schedule* s, int64_t* n);
 }  // namespace cm
 
 // Arena bytes of a plan: its pair table, the work counter and, for the
@@ -313,6 +315,9 @@ struct cm_match_plan {
     int32_t n_items = 0;
     int32_t max_ni = 0;      // largest query image of the plan
     bool reserved = false;   // placed in the index's reserved plan block
+    uint8_t* ext = nullptr;  // caller's workspace holding the table instead of the arena (cm_match_pairs)
+    // device address of the plan's table (then the work counter and the hand-over)
+    uint8_t* base() const { return ext ? ext : ix->arena + table_at; }
 };
 
 

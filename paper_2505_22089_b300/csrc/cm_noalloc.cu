@@ -8,11 +8,17 @@
 // tables, the work counter - lives in one file-scope device array of
 // kNoAllocBytes that every GPU which loads this library keeps until the
 // process exits.  The caller passes only its inputs and outputs.
+//
+// The small tables reach the array through set-up kernels that take them as
+// kernel arguments (copied at launch), so no host buffer of this call has to
+// outlive it and the host never waits for the stream.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "cm_internal.h"
 
@@ -25,12 +31,9 @@ using namespace cm;
 constexpr int kNoAllocMaxDesc = 8192;              // descriptors per image
 constexpr size_t kNoAllocBytes = size_t(5) << 20;  // 5 MiB of device scratch
 constexpr int kMaxDevices = 64;
+constexpr int kWChunk = 7680;                      // weights per set-up launch (30 KB of kernel arguments)
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-
-std::mutex g_setup_mu;
-unsigned char* g_scratch_ptr[kMaxDevices] = {};    // device address of the array, per device
-float g_w_host[kDim * kMaxP];                      // host staging of the weights (under g_setup_mu)
 
 constexpr uint64_t kA = 256;
 inline uint64_t up(uint64_t v) { return (v + kA - 1) / kA * kA; }
@@ -68,7 +71,95 @@ Layout layout(const cm_params* p, const int n[2]) {
     return g;
 }
 
+// A slice of the weight matrix, passed by value.
+struct WChunk {
+    uint32_t at;     // byte offset in the array
+    uint32_t count;  // floats
+    float w[kWChunk];
+};
+
+// The per-call tables, passed by value, and the regions to clear.
+struct Tables {
+    Layout g;
+    float mu[kDim];
+    DevImage img[2];
+    int32_t batch[2];
+    int32_t tiles[3];
+    DevPair pair;
+    uint32_t hist_words;  // per image: L * 2^m bucket counts to zero
+};
+
+__global__ void k_noalloc_weights(WChunk c) {
+    float* dst = reinterpret_cast<float*>(g_noalloc_scratch + c.at);
+    for (uint32_t k = threadIdx.x; k < c.count; k += blockDim.x) dst[k] = c.w[k];
+}
+
+__global__ void k_noalloc_tables(Tables t) {
+    unsigned char* a = g_noalloc_scratch;
+    const int tid = threadIdx.x;
+    for (int k = tid; k < kDim; k += blockDim.x) reinterpret_cast<float*>(a + t.g.mu)[k] = t.mu[k];
+    if (tid < 2) {
+        reinterpret_cast<DevImage*>(a + t.g.imgs)[tid] = t.img[tid];
+        reinterpret_cast<int32_t*>(a + t.g.batch)[tid] = t.batch[tid];
+    }
+    if (tid < 3) reinterpret_cast<int32_t*>(a + t.g.tiles)[tid] = t.tiles[tid];
+    if (tid == 0) {
+        *reinterpret_cast<DevPair*>(a + t.g.pair) = t.pair;
+        *reinterpret_cast<unsigned*>(a + t.g.counter) = 0u;   // the work counter starts at zero
+    }
+    // the array keeps the previous call's contents: bucket counts must start at zero
+    for (int k = 0; k < 2; ++k)
+        for (uint32_t w = tid; w < t.hist_words; w += blockDim.x) reinterpret_cast<uint32_t*>(a + t.g.hist[k])[w] = 0u;
+}
+
 cm_status fail(cm_status st, const char* msg) { return cm_internal_fail(st, msg); }
+
+// Set-up of the array's device address, once per device and CUDA context: a
+// context created after cudaDeviceReset holds a new copy of the array, which
+// gets its own set-up.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+std::mutex g_setup_mu;
+struct DevSetup {
+    unsigned long long ctx_id = 0;
+    unsigned char* ptr = nullptr;
+};
+DevSetup g_setup[kMaxDevices];
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_entry_looked_up = false;
+
+cm_status scratch_address(int dev, unsigned char** out) {
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    if (!g_entry_looked_up) {
+        g_entry_looked_up = true;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+            g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
+        }
+    }
+    unsigned long long id = 0;
+    CUcontext ctx = nullptr;
+    const bool have_id = g_ctx_current && g_ctx_id && g_ctx_current(&ctx) == CUDA_SUCCESS && ctx &&
+                         g_ctx_id(ctx, &id) == CUDA_SUCCESS;
+    DevSetup& d = g_setup[dev];
+    if (!d.ptr || !have_id || d.ctx_id != id) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return fail(CM_ERR_CUDA, "cm_match_pair_noalloc: cudaGetSymbolAddress failed");
+        d.ptr = static_cast<unsigned char*>(ptr);
+        d.ctx_id = have_id ? id : 0;
+    }
+    *out = d.ptr;
+    return CM_OK;
+}
 
 }  // namespace
 
@@ -80,6 +171,10 @@ extern "C" cm_status cm_match_pair_noalloc(const cm_params* p, const uint8_t* d_
     if (st != CM_OK) return st;
     if (p->rerank != CM_RERANK_FP32 && p->rerank != CM_RERANK_INT)
         return fail(CM_ERR_INVALID, "cm_match_pair_noalloc: only the FP32 and INT reranks are available");
+    if (p->projection != CM_PROJ_FFMA)
+        return fail(CM_ERR_INVALID, "cm_match_pair_noalloc: only the FP32 FFMA projection (CM_PROJ_FFMA) is available");
+    if (p->algo == CM_ALGO_TC)
+        return fail(CM_ERR_INVALID, "cm_match_pair_noalloc: the tensor-core scan needs a hand-over area; use TILE or WARP");
     if (n_i < 0 || n_j < 0 || n_i > kNoAllocMaxDesc || n_j > kNoAllocMaxDesc)
         return fail(CM_ERR_BUDGET, "cm_match_pair_noalloc: images are limited to 8192 descriptors each");
     if ((n_i && !d_desc_i) || (n_j && !d_desc_j) || !col_sums_host || !n_total || (n_i && !d_best_j))
@@ -88,88 +183,81 @@ extern "C" cm_status cm_match_pair_noalloc(const cm_params* p, const uint8_t* d_
     const Layout g = layout(p, n);
     if (g.total > kNoAllocBytes)
         return fail(CM_ERR_BUDGET, "cm_match_pair_noalloc: parameters need more than the 5 MiB scratch");
+    const int S = p->query_tile ? p->query_tile : kDefaultQueryTile;
+    const bool tile = p->algo != CM_ALGO_WARP && match_smem_bytes(S, p->K) <= kMatchSmemLimit;
+    if (p->algo == CM_ALGO_TILE && !tile)
+        return fail(CM_ERR_INVALID, "cm_match_pair_noalloc: the tile mapping's shared memory does not fit this query tile");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
-    // set-up, once per device: the device address of the scratch array
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return fail(CM_ERR_CUDA, "cm_match_pair_noalloc: no current device");
     unsigned char* base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_setup_mu);
-        if (!g_scratch_ptr[dev]) {
-            void* ptr = nullptr;
-            const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess || !ptr) return fail(CM_ERR_CUDA, "cm_match_pair_noalloc: cudaGetSymbolAddress failed");
-            g_scratch_ptr[dev] = static_cast<unsigned char*>(ptr);
-        }
-        base = g_scratch_ptr[dev];
-    }
+    if ((st = scratch_address(dev, &base)) != CM_OK) return st;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 
-    // small tables are copied from host memory of this call (pageable copies
-    // are staged by the driver before cudaMemcpyAsync returns)
+    // weights W[128][P] with P_pad columns (zero padded), written by value in slices
     const int P = p->L * p->m + p->n_bits, P_pad = (P + 15) / 16 * 16;
-    float mu[kDim];
-    for (int k = 0; k < kDim; ++k) mu[k] = (float)((double)col_sums_host[k] / (double)n_total);
-    DevImage img[2];
+    std::vector<float> W((size_t)kDim * P), Wp((size_t)kDim * P_pad, 0.f);
+    cm_make_weights(p, W.data());
+    for (int k = 0; k < kDim; ++k)
+        for (int h = 0; h < P; ++h) Wp[(size_t)k * P_pad + h] = W[(size_t)k * P + h];
+    cudaError_t e = cudaSuccess;
+    {
+        WChunk c;
+        for (size_t f0 = 0; f0 < Wp.size() && e == cudaSuccess; f0 += kWChunk) {
+            c.at = (uint32_t)(g.W + f0 * 4);
+            c.count = (uint32_t)std::min<size_t>(kWChunk, Wp.size() - f0);
+            std::memcpy(c.w, Wp.data() + f0, c.count * 4);
+            k_noalloc_weights<<<1, 256, 0, s>>>(c);
+            e = cudaGetLastError();
+        }
+    }
+    Tables t{};
+    t.g = g;
+    for (int k = 0; k < kDim; ++k) t.mu[k] = (float)((double)col_sums_host[k] / (double)n_total);
     const uint8_t* descs[2] = {d_desc_i, d_desc_j};
     for (int k = 0; k < 2; ++k) {
-        img[k] = DevImage{};
-        img[k].desc = descs[k];
-        img[k].key = reinterpret_cast<uint64_t*>(base + g.key[k]);
-        img[k].code = reinterpret_cast<uint4*>(base + g.code[k]);
-        img[k].scode = reinterpret_cast<uint4*>(base + g.scode[k]);
-        img[k].sidx = reinterpret_cast<uint16_t*>(base + g.sidx[k]);
-        img[k].off = reinterpret_cast<uint32_t*>(base + g.off[k]);
-        img[k].hist = reinterpret_cast<uint32_t*>(base + g.hist[k]);
-        img[k].brank = base + g.brank[k];
-        img[k].norm = reinterpret_cast<uint32_t*>(base + g.norm[k]);
-        img[k].n = n[k];
+        DevImage& im = t.img[k];
+        im = DevImage{};
+        im.desc = descs[k];
+        im.key = reinterpret_cast<uint64_t*>(base + g.key[k]);
+        im.code = reinterpret_cast<uint4*>(base + g.code[k]);
+        im.scode = reinterpret_cast<uint4*>(base + g.scode[k]);
+        im.sidx = reinterpret_cast<uint16_t*>(base + g.sidx[k]);
+        im.off = reinterpret_cast<uint32_t*>(base + g.off[k]);
+        im.hist = reinterpret_cast<uint32_t*>(base + g.hist[k]);
+        im.brank = base + g.brank[k];
+        im.norm = reinterpret_cast<uint32_t*>(base + g.norm[k]);
+        im.n = n[k];
     }
-    const int32_t batch[2] = {0, 1};
-    const int32_t tiles[3] = {0, (n_i + kHashTile - 1) / kHashTile,
-                              (n_i + kHashTile - 1) / kHashTile + (n_j + kHashTile - 1) / kHashTile};
-    const int S = p->query_tile ? p->query_tile : kDefaultQueryTile;
-    DevPair pair{};
-    pair.i = 0;
-    pair.j = 1;
-    pair.row_off = 0;
-    pair.item0 = 0;
-    pair.nitems = (n_i + S - 1) / S;
-    pair.ni = n_i;
-    pair.rev = -1;
-
-    cudaError_t e = cudaSuccess;
-    auto h2d = [&](uint64_t off, const void* src, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMemcpyAsync(base + off, src, bytes, cudaMemcpyHostToDevice, s);
-    };
-    {
-        // weights W[128][P] laid out with P_pad columns (zero padded), then copied
-        std::lock_guard<std::mutex> lock(g_setup_mu);
-        cm_make_weights(p, g_w_host);
-        for (int k = kDim - 1; k >= 0; --k)
-            for (int h = P_pad - 1; h >= 0; --h) g_w_host[k * P_pad + h] = h < P ? g_w_host[k * P + h] : 0.f;
-        h2d(g.W, g_w_host, (size_t)kDim * P_pad * 4);
+    t.batch[0] = 0;
+    t.batch[1] = 1;
+    t.tiles[0] = 0;
+    t.tiles[1] = (n_i + kHashTile - 1) / kHashTile;
+    t.tiles[2] = t.tiles[1] + (n_j + kHashTile - 1) / kHashTile;
+    t.pair = DevPair{};
+    t.pair.i = 0;
+    t.pair.j = 1;
+    t.pair.row_off = 0;
+    t.pair.item0 = 0;
+    t.pair.nitems = (n_i + S - 1) / S;
+    t.pair.ni = n_i;
+    t.pair.rev = -1;
+    t.hist_words = (uint32_t)(p->L << p->m);
+    if (e == cudaSuccess) {
+        k_noalloc_tables<<<1, 256, 0, s>>>(t);
+        e = cudaGetLastError();
     }
-    h2d(g.mu, mu, sizeof mu);
-    h2d(g.imgs, img, sizeof img);
-    h2d(g.batch, batch, sizeof batch);
-    h2d(g.tiles, tiles, sizeof tiles);
-    h2d(g.pair, &pair, sizeof pair);
-    // the array keeps the previous call's contents: clear the bucket counts and the work counter
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
-        e = cudaMemsetAsync(base + g.hist[k], 0, (size_t)p->L * (1u << p->m) * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + g.counter, 0, 4, s);
-    if (e != cudaSuccess) return fail(CM_ERR_CUDA, "cm_match_pair_noalloc: copy to scratch failed");
+    if (e != cudaSuccess) return fail(CM_ERR_CUDA, "cm_match_pair_noalloc: set-up launch failed");
 
     HashLaunch h{};
     h.imgs = reinterpret_cast<const DevImage*>(base + g.imgs);
     h.batch = reinterpret_cast<const int32_t*>(base + g.batch);
     h.tile_pref = reinterpret_cast<const int32_t*>(base + g.tiles);
     h.n_batch = 2;
-    h.n_tiles = tiles[2];
+    h.n_tiles = t.tiles[2];
     h.W = reinterpret_cast<const float*>(base + g.W);
     h.mu = reinterpret_cast<const float*>(base + g.mu);
     h.L = p->L;
@@ -180,12 +268,12 @@ extern "C" cm_status cm_match_pair_noalloc(const cm_params* p, const uint8_t* d_
         e = launch_hash(h, sms, s);
         if (e == cudaSuccess) e = launch_bucket(h, s);
     }
-    if (e == cudaSuccess && pair.nitems > 0) {
+    if (e == cudaSuccess && t.pair.nitems > 0) {
         MatchLaunch m{};
         m.imgs = h.imgs;
         m.pairs = reinterpret_cast<const DevPair*>(base + g.pair);
         m.n_pairs = 1;
-        m.n_items = pair.nitems;
+        m.n_items = t.pair.nitems;
         m.S = S;
         m.L = p->L;
         m.m = p->m;
@@ -193,12 +281,12 @@ extern "C" cm_status cm_match_pair_noalloc(const cm_params* p, const uint8_t* d_
         m.ratio_num = p->ratio_num;
         m.ratio_den = p->ratio_den;
         m.rerank = p->rerank;
-        m.algo = CM_ALGO_WARP;
+        m.algo = tile ? CM_ALGO_TILE : CM_ALGO_WARP;
         m.counter = reinterpret_cast<unsigned*>(base + g.counter);
         m.out.best_j = d_best_j;
         m.out.d1sq = d_d1sq;
         m.out.d2sq = d_d2sq;
-        e = launch_match_wq(m, sms, s);
+        e = tile ? launch_match(m, sms, s) : launch_match_wq(m, sms, s);
     }
     if (e != cudaSuccess) return fail(CM_ERR_CUDA, "cm_match_pair_noalloc: kernel launch failed");
     return CM_OK;

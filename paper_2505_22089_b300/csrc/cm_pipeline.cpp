@@ -693,6 +693,7 @@ extern "C" cm_status cm_run_schedule_ex(cm_index* ix, const cm_schedule* s, cons
                 S.h2d_bytes += (uint64_t)ix->n_desc[row.load[k]] * kDim;
             }
             if (prefetched[r]) {   // copied during the previous row: make resident and hash
+                S.prefetched_rows++;
                 if (cudaStreamWaitEvent(cs, ev_copied[r], 0) != cudaSuccess) {
                     fail(CM_ERR_CUDA, "cm_run_schedule: stream wait");
                     return bail(CM_ERR_CUDA);

@@ -438,7 +438,7 @@ extern "C" cm_status cm_match_plan_sao(cm_match_plan* pl, const int32_t* d_best_
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cm_index* ix = pl->ix;
     unsigned char* base = static_cast<unsigned char*>(d_work);
-    const DevPair* dp = reinterpret_cast<const DevPair*>(ix->arena + pl->table_at);
+    const DevPair* dp = reinterpret_cast<const DevPair*>(pl->base());
     auto* offsets = reinterpret_cast<unsigned long long*>(base + w.offsets);
     auto* matches = reinterpret_cast<uint32_t*>(base + w.matches);
     if (d_best_out != d_best_in)

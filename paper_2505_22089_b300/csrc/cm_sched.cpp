@@ -183,7 +183,15 @@ struct cm_schedule {
     };
     std::vector<Row> rows;
     int32_t iterations = 0;
+    std::vector<cm_pair> pairs;   // the caller's pair list the rows index (cm_index_workspace_bytes)
 };
+
+namespace cm {
+const cm_pair* schedule_pairs(const cm_schedule* s, int64_t* n) {
+    *n = (int64_t)s->pairs.size();
+    return s->pairs.data();
+}
+}  // namespace cm
 
 // Error text is routed through cm_last_error by a small shim in cm_api.cpp.
 extern "C" cm_status cm_internal_fail(cm_status st, const char* msg);
@@ -237,6 +245,7 @@ extern "C" cm_status cm_schedule_blocks(const cm_pair* pairs, int64_t n_pairs, i
     }
     cm_schedule* s = new (std::nothrow) cm_schedule();
     if (!s) return sfail(CM_ERR_NOMEM, "schedule: host allocation");
+    s->pairs.assign(pairs, pairs + n_pairs);
     std::set<std::pair<int, int>> remaining;
     for (auto& kv : edge_pairs) remaining.insert(kv.first);
     int it = 0;
@@ -343,6 +352,7 @@ extern "C" cm_status cm_schedule_from_rows(int32_t n_rows, const cm_schedule_row
     std::vector<char> res((size_t)n_images, 0), seen((size_t)n_pairs, 0);
     auto s = std::make_unique<cm_schedule>();
     s->rows.resize((size_t)n_rows);
+    s->pairs.assign(pairs, pairs + n_pairs);
     int32_t iters = 0;
     for (int32_t r = 0; r < n_rows; ++r) {
         const cm_schedule_row& R = rows[r];

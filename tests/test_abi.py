@@ -143,3 +143,22 @@ def test_images_above_65535_descriptors_are_rejected():
     assert lib.cm_nn_pairs(fake, off.ctypes.data, 2, pr.ctypes.data, 1, 4, 5, fake, 1 << 30, fake, None, None,
                            None) == cm.CM_ERR_INVALID
     assert b"65535" in lib.cm_last_error()
+
+
+def test_noalloc_rejects_unsupported_forms_before_touching_the_gpu():
+    """The allocation-free entry point checks its parameters on the host: the
+    tensor-core projection and scan and the tensor-core reranks are refused
+    with CM_ERR_INVALID, images over 8,192 rows with CM_ERR_BUDGET."""
+    import ctypes
+    lib = cm.lib()
+    sums = np.ones(128, np.uint64)
+    fake = ctypes.c_void_p(1 << 20)    # never dereferenced: every case fails on the host first
+    for kw, n_i, want in ((dict(projection="tc"), 10, cm.CM_ERR_INVALID),
+                          (dict(projection="ffma", algo="tc"), 10, cm.CM_ERR_INVALID),
+                          (dict(projection="ffma", rerank="bf16"), 10, cm.CM_ERR_INVALID),
+                          (dict(projection="ffma"), 8193, cm.CM_ERR_BUDGET)):
+        p = cm.Params.make(**kw)
+        st = lib.cm_match_pair_noalloc(ctypes.byref(p), fake, n_i, fake, 10, sums.ctypes.data, 100, fake, None, None,
+                                       None)
+        assert st == want, (kw, st)
+        assert lib.cm_last_error()

@@ -48,3 +48,18 @@ def test_traffic_is_reported_only_where_it_was_measured():
     assert bench.kmatch_traffic(_args()) == (t["bytes_per_launch"] if same_sources else None)
     for kw in (dict(grid="20x10"), dict(workload="grid500"), dict(rerank="fp8"), dict(K=16)):
         assert bench.kmatch_traffic(_args(**kw)) is None, kw
+
+
+def test_oracle_sample_covers_its_share_and_the_pairs_among_its_images():
+    import numpy as np
+    import synth
+    wl = synth.grid500(gx=10, gy=8)
+    sel, imgs, elig = bench.pick_sample(wl.pairs, 0.02, 50)
+    assert len(sel) == max(50, int(np.ceil(0.02 * len(wl.pairs)))) and len(set(sel.tolist())) == len(sel)
+    assert set(sel.tolist()) <= set(elig.tolist())
+    assert set(np.unique(wl.pairs[sel]).tolist()) == set(imgs.tolist())
+    both = [k for k, (i, j) in enumerate(wl.pairs) if i in imgs and j in imgs]
+    assert both == elig.tolist()
+    # the same seed gives the same sample; all pairs when the share covers them
+    assert np.array_equal(bench.pick_sample(wl.pairs, 0.02, 50)[0], sel)
+    assert len(bench.pick_sample(wl.pairs, 1.0, 1)[0]) == len(wl.pairs)
