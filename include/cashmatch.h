@@ -56,13 +56,16 @@ typedef enum {
 
 /* Thread mapping of the match kernel (both compute the same result). */
 typedef enum {
-    CM_ALGO_AUTO = 0,    /* library choice */
+    CM_ALGO_AUTO = 0,    /* library choice: CM_ALGO_BUCKET */
     CM_ALGO_TILE = 1,    /* one lane per query; a CTA keeps a tile of queries' top-K in shared memory and
                             sweeps the tables with the queries sorted by bucket */
     CM_ALGO_WARP = 2,    /* one warp per query; top-K kept across the warp with ballots and shuffles */
-    CM_ALGO_TC = 3       /* a CTA per pair; each bucket's queries x database points block of Hamming
+    CM_ALGO_TC = 3,      /* a CTA per pair; each bucket's queries x database points block of Hamming
                             distances on the tensor cores (code bits as E4M3 +-1: dot = 128 - 2 h, exact);
                             then a separate rerank launch.  K in {4, 8, 16} */
+    CM_ALGO_BUCKET = 4   /* bucket-major (the AUTO choice): a CTA per pair sweeps the tables; a warp takes 32
+                            queries of one bucket and streams that bucket's database run through shared memory
+                            (bulk copies), every lane reading the same candidate; lists kept in the plan */
 } cm_algo;
 
 /* How the projections onto the hyperplanes are computed (both decide the same
@@ -224,6 +227,21 @@ cm_status cm_index_check(cm_index* ix, cm_stream stream);
 /* Recomputes centring statistics from the resident descriptors, then keys,
  * codes and buckets of every resident image (async; a whole hashing pass). */
 cm_status cm_index_rehash(cm_index* ix, cm_stream stream);
+/* Exact uint64 column sums of the listed resident images' descriptors into
+ * d_sums (device, 128 entries; zeroed first), asynchronous on stream.  With
+ * cm_index_set_mean_device and cm_index_hash this splits cm_index_rehash so
+ * the sums can be reduced across processes in between: each process of a
+ * sharded job sums the images it owns, an all-reduce of the 128 integers
+ * (exact in any order) gives every process the global sums.  Errors:
+ * CM_ERR_INVALID (ids, NULL), CM_ERR_STATE (an image not resident). */
+cm_status cm_index_col_sums_of(cm_index* ix, int32_t count, const int32_t* ids, uint64_t* d_sums, cm_stream stream);
+/* Centring mean mu = sums / n_total from 128 exact column sums in device
+ * memory (async, on stream).  The index keeps a copy of the sums. */
+cm_status cm_index_set_mean_device(cm_index* ix, const uint64_t* d_sums, uint64_t n_total, cm_stream stream);
+/* Keys, codes and buckets of every resident image under the current mean
+ * (async; cm_index_rehash without recomputing the mean).  CM_ERR_STATE when
+ * no mean is set or nothing is resident. */
+cm_status cm_index_hash(cm_index* ix, cm_stream stream);
 /* Releases resident images (Sec. 2.3.2 step (3)) and refreshes the device
  * tables on stream.  Every call on an index must use the same stream: work
  * already enqueued that reads an evicted image then precedes any later load

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libcashmatch.so")
 
 CM_OK, CM_ERR_INVALID, CM_ERR_BUDGET, CM_ERR_CUDA, CM_ERR_TIMEOUT, CM_ERR_NOMEM, CM_ERR_STATE = range(7)
 RERANK = {"fp32": 0, "bf16": 1, "fp8": 2, "int": 3}
-ALGO = {"auto": 0, "tile": 1, "warp": 2, "tc": 3}
+ALGO = {"auto": 0, "tile": 1, "warp": 2, "tc": 3, "bucket": 4}
 PROJ = {"tc": 0, "ffma": 1}
 MEM_HOST, MEM_DEVICE, MEM_DEVICE_INPLACE = 0, 1, 2
 # Arena headroom the binding adds to cm_index_bytes for match-plan tables
@@ -56,7 +56,7 @@ EXPORTS = [
     "cm_workspace_status", "cm_nn_workspace_bytes", "cm_nn_pairs", "cm_selftest_wait", "cm_match_plan_sao_bytes",
     "cm_match_plan_sao", "cm_pipeline_workspace_bytes_ex", "cm_run_schedule_ex", "cm_autotune", "cm_match_pair_noalloc",
     "cm_match_pairs_workspace_bytes", "cm_index_workspace_bytes", "cm_free_index", "cm_index_mean_host",
-    "cm_probe_int",
+    "cm_probe_int", "cm_index_col_sums_of", "cm_index_set_mean_device", "cm_index_hash",
 ]
 
 
@@ -182,6 +182,9 @@ def lib():
             "cm_free_index": (None, [vp]),
             "cm_index_mean_host": (i32, [vp, vp, vp]),
             "cm_probe_int": (i32, [i32, i32, vp, u64, vp, ctypes.POINTER(ctypes.c_double)]),
+            "cm_index_col_sums_of": (i32, [vp, i32, vp, vp, vp]),
+            "cm_index_set_mean_device": (i32, [vp, vp, u64, vp]),
+            "cm_index_hash": (i32, [vp, vp]),
             "cm_match_pair_noalloc": (i32, [P, vp, i32, vp, i32, vp, u64, vp, vp, vp, vp]),
             "cm_sequence_create": (i32, [vp, i32, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]),
             "cm_sequence_launch": (i32, [vp, vp]),
@@ -541,6 +544,19 @@ class Index:
         b = ctypes.c_uint64()
         check(lib().cm_match_pairs_workspace_bytes(self.h, pr.ctypes.data, len(pr), ctypes.byref(b)))
         return int(b.value)
+
+    def col_sums_of(self, ids, d_sums, stream=None):
+        """cm_index_col_sums_of: exact column sums of resident images `ids` into
+        d_sums (CUDA int64/uint64 tensor of 128 entries), asynchronous."""
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        check(lib().cm_index_col_sums_of(self.h, len(ids), ids.ctypes.data if len(ids) else None, _ptr(d_sums),
+                                         _stream(stream)))
+
+    def set_mean_device(self, d_sums, n_total: int, stream=None):
+        check(lib().cm_index_set_mean_device(self.h, _ptr(d_sums), int(n_total), _stream(stream)))
+
+    def hash(self, stream=None):
+        check(lib().cm_index_hash(self.h, _stream(stream)))
 
     def mean_device(self, desc, stream=None):
         check(lib().cm_index_mean_device(self.h, _ptr(desc), desc.shape[0], _stream(stream)))

@@ -71,7 +71,7 @@ extern "C" cm_status cm_params_check(const cm_params* p) {
     if (p->query_tile != 0 && (p->query_tile < 64 || p->query_tile > 8192 || p->query_tile % 64))
         return fail(CM_ERR_INVALID, "params: query_tile=%d must be 0 or a multiple of 64 in 64..8192",
                     p->query_tile);
-    if (p->algo < CM_ALGO_AUTO || p->algo > CM_ALGO_TC) return fail(CM_ERR_INVALID, "params: algo %d", p->algo);
+    if (p->algo < CM_ALGO_AUTO || p->algo > CM_ALGO_BUCKET) return fail(CM_ERR_INVALID, "params: algo %d", p->algo);
     if (p->algo == CM_ALGO_TC && p->K < 4)
         return fail(CM_ERR_INVALID, "params: the tensor-core Hamming scan needs K in {4, 8, 16}");
     if (p->projection != CM_PROJ_TC && p->projection != CM_PROJ_FFMA)
@@ -553,6 +553,53 @@ extern "C" cm_status cm_index_rehash(cm_index* ix, cm_stream stream) {
     return hash_batch(ix, h, s);
 }
 
+extern "C" cm_status cm_index_col_sums_of(cm_index* ix, int32_t count, const int32_t* ids, uint64_t* d_sums,
+                                          cm_stream stream) {
+    if (!ix || count < 0 || (count && !ids) || !d_sums) return fail(CM_ERR_INVALID, "cm_index_col_sums_of: bad argument");
+    std::vector<int32_t> batch(count), tiles(count + 1, 0);
+    for (int k = 0; k < count; ++k) {
+        const int i = ids[k];
+        if (i < 0 || i >= ix->n_images) return fail(CM_ERR_INVALID, "cm_index_col_sums_of: image id %d", i);
+        if (!ix->resident[i]) return fail(CM_ERR_STATE, "cm_index_col_sums_of: image %d is not resident", i);
+        batch[k] = i;
+        tiles[k + 1] = tiles[k] + (ix->n_desc[i] + kHashTile - 1) / kHashTile;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CM_CUDA(cudaMemsetAsync(d_sums, 0, kDim * 8, s));
+    if (!count || !tiles[count]) return CM_OK;
+    cm_status st = upload_table(ix, ix->fx.batch, batch.data(), batch.size() * 4, s);
+    if (st == CM_OK) st = upload_table(ix, ix->fx.tiles, tiles.data(), tiles.size() * 4, s);
+    if (st != CM_OK) return st;
+    CM_CUDA(launch_colsum_images(ix->hash_launch(false, count, tiles[count], 0), reinterpret_cast<unsigned long long*>(d_sums),
+                                 s));
+    return CM_OK;
+}
+
+extern "C" cm_status cm_index_set_mean_device(cm_index* ix, const uint64_t* d_sums, uint64_t n_total, cm_stream stream) {
+    if (!ix || !d_sums || !n_total) return fail(CM_ERR_INVALID, "cm_index_set_mean_device: bad argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long* sums = ix->at<unsigned long long>(ix->fx.sums);
+    CM_CUDA(cudaMemcpyAsync(sums, d_sums, kDim * 8, cudaMemcpyDeviceToDevice, s));
+    CM_CUDA(launch_mean(sums, nullptr, n_total, ix->at<float>(ix->fx.mu), s));
+    ix->mean_set = true;
+    ix->sums_on_host = false;
+    ix->n_total = n_total;
+    return CM_OK;
+}
+
+extern "C" cm_status cm_index_hash(cm_index* ix, cm_stream stream) {
+    if (!ix) return fail(CM_ERR_INVALID, "cm_index_hash: NULL index");
+    if (!ix->mean_set) return fail(CM_ERR_STATE, "cm_index_hash: centring mean not set");
+    int nb = 0, nt = 0;
+    for (int i = 0; i < ix->n_images; ++i)
+        if (ix->resident[i]) {
+            ++nb;
+            nt += (ix->n_desc[i] + kHashTile - 1) / kHashTile;
+        }
+    if (!nb) return fail(CM_ERR_STATE, "cm_index_hash: no resident image");
+    return hash_batch(ix, ix->hash_launch(true, nb, nt, tiles_of(ix, 128)), reinterpret_cast<cudaStream_t>(stream));
+}
+
 extern "C" cm_status cm_index_evict(cm_index* ix, int32_t count, const int32_t* ids, cm_stream stream) {
     if (!ix || count < 0 || (count && !ids)) return fail(CM_ERR_INVALID, "cm_index_evict: bad argument");
     for (int k = 0; k < count; ++k) {
@@ -752,30 +799,39 @@ extern "C" cm_status cm_match_plan_run_marked(cm_match_plan* pl, const cm_match_
     m.rerank = pp.rerank;
     m.counter = counter;
     m.out = *out;
-    m.algo = pp.algo == CM_ALGO_WARP ? CM_ALGO_WARP : CM_ALGO_TILE;   // auto: tile, if its tile fits
+    m.algo = resolved_algo(&pp);
     if (m.algo == CM_ALGO_TILE && match_smem_bytes(m.S, m.K) > kMatchSmemLimit) m.algo = CM_ALGO_WARP;
     m.err = ix->at<int>(ix->fx.err);
+    const HandOver ho = hand_over(&pp, pl->rows, pl->max_ni);
+    uint8_t* base = counter_ptr + kAlign;
+    m.klists = reinterpret_cast<uint32_t*>(base + ho.klists);
+    auto scan = [&]() -> cudaError_t {
+        switch (m.algo) {
+            case CM_ALGO_BUCKET: return launch_match_bm(m, ix->sms, s);
+            case CM_ALGO_TILE: return launch_match(m, ix->sms, s);
+            default: return launch_match_wq(m, ix->sms, s);
+        }
+    };
     if (needs_hand_over(&pp)) {
-        // a scan leaves each query's top-K in the plan's hand-over area, then a rerank launch
-        const HandOver ho = hand_over(&pp, pl->rows, pl->max_ni);
-        uint8_t* base = counter_ptr + kAlign;
-        m.topk16 = reinterpret_cast<uint16_t*>(base + ho.idx);
-        m.hnorm = reinterpret_cast<uint32_t*>(base + ho.norm);
-        m.hscale = pp.rerank == CM_RERANK_FP8 ? reinterpret_cast<float*>(base + ho.scale) : nullptr;
-        if (pp.algo == CM_ALGO_TC) {
-            m.algo = CM_ALGO_TC;
+        // a scan leaves each query's top-K in the plan's hand-over area (the bucket-major
+        // scan: its key lists), then a rerank launch
+        if (m.algo != CM_ALGO_BUCKET) {
+            m.topk16 = reinterpret_cast<uint16_t*>(base + ho.idx);
+            m.hnorm = reinterpret_cast<uint32_t*>(base + ho.norm);
+            m.hscale = pp.rerank == CM_RERANK_FP8 ? reinterpret_cast<float*>(base + ho.scale) : nullptr;
+        }
+        if (m.algo == CM_ALGO_TC) {
             m.lists = reinterpret_cast<uint32_t*>(base + ho.lists);
             m.max_ni = pl->max_ni;
             CM_CUDA(launch_scan_tc(m, std::min(ix->sms, kMaxScanCtas), s));
         } else {
-            m.algo = CM_ALGO_TILE;
-            CM_CUDA(launch_match(m, ix->sms, s));
+            CM_CUDA(scan());
         }
         if (mark) CM_CUDA(cudaEventRecord(mark, s));
         CM_CUDA(tc_rerank(&pp) ? launch_rerank_tc(m, ix->sms, s) : launch_rerank_cc(m, ix->sms, s));
         return CM_OK;
     }
-    CM_CUDA(m.algo == CM_ALGO_TILE ? launch_match(m, ix->sms, s) : launch_match_wq(m, ix->sms, s));
+    CM_CUDA(scan());
     if (mark) CM_CUDA(cudaEventRecord(mark, s));
     return CM_OK;
 }

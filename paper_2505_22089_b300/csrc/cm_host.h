@@ -277,28 +277,40 @@ uint64_t sao_work_bytes(int64_t n_pairs, int64_t rows);
 const cm_pair* schedule_pairs(const cm_schedule* s, int64_t* n);
 }  // namespace cm
 
-// Arena bytes of a plan: its pair table, the work counter and, for the
-// tensor-core reranks, the [rows][K] top-K hand-over from scan to rerank
-// (index, squared norm and, for FP8, scale of every kept candidate).
-// Hand-over areas after the counter: indices u16, norms u32, scales f32 (FP8), [rows][K] each,
-// for the tensor-core reranks and for the tensor-core Hamming scan; the scan adds per-CTA
-// scratch for per-table top-K lists: [kMaxScanCtas][max query rows][L][K] u32.
+// Arena bytes of a plan: its pair table, the work counter and:
+//   - for the tensor-core reranks after the tile or tensor-core scan, the
+//     [rows][K] top-K hand-over from scan to rerank (index u16, squared norm
+//     u32 and, for FP8, scale f32 of every kept candidate);
+//   - for the tensor-core Hamming scan, per-CTA scratch for per-table top-K
+//     lists: [kMaxScanCtas][max query rows][L][K] u32;
+//   - for the bucket-major matcher, every query row's running top-K keys,
+//     [rows][K] u32.
 constexpr int kMaxScanCtas = 160;   // >= the SM count; the scan's grid is capped to it
 struct HandOver {
-    uint64_t idx, norm, scale, lists, total;
+    uint64_t idx, norm, scale, lists, klists, total;
 };
 inline bool needs_hand_over(const cm_params* p) { return tc_rerank(p) || p->algo == CM_ALGO_TC; }
+// The matcher a plan's launch uses: the tensor-core scan, the warp-per-query
+// form, the tile form, or the bucket-major form (AUTO).
+inline int resolved_algo(const cm_params* p) {
+    if (p->algo == CM_ALGO_TC || p->algo == CM_ALGO_WARP || p->algo == CM_ALGO_TILE) return p->algo;
+    return CM_ALGO_BUCKET;
+}
 inline HandOver hand_over(const cm_params* p, int64_t rows, int32_t max_ni) {
     HandOver h{};
-    if (!needs_hand_over(p)) return h;
     const uint64_t e = (uint64_t)rows * (uint64_t)p->K;
-    h.idx = 0;
-    h.norm = align_up(e * 2);
-    h.scale = h.norm + align_up(e * 4);
-    h.lists = h.scale + (p->rerank == CM_RERANK_FP8 ? align_up(e * 4) : 0);
-    h.total = h.lists;
-    if (p->algo == CM_ALGO_TC)
-        h.total += align_up((uint64_t)kMaxScanCtas * (uint64_t)max_ni * (uint64_t)p->L * (uint64_t)p->K * 4);
+    // the bucket-major scan's key lists serve as the tensor-core rerank's hand-over
+    if (needs_hand_over(p) && resolved_algo(p) != CM_ALGO_BUCKET) {
+        h.idx = 0;
+        h.norm = align_up(e * 2);
+        h.scale = h.norm + align_up(e * 4);
+        h.lists = h.scale + (p->rerank == CM_RERANK_FP8 ? align_up(e * 4) : 0);
+        h.total = h.lists;
+        if (p->algo == CM_ALGO_TC)
+            h.total += align_up((uint64_t)kMaxScanCtas * (uint64_t)max_ni * (uint64_t)p->L * (uint64_t)p->K * 4);
+    }
+    h.klists = h.total;
+    if (resolved_algo(p) == CM_ALGO_BUCKET) h.total += align_up(e * 4);
     return h;
 }
 inline uint64_t plan_bytes(const cm_params* p, int64_t n_pairs, int64_t rows, int32_t max_ni) {

@@ -17,6 +17,7 @@ constexpr int kMatchThreads = 1024;
 constexpr int kDefaultQueryTile = 2048;  // queries per work item
 constexpr size_t kMatchSmemLimit = 214 * 1024;  // dynamic shared memory of the tile kernel (static extra)
 constexpr int kWqThreads = 256;          // warp-per-query matcher: 8 warps per CTA
+constexpr int kBmThreads = 512;          // bucket-major matcher: 16 warps per CTA, 2 CTAs per SM
 constexpr int kWqBlocksPerSM = 3;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
@@ -73,7 +74,7 @@ struct MatchLaunch {
     int32_t L, m, K;
     int32_t ratio_num, ratio_den;
     int32_t rerank;
-    int32_t algo;              // CM_ALGO_TILE or CM_ALGO_WARP
+    int32_t algo;              // CM_ALGO_TILE, CM_ALGO_WARP, CM_ALGO_BUCKET or CM_ALGO_TC
     unsigned* counter;         // work counter (zeroed before each launch)
     int* err;                  // set to 1 when a bounded device wait gives up
     // tensor-core forms, scan -> rerank hand-over, [rows][K] in rank order:
@@ -82,6 +83,7 @@ struct MatchLaunch {
     float* hscale;             // their FP8 row scales (FP8 form)
     uint32_t* lists;           // tensor-core Hamming scan: per-CTA [max_ni][L][K] per-table top-K keys
     int32_t max_ni;            // largest query image of the launch
+    uint32_t* klists;          // bucket-major matcher: [rows][K] running top-K keys (Hamming << 16 | index)
     cm_match_out out;
 };
 
@@ -98,6 +100,8 @@ cudaError_t launch_bucket(const HashLaunch& h, cudaStream_t s);
 cudaError_t launch_match(const MatchLaunch& m, int sm_count, cudaStream_t s);      // lane per query (cm_match.cu)
 cudaError_t launch_match_wq(const MatchLaunch& m, int sm_count, cudaStream_t s);   // warp per query (cm_match_wq.cu)
 size_t match_smem_bytes(int S, int K);
+cudaError_t launch_match_bm(const MatchLaunch& m, int sm_count, cudaStream_t s);   // bucket-major (cm_match_bm.cu)
+size_t match_bm_smem_bytes();
 cudaError_t launch_compact(const DevPair* pairs, int n_pairs, const DevImage* imgs, const int32_t* best,
                            uint32_t* counts, unsigned long long* offsets, unsigned long long* total, uint32_t* out,
                            unsigned long long capacity, cudaStream_t s);                 // cm_compact.cu

@@ -94,10 +94,17 @@ struct SubTile {
     int64_t row;   // output row of the first query
     // the pair's images: row copies, query norms / scales, raw rows (FP8 re-score)
     const unsigned char *ixq, *jxq;
-    const uint32_t* inorm;
-    const float* iscale;
+    const uint32_t *inorm, *jnorm;
+    const float *iscale, *jscale;
     const uint8_t *idesc, *jdesc;
 };
+
+// Index of kept candidate e (flat [row][K] position) and, from the plan's
+// hand-over or the bucket-major scan's key lists (Hamming << 16 | index; an
+// empty key's low half is kNoCand as well), whether it exists.
+__device__ __forceinline__ uint32_t cand_index(const MatchLaunch& ml, int64_t e) {
+    return ml.topk16 ? (uint32_t)ml.topk16[e] : (ml.klists[e] & 0xFFFFu);
+}
 
 // Walks a CTA's increasing sequence of sub-tiles; the current pair's record is
 // kept in registers and replaced only when the sequence crosses into a later
@@ -109,8 +116,8 @@ struct Cursor {
     int pair = -1, item0 = 0, item_end = 0, n_i = 0;
     int64_t row_off = 0;
     const unsigned char *ixq = nullptr, *jxq = nullptr;
-    const uint32_t* inorm = nullptr;
-    const float* iscale = nullptr;
+    const uint32_t *inorm = nullptr, *jnorm = nullptr;
+    const float *iscale = nullptr, *jscale = nullptr;
     const uint8_t *idesc = nullptr, *jdesc = nullptr;
     DevPair nxt{};   // record of pair + 1
 
@@ -130,7 +137,9 @@ struct Cursor {
                 ixq = static_cast<const unsigned char*>(I.xq);
                 jxq = static_cast<const unsigned char*>(J.xq);
                 inorm = I.norm;
+                jnorm = J.norm;
                 iscale = I.xscale;
+                jscale = J.xscale;
                 idesc = I.desc;
                 jdesc = J.desc;
             }
@@ -142,7 +151,9 @@ struct Cursor {
         t.ixq = ixq;
         t.jxq = jxq;
         t.inorm = inorm;
+        t.jnorm = jnorm;
         t.iscale = iscale;
+        t.jscale = jscale;
         t.idesc = idesc;
         t.jdesc = jdesc;
         return t;
@@ -245,7 +256,7 @@ __global__ void __launch_bounds__(RR<K, FP8>::THREADS, RR<K, FP8>::CTAS) k_reran
 #pragma unroll
             for (int q = 0; q < C::PER_THREAD; ++q) {
                 const int r = (tid + q * C::PROD) / C::CPR;
-                jr[q] = (r < 128 && r / K < t.nq) ? (uint32_t)ml.topk16[t.row * K + r] : (uint32_t)kNoCand;
+                jr[q] = (r < 128 && r / K < t.nq) ? cand_index(ml, t.row * K + r) : (uint32_t)kNoCand;
             }
         };
         // copies sub-tile t into stage it % STAGES; the stage goes to the MMA once every
@@ -349,11 +360,12 @@ __global__ void __launch_bounds__(RR<K, FP8>::THREADS, RR<K, FP8>::CTAS) k_reran
             In v{kNoCand, 0u, 0u, 1.f, 1.f};
             if (c < t.nq) {
                 const int64_t e = (t.row + c) * K + k;
-                v.j = ml.topk16[e];
-                v.ny = ml.hnorm[e];
+                v.j = cand_index(ml, e);
+                const bool hv = v.j != kNoCand;
+                v.ny = ml.hnorm ? ml.hnorm[e] : (hv ? __ldg(t.jnorm + v.j) : 0u);
                 v.nx = __ldg(t.inorm + t.q0 + c);
                 if (FP8) {
-                    v.sy = ml.hscale[e];
+                    v.sy = ml.hscale ? ml.hscale[e] : (hv ? __ldg(t.jscale + v.j) : 0.f);
                     v.sx = __ldg(t.iscale + t.q0 + c);
                 }
             }

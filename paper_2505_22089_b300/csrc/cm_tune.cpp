@@ -1,5 +1,6 @@
-// Autotuner of the match launch: picks the work-item size (queries per CTA
-// work item) and the thread mapping (tile or warp-per-query) by timing them on
+// Autotuner of the match launch: picks the thread mapping (bucket-major, tile
+// or warp-per-query) and, for the tile forms, the work-item size (queries per
+// CTA work item) by timing them on
 // a sample of pairs, and optionally the Hamming top-K size K under a floor on
 // decision agreement with the largest K tried.
 //
@@ -80,10 +81,11 @@ extern "C" cm_status cm_autotune(cm_index* ix, const cm_pair* pairs, int64_t n_p
     const bool tcr = tc_rerank(&ix->p);
     const int tiles[] = {256, 512, 1024, 2048, 4096};
     float best_ms = -1.f;
-    for (int a = 0; a < 2 && st == CM_OK; ++a) {
-        const int algo = a == 0 ? CM_ALGO_TILE : CM_ALGO_WARP;
-        if (algo == CM_ALGO_WARP && tcr) continue;   // the tensor-core forms run after the tile scan
+    for (int a = 0; a < 3 && st == CM_OK; ++a) {
+        const int algo = a == 0 ? CM_ALGO_BUCKET : (a == 1 ? CM_ALGO_TILE : CM_ALGO_WARP);
+        if (algo == CM_ALGO_WARP && tcr) continue;   // the tensor-core forms need a tile or bucket scan
         for (int S : tiles) {
+            if (algo == CM_ALGO_BUCKET && S != tiles[0]) continue;   // no work-item size: one trial
             if (algo == CM_ALGO_TILE && match_smem_bytes(S, ix->p.K) > kMatchSmemLimit) continue;
             ix->p = saved;
             ix->p.query_tile = S;
@@ -98,7 +100,7 @@ extern "C" cm_status cm_autotune(cm_index* ix, const cm_pair* pairs, int64_t n_p
             }
             if (best_ms < 0.f || t.ms < best_ms) {
                 best_ms = t.ms;
-                r.query_tile = S;
+                r.query_tile = algo == CM_ALGO_BUCKET ? 0 : S;
                 r.algo = algo;
             }
         }

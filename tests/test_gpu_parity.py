@@ -50,12 +50,12 @@ def test_pair2k_query_tiles_with_ragged_tail(tile, algo):
     _run(synth.pair2k(), cm.Params.make(query_tile=tile, algo=algo))
 
 
-@pytest.mark.parametrize("algo", ["tile", "warp", "tc"])
+@pytest.mark.parametrize("algo", ["bucket", "tile", "warp", "tc"])
 def test_pair2k_integer_rerank(algo):
     _run(synth.pair2k(), cm.Params.make(rerank="int", algo=algo))
 
 
-@pytest.mark.parametrize("algo", ["tile", "warp", "tc"])
+@pytest.mark.parametrize("algo", ["bucket", "tile", "warp", "tc"])
 def test_strip30_full_block(algo):
     # 30 images x 8,000 descriptors, 120 ordered pairs: one MBR block
     _run(synth.strip30(), cm.Params.make(algo=algo), threads=16)
@@ -69,7 +69,7 @@ def test_projection_forms(projection, kw):
     _run(synth.pair2k(n=3000, shared=1000), cm.Params.make(projection=projection, **kw))
 
 
-@pytest.mark.parametrize("algo", ["tile", "warp", "tc"])
+@pytest.mark.parametrize("algo", ["bucket", "tile", "warp", "tc"])
 def test_uneven_sizes_including_tiny_images(algo):
     wl = synth.grid500(gx=5, gy=4, nmin=1, nmax=5000)
     wl.images["n"][[0, 7]] = [1, 63]
@@ -79,7 +79,7 @@ def test_uneven_sizes_including_tiny_images(algo):
 @pytest.mark.parametrize("kw", [dict(K=2), dict(K=4), dict(K=16), dict(m=4), dict(m=0, K=16), dict(L=1),
                                 dict(L=8), dict(L=8, m=6), dict(ratio=(0, 1)), dict(ratio=(1, 2)),
                                 dict(ratio=(1, 1)), dict(seed=12345)])
-@pytest.mark.parametrize("algo", ["tile", "warp", "tc"])
+@pytest.mark.parametrize("algo", ["bucket", "tile", "warp", "tc"])
 def test_parameter_variants(kw, algo):
     if algo == "tc" and kw.get("K") == 2:
         pytest.skip("the tensor-core scan keeps K >= 4")
@@ -87,7 +87,7 @@ def test_parameter_variants(kw, algo):
     _run(wl, cm.Params.make(algo=algo, **kw))
 
 
-@pytest.mark.parametrize("algo", ["tile", "warp", "tc"])
+@pytest.mark.parametrize("algo", ["bucket", "tile", "warp", "tc"])
 def test_one_bucket_full_rerank_is_exhaustive_nn(algo):
     # m = 0 and K >= N_J: every database point is reranked, so the GPU result
     # equals exhaustive L2 nearest neighbours with the ratio test.
@@ -298,3 +298,22 @@ def test_tensor_core_scan_equals_tile_scan(K):
         outs.append(res)
     for key in ("best_j", "d1sq", "d2sq", "topk"):
         assert np.array_equal(outs[0][key], outs[1][key]), key
+
+
+@pytest.mark.parametrize("rerank", ["int", "bf16"])
+def test_bucket_major_equals_tile_form_on_a_grid(rerank):
+    """The bucket-major matcher (units of 32 queries of one bucket, database runs
+    staged in chunks of 64 by bulk copies) against the tile form on uneven
+    images with long runs: top-K lists, distances and decisions bit for bit."""
+    wl = synth.scaled("grid500", gx=5, gy=4, nmin=2000, nmax=12000)
+    desc = wl.generate()
+    res = {}
+    for algo in ("bucket", "tile"):
+        p = cm.Params.make(rerank=rerank, algo=algo)
+        index = cm.Index.build(p, wl.n_desc, torch.from_numpy(desc).cuda())
+        plan, got = gpu_match(index, wl.pairs)
+        res[algo] = got
+        del plan, index
+    for k in ("best_j", "d1sq", "d2sq", "topk"):
+        assert np.array_equal(res["bucket"][k], res["tile"][k]), k
+    assert (res["bucket"]["best_j"] >= 0).sum() > 0.1 * len(res["bucket"]["best_j"])

@@ -93,3 +93,113 @@ def test_two_gloo_ranks_match_the_single_process_run(tmp_path):
     ref = oix.match(wl.pairs)
     for k, r in enumerate(ref):
         assert np.array_equal(seen[k], r["best_j"])
+
+
+class _CpuEngine:
+    """A stand-in for the bench's GPU engine with the same interface: exact
+    column sums in numpy, the mean from the all-reduced sums, and the FP64
+    oracle as the matcher of the rank's rows.  It lets the bench's sharded
+    orchestration (schedule, partition, the one all-reduce, timing max over
+    ranks, checksum and count combination) run on CPU ranks."""
+
+    def __init__(self, args, wl, p, part):
+        self.wl, self.part = wl, part
+        self.desc = wl.generate(threads=1)
+        off = wl.row_off
+        self.local = np.zeros(128, np.uint64)
+        for i in part["owned"]:
+            self.local += self.desc[off[i]:off[i + 1]].astype(np.uint64).sum(0)
+        self.rows = [r for r in part["rows"] if len(r)]
+        self.res = None
+        self.h2d_bytes = 0
+
+    def local_sums(self):
+        return torch.tensor(self.local.astype(np.int64))
+
+    def apply_mean(self, sums, n_total):
+        self.sums, self.n_total = sums.numpy().astype(np.uint64), n_total
+
+    def match(self):
+        oix = oracle.Index(self.desc, self.wl.n_desc, oracle.Params(), threads=1, sums=self.sums,
+                           n_total=self.n_total)
+        self.res = [oix.match(self.wl.pairs[r]) for r in self.rows]
+
+    def timer(self):
+        import time
+
+        class T:
+            def __enter__(s):
+                s.t0 = time.perf_counter()
+                return s
+
+            def __exit__(s, *a):
+                s.ms = (time.perf_counter() - s.t0) * 1e3
+        return T()
+
+    def sync(self):
+        pass
+
+    def upload(self):
+        pass
+
+    def download(self):
+        return 0
+
+    def launches(self, p):
+        return 0
+
+    def results(self):
+        out, n = [], 0
+        for r, rr in zip(self.rows, self.res):
+            nd = self.wl.n_desc[self.wl.pairs[r][:, 0]].astype(np.int64)
+            ro = np.concatenate([[0], np.cumsum(nd)])
+            b = np.concatenate([x["best_j"] for x in rr]) if rr else np.zeros(0, np.int32)
+            out.append((r, ro, b))
+            n += int((b >= 0).sum())
+        return out, n
+
+    def scalar(self, v):
+        return torch.tensor([float(v)], dtype=torch.float64)
+
+
+def _bench_rank(rank, world, port, out_dir):
+    import argparse
+    import json
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    args = argparse.Namespace(workload="grid500", grid="4x3", rerank="fp32", algo="auto", projection="tc", K=8,
+                              budget_gb=0.004, block_images=4, steps=1, warmup=1, e2e_steps=1,
+                              workload_kw=dict(nmin=300, nmax=700))
+    res = bench.run_sharded(args, rank, world, _CpuEngine)
+    if rank == 0:
+        with open(os.path.join(out_dir, "res%d.json" % world), "w") as f:
+            json.dump(res, f)
+    dist.destroy_process_group()
+
+
+def test_bench_sharded_path_with_a_cpu_engine(tmp_path):
+    """bench.run_sharded on 2 gloo ranks and on 1: every pair matched once,
+    the same decision checksum and match count as the single run and as the
+    oracle over the whole job, strong-scaling JSON keys."""
+    import json
+    import torch.multiprocessing as mp
+    from paper_2505_22089_b300 import shard
+    for world in (1, 2):
+        mp.spawn(_bench_rank, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    r1 = json.load(open(tmp_path / "res1.json"))
+    r2 = json.load(open(tmp_path / "res2.json"))
+    assert r2["n_gpus"] == 2 and r2["scaling"] == "strong" and r2["value"] > 0 and r2["ms_per_step"] > 0
+    assert r2["decision_checksum"] == r1["decision_checksum"] and r2["matches"] == r1["matches"]
+    assert sum(sh["pairs"] for sh in r2["shards"]) == r2["config"]["pairs"]
+    assert all(sh["pairs"] > 0 for sh in r2["shards"])
+    wl = synth.grid500(gx=4, gy=3, nmin=300, nmax=700)
+    desc = wl.generate(threads=1)
+    oix = oracle.Index(desc, wl.n_desc, oracle.Params(), threads=4)
+    ref = oix.match(wl.pairs)
+    ro = np.concatenate([[0], np.cumsum(wl.n_desc[wl.pairs[:, 0]].astype(np.int64))])
+    b = np.concatenate([x["best_j"] for x in ref])
+    assert shard.checksum(np.arange(len(wl.pairs)), ro, b) == r2["decision_checksum"]
+    assert int((b >= 0).sum()) == r2["matches"]
