@@ -446,7 +446,7 @@ cm_status cm_run_schedule(cm_index* ix, const cm_schedule* s, const cm_pair* pai
                           const uint8_t* const* desc_host, void* d_work, uint64_t work_bytes, cm_verify_fn verify,
                           void* user, int32_t n_workers, cm_stream stream, cm_pipeline_stats* stats);
 
-/* Options of cm_run_schedule_ex.  sao_k > 0 runs the SAO local constraint
+/* Options of cm_run_schedule_ex (all zero: as cm_run_schedule).  sao_k > 0 runs the SAO local constraint
  * on the GPU for every row, right after the match launch
  * (cm_match_plan_sao), so verification receives only the kept matches;
  * d_kp / d_kp_off are as in cm_match_plan_sao and must cover every image. */
@@ -455,6 +455,10 @@ typedef struct cm_pipeline_opts {
     float sao_max_score;
     const float* d_kp;         /* device float [rows][2], all images concatenated */
     const int64_t* d_kp_off;   /* device int64 [n_images + 1] */
+    int32_t centre;            /* 1: the run computes the centring mean itself from desc_host (exact column
+                                  sums on the GPU): the first row's images are copied into their slots and
+                                  summed there, every other image's rows pass once through a staging block
+                                  of the workspace; the index needs no mean beforehand */
 } cm_pipeline_opts;
 /* cm_pipeline_workspace_bytes for a run with these options (NULL: none). */
 cm_status cm_pipeline_workspace_bytes_ex(const cm_index* ix, const cm_schedule* s, const cm_pair* pairs,

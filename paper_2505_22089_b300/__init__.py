@@ -25,19 +25,23 @@ MEM_HOST, MEM_DEVICE, MEM_DEVICE_INPLACE = 0, 1, 2
 # Arena headroom the binding adds to cm_index_bytes for match-plan tables
 # (24 bytes per planned pair): room for about 600,000 pairs of plans.
 PLAN_HEADROOM = 16 << 20
-# With the BF16 / FP8 reranks a plan also holds its top-K hand-over (6 K bytes
-# per query row, 10 K with FP8); the default arena has room for plans totalling this many
-# times the index's descriptors as query rows.
+# A plan also holds its per-query lists (4 K bytes per query row with the
+# bucket-major scan; 6 K, 10 K with FP8, for the hand-over of the tile and
+# tensor-core scans to the tensor-core rerank); the default arena has room for
+# plans totalling this many times the index's descriptors as query rows.
 TC_PLAN_ROWS_FACTOR = 16
 
 
 def default_headroom(p, n_desc) -> int:
     """Arena bytes the binding adds to cm_index_bytes by default."""
-    extra = 0
     nd = np.asarray(n_desc, dtype=np.int64)
-    if p.rerank in (RERANK["bf16"], RERANK["fp8"]) or p.algo == ALGO["tc"]:
-        per_row = p.K * (10 if p.rerank == RERANK["fp8"] else 6)
-        extra = TC_PLAN_ROWS_FACTOR * int(nd.sum()) * per_row
+    bucket = p.algo in (ALGO["auto"], ALGO["bucket"])
+    per_row = 0
+    if (p.rerank in (RERANK["bf16"], RERANK["fp8"]) and not bucket) or p.algo == ALGO["tc"]:
+        per_row += p.K * (10 if p.rerank == RERANK["fp8"] else 6)   # the scan -> rerank hand-over
+    if bucket:
+        per_row += 4 * p.K                                           # the bucket-major scan's key lists
+    extra = TC_PLAN_ROWS_FACTOR * int(nd.sum()) * per_row
     if p.algo == ALGO["tc"]:   # per-table lists of the tensor-core scan, for a few plans
         extra += 4 * 160 * int(nd.max() if len(nd) else 0) * p.L * p.K * 4
     return PLAN_HEADROOM + extra
@@ -117,7 +121,7 @@ VERIFY_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ct
 
 class PipelineOpts(ctypes.Structure):
     _fields_ = [("sao_k", ctypes.c_int32), ("sao_max_score", ctypes.c_float), ("d_kp", ctypes.c_void_p),
-                ("d_kp_off", ctypes.c_void_p)]
+                ("d_kp_off", ctypes.c_void_p), ("centre", ctypes.c_int32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -813,7 +817,8 @@ def compact_out(plan: "MatchPlan", capacity: int | None = None) -> dict:
 
 def run_schedule(index: Index, sched: Schedule, desc_host, verify=None, keypoints=None, thresh_px: float = 3.0,
                  max_iters: int = 500, seed: int = 7, workers: int = 4, stream=None, sao_k: int = 0,
-                 sao_max_score: float = 0.875, sao_kept=None, gpu_sao_k: int = 0, kp_dev=None, kp_off_dev=None):
+                 sao_max_score: float = 0.875, sao_kept=None, gpu_sao_k: int = 0, kp_dev=None, kp_off_dev=None,
+                 centre: bool = False):
     """cm_run_schedule.  desc_host: per image a host uint8 [n][128] array or
     pinned CPU tensor.  verify: None (count matches only), "affine" (the
     library's RANSAC callback over `keypoints`, per image float [n][2], after
@@ -823,12 +828,15 @@ def run_schedule(index: Index, sched: Schedule, desc_host, verify=None, keypoint
     runs the SAO constraint on the GPU for every row before the matches reach
     the host (kp_dev: CUDA float [rows][2] of all images, kp_off_dev: CUDA
     int64 [n_images + 1]); verification then sees only the kept matches.
+    centre=True: the run computes the centring mean itself from desc_host (the
+    index needs none beforehand and must have nothing resident).
     Returns (stats dict, inliers per pair or None)."""
     import torch
     pairs = sched.pairs
     opts = None
-    if gpu_sao_k:
-        opts = PipelineOpts(int(gpu_sao_k), float(sao_max_score), kp_dev.data_ptr(), kp_off_dev.data_ptr())
+    if gpu_sao_k or centre:
+        opts = PipelineOpts(int(gpu_sao_k), float(sao_max_score), kp_dev.data_ptr() if gpu_sao_k else None,
+                            kp_off_dev.data_ptr() if gpu_sao_k else None, int(bool(centre)))
     ws = ctypes.c_uint64()
     check(lib().cm_pipeline_workspace_bytes_ex(index.h, sched.h, pairs.ctypes.data, len(pairs),
                                                ctypes.byref(opts) if opts is not None else None, ctypes.byref(ws)))

@@ -261,6 +261,51 @@ extern "C" cm_status cm_index_mean_device(cm_index* ix, const uint8_t* d_desc, u
     return CM_OK;
 }
 
+namespace cm {
+// Adds the exact column sums of the host rows of images ids[0..count) to the
+// index's sums (fx.sums, not cleared here), copying them through the device
+// staging block [stage, stage + stage_bytes) (a multiple of 128 bytes) in
+// stream order.  Returns the rows summed in *rows.
+cm_status index_stream_sums(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc_host,
+                            uint8_t* stage, uint64_t stage_bytes, cudaStream_t s, uint64_t* rows) {
+    const uint64_t rows_per_chunk = stage_bytes / kDim;
+    if (!rows_per_chunk) return fail(CM_ERR_BUDGET, "centring: staging block of %llu bytes", (unsigned long long)stage_bytes);
+    unsigned long long* sums = ix->at<unsigned long long>(ix->fx.sums);
+    uint64_t fill = 0, total = 0;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        const int i = ids[k];
+        const uint64_t n = (uint64_t)ix->n_desc[i];
+        if (n && !desc_host[i]) return fail(CM_ERR_INVALID, "centring: image %d has no rows", i);
+        uint64_t done = 0;
+        while (done < n && e == cudaSuccess) {
+            const uint64_t take = std::min(n - done, rows_per_chunk - fill);
+            e = cudaMemcpyAsync(stage + fill * kDim, desc_host[i] + done * kDim, take * kDim, cudaMemcpyHostToDevice, s);
+            fill += take;
+            done += take;
+            if (fill == rows_per_chunk && e == cudaSuccess) {
+                e = launch_colsum_rows(stage, fill, sums, s);
+                fill = 0;
+            }
+        }
+        total += n;
+    }
+    if (fill && e == cudaSuccess) e = launch_colsum_rows(stage, fill, sums, s);
+    if (e != cudaSuccess) return fail(CM_ERR_CUDA, "centring: %s", cudaGetErrorString(e));
+    *rows = total;
+    return CM_OK;
+}
+
+// mu = sums / n_total from the index's sums (fx.sums), on the device.
+cm_status index_mean_from_sums(cm_index* ix, uint64_t n_total, cudaStream_t s) {
+    CM_CUDA(launch_mean(ix->at<unsigned long long>(ix->fx.sums), nullptr, n_total, ix->at<float>(ix->fx.mu), s));
+    ix->mean_set = true;
+    ix->sums_on_host = false;
+    ix->n_total = n_total;
+    return CM_OK;
+}
+}  // namespace cm
+
 extern "C" cm_status cm_index_mean_host(cm_index* ix, const uint8_t* const* desc_host, cm_stream stream) {
     if (!ix || !desc_host) return fail(CM_ERR_INVALID, "cm_index_mean_host: bad argument");
     uint64_t total = 0;
@@ -274,34 +319,17 @@ extern "C" cm_status cm_index_mean_host(cm_index* ix, const uint8_t* const* desc
     while (chunk >= (1ull << 20) && !ix->alloc.alloc(chunk, &at)) chunk /= 2;
     if (chunk < (1ull << 20)) return fail(CM_ERR_BUDGET, "cm_index_mean_host: no 1 MiB of the arena is free");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    uint8_t* stage = ix->arena + at;
-    const uint64_t rows_per_chunk = chunk / kDim;
-    unsigned long long* sums = ix->at<unsigned long long>(ix->fx.sums);
-    cudaError_t e = cudaMemsetAsync(sums, 0, kDim * 8, s);
-    // fill the staging block with consecutive rows (image segments), then sum it
-    uint64_t fill = 0;
-    for (int i = 0; i < ix->n_images && e == cudaSuccess; ++i) {
-        uint64_t done = 0, n = (uint64_t)ix->n_desc[i];
-        while (done < n && e == cudaSuccess) {
-            const uint64_t take = std::min(n - done, rows_per_chunk - fill);
-            e = cudaMemcpyAsync(stage + fill * kDim, desc_host[i] + done * kDim, take * kDim, cudaMemcpyHostToDevice, s);
-            fill += take;
-            done += take;
-            if (fill == rows_per_chunk && e == cudaSuccess) {
-                e = launch_colsum_rows(stage, fill, sums, s);
-                fill = 0;
-            }
-        }
-    }
-    if (fill && e == cudaSuccess) e = launch_colsum_rows(stage, fill, sums, s);
-    if (e == cudaSuccess) e = launch_mean(sums, nullptr, total, ix->at<float>(ix->fx.mu), s);
+    std::vector<int32_t> all(ix->n_images);
+    for (int i = 0; i < ix->n_images; ++i) all[i] = i;
+    uint64_t rows = 0;
+    cudaError_t e = cudaMemsetAsync(ix->arena + ix->fx.sums, 0, kDim * 8, s);
+    cm_status st = e == cudaSuccess ? index_stream_sums(ix, ix->n_images, all.data(), desc_host, ix->arena + at,
+                                                        chunk / kDim * kDim, s, &rows)
+                                    : fail(CM_ERR_CUDA, "cm_index_mean_host: %s", cudaGetErrorString(e));
     // later work on this stream is ordered after the sums: the block may be placed again at once
     ix->alloc.release(at);
-    if (e != cudaSuccess) return fail(CM_ERR_CUDA, "cm_index_mean_host: %s", cudaGetErrorString(e));
-    ix->mean_set = true;
-    ix->sums_on_host = false;
-    ix->n_total = total;
-    return CM_OK;
+    if (st != CM_OK) return st;
+    return index_mean_from_sums(ix, total, s);
 }
 
 // Allocate slots, copy descriptors, refresh the device image table and the
@@ -503,7 +531,7 @@ cm_status index_prefetch(cm_index* ix, int32_t count, const int32_t* ids, const 
     return CM_OK;
 }
 
-cm_status index_publish(cm_index* ix, int32_t count, const int32_t* ids, cudaStream_t s) {
+cm_status index_publish(cm_index* ix, int32_t count, const int32_t* ids, cudaStream_t s, bool centre_first) {
     for (int k = 0; k < count; ++k)
         if (ids[k] < 0 || ids[k] >= ix->n_images || !ix->pending[ids[k]])
             return fail(CM_ERR_STATE, "publish: image %d was not prefetched", ids[k]);
@@ -514,7 +542,15 @@ cm_status index_publish(cm_index* ix, int32_t count, const int32_t* ids, cudaStr
     uint64_t rows = 0;
     st = refresh_resident(ix, s, &rb, &rt, &rows);
     if (st != CM_OK) return st;
-    return hash_batch(ix, ix->hash_launch(false, count, n_tiles, n_tiles128), s);
+    const HashLaunch h = ix->hash_launch(false, count, n_tiles, n_tiles128);
+    if (centre_first) {
+        // the batch's column sums join those already in fx.sums; then the mean of every image
+        uint64_t total = 0;
+        for (int i = 0; i < ix->n_images; ++i) total += (uint64_t)ix->n_desc[i];
+        if (n_tiles) CM_CUDA(launch_colsum_images(h, ix->at<unsigned long long>(ix->fx.sums), s));
+        if ((st = index_mean_from_sums(ix, total, s)) != CM_OK) return st;
+    }
+    return hash_batch(ix, h, s);
 }
 
 void index_cancel_prefetch(cm_index* ix, int32_t count, const int32_t* ids) {

@@ -269,7 +269,13 @@ struct cm_index {
 namespace cm {
 cm_status index_prefetch(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc,
                          cudaStream_t copy_stream, bool* placed);
-cm_status index_publish(cm_index* ix, int32_t count, const int32_t* ids, cudaStream_t s);
+// centre_first: before hashing, add the batch's column sums to the index's
+// sums and set the mean over all images from them (the pipeline's own
+// centring pass, which summed every other image's host rows first).
+cm_status index_publish(cm_index* ix, int32_t count, const int32_t* ids, cudaStream_t s, bool centre_first = false);
+cm_status index_stream_sums(cm_index* ix, int32_t count, const int32_t* ids, const uint8_t* const* desc_host,
+                            uint8_t* stage, uint64_t stage_bytes, cudaStream_t s, uint64_t* rows);
+cm_status index_mean_from_sums(cm_index* ix, uint64_t n_total, cudaStream_t s);
 void index_cancel_prefetch(cm_index* ix, int32_t count, const int32_t* ids);
 // Device workspace of cm_match_plan_sao for a plan of n_pairs pairs and rows query rows.
 uint64_t sao_work_bytes(int64_t n_pairs, int64_t rows);

@@ -49,8 +49,16 @@ constexpr int kWaitPolls = 1 << 22;                // bounded mbarrier wait (eac
 
 static_assert(kBufBytes % 16 == 0, "staging buffers keep 16-byte alignment");
 
+// 128-bit Hamming distance with three population counts instead of four: the
+// four XOR words are added bitwise by a carry-save step (s, c1, c2 with
+// w0 + w1 + w2 + w3 = s + 2 c1 + 2 c2 per bit position), so the count is
+// popc(s) + 2 (popc(c1) + popc(c2)).  POPC runs at a quarter of the rate of
+// the logic ops that replace one of them (16 against 64 per clock per SM).
 __device__ __forceinline__ uint32_t ham128(uint4 a, uint4 b) {
-    return (uint32_t)(__popc(a.x ^ b.x) + __popc(a.y ^ b.y) + __popc(a.z ^ b.z) + __popc(a.w ^ b.w));
+    const uint32_t w0 = a.x ^ b.x, w1 = a.y ^ b.y, w2 = a.z ^ b.z, w3 = a.w ^ b.w;
+    const uint32_t s1 = w0 ^ w1 ^ w2, c1 = (w0 & w1) | (w2 & (w0 ^ w1));
+    const uint32_t s2 = s1 ^ w3, c2 = s1 & w3;
+    return (uint32_t)__popc(s2) + 2u * (uint32_t)(__popc(c1) + __popc(c2));
 }
 
 // Insert key into the ascending list s unless already present.

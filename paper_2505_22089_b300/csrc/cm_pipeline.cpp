@@ -287,12 +287,13 @@ extern "C" int32_t cm_affine_verify_cb(void* user, int32_t, int64_t pair_id, con
 namespace {
 
 struct WorkLayout {
-    uint64_t best_j, counts, offsets, sao, sao_bytes, total;
+    uint64_t best_j, counts, offsets, sao, sao_bytes, stage, stage_bytes, total;
 };
+constexpr uint64_t kCentreStage = 64ull << 20;   // staging block of the pipeline's own centring pass
 
 // Workspace of the largest row: best_j per query, counts and offsets (+ total)
 // per pair, and, with the GPU SAO constraint, its compaction scratch.
-WorkLayout work_layout(int64_t max_rows, int64_t max_pairs, bool sao) {
+WorkLayout work_layout(int64_t max_rows, int64_t max_pairs, bool sao, bool centre) {
     WorkLayout w{};
     uint64_t o = 0;
     auto take = [&](uint64_t bytes) { uint64_t at = o; o = align_up(o + bytes); return at; };
@@ -301,11 +302,14 @@ WorkLayout work_layout(int64_t max_rows, int64_t max_pairs, bool sao) {
     w.offsets = take((uint64_t)(max_pairs + 1) * 8);  // the total sits right after the offsets
     w.sao_bytes = sao ? sao_work_bytes(max_pairs, max_rows) : 0;
     w.sao = take(w.sao_bytes);
+    w.stage_bytes = centre ? kCentreStage : 0;
+    w.stage = take(w.stage_bytes);
     w.total = o;
     return w;
 }
 
 bool sao_on(const cm_pipeline_opts* o) { return o && o->sao_k > 0; }
+bool centre_on(const cm_pipeline_opts* o) { return o && o->centre; }
 
 cm_status row_sizes(const cm_index* ix, const cm_schedule* s, const cm_pair* pairs, int64_t n_pairs, int64_t* max_rows,
                     int64_t* max_pairs, uint64_t* max_plan = nullptr) {
@@ -493,7 +497,7 @@ extern "C" cm_status cm_pipeline_workspace_bytes_ex(const cm_index* ix, const cm
     int64_t mr = 0, mp = 0;
     cm_status st = row_sizes(ix, s, pairs, n_pairs, &mr, &mp);
     if (st != CM_OK) return st;
-    *bytes = work_layout(mr, mp, sao_on(opts)).total;
+    *bytes = work_layout(mr, mp, sao_on(opts), centre_on(opts)).total;
     return CM_OK;
 }
 
@@ -519,12 +523,16 @@ extern "C" cm_status cm_run_schedule_ex(cm_index* ix, const cm_schedule* s, cons
         return fail(CM_ERR_INVALID, "cm_run_schedule: bad argument");
     if (sao_on(opts) && (opts->sao_k > 16 || !opts->d_kp || !opts->d_kp_off || !(opts->sao_max_score >= 0.f)))
         return fail(CM_ERR_INVALID, "cm_run_schedule: bad SAO options (1 <= sao_k <= 16, keypoints on the device)");
-    if (!ix->mean_set) return fail(CM_ERR_STATE, "cm_run_schedule: centring mean not set");
+    if (!ix->mean_set && !centre_on(opts)) return fail(CM_ERR_STATE, "cm_run_schedule: centring mean not set");
+    if (centre_on(opts))
+        for (int i = 0; i < ix->n_images; ++i)
+            if (ix->resident[i] || ix->pending[i])
+                return fail(CM_ERR_STATE, "cm_run_schedule: centring from host rows needs an index with nothing resident");
     int64_t max_rows = 0, max_pairs = 0;
     uint64_t max_plan = 0;
     cm_status st = row_sizes(ix, s, pairs, n_pairs, &max_rows, &max_pairs, &max_plan);
     if (st != CM_OK) return st;
-    const WorkLayout wl = work_layout(max_rows, max_pairs, sao_on(opts));
+    const WorkLayout wl = work_layout(max_rows, max_pairs, sao_on(opts), centre_on(opts));
     if (work_bytes < wl.total)
         return fail(CM_ERR_BUDGET, "cm_run_schedule: workspace %llu bytes, %llu needed", (unsigned long long)work_bytes,
                     (unsigned long long)wl.total);
@@ -542,7 +550,8 @@ extern "C" cm_status cm_run_schedule_ex(cm_index* ix, const cm_schedule* s, cons
     P.verify = verify;
     P.user = user;
     std::vector<cudaEvent_t> ev_start(R, nullptr), ev_done(R, nullptr), ev_copied(R, nullptr);
-    std::vector<char> prefetched(R, 0);   // row r's loads were placed and copied during row r-1
+    // row r's loads were placed and copied early: 1 during row r-1, 2 (row 0) by the centring pass
+    std::vector<char> prefetched(R, 0);
     cudaStream_t cpy = nullptr;           // copies of the next row's descriptors
     cudaEvent_t ev_origin = nullptr;
     std::vector<std::unique_ptr<RowJob>> jobs;
@@ -664,6 +673,46 @@ extern "C" cm_status cm_run_schedule_ex(cm_index* ix, const cm_schedule* s, cons
         ix->plan_reserve_bytes = max_plan;
         ix->plan_reserve_busy = false;
     }
+    // The run's own centring pass: row 0's images go straight into their slots
+    // (summed there when they are published), every other image's rows pass
+    // once through the workspace's staging block; each image is read from the
+    // host once before its first hashing.
+    if (centre_on(opts)) {
+        bool kept0 = false;
+        cm_schedule_row row0{};
+        if (R > 0 && (st = cm_schedule_get_row(s, 0, &row0)) != CM_OK) return bail(st);
+        std::vector<char> in0(ix->n_images, 0);
+        if (R > 0 && row0.n_load) {
+            std::vector<const uint8_t*> src(row0.n_load);
+            for (int k = 0; k < row0.n_load; ++k) src[k] = desc_host[row0.load[k]];
+            if ((st = index_prefetch(ix, row0.n_load, row0.load, src.data(), cs, &kept0)) != CM_OK) return bail(st);
+            if (kept0) {
+                prefetched[0] = 2;
+                for (int k = 0; k < row0.n_load; ++k) in0[row0.load[k]] = 1;
+            }
+        }
+        std::vector<int32_t> rest;
+        for (int i = 0; i < ix->n_images; ++i)
+            if (!in0[i]) rest.push_back(i);
+        uint64_t rows_streamed = 0;
+        if (cudaMemsetAsync(ix->arena + ix->fx.sums, 0, kDim * 8, cs) != cudaSuccess) {
+            fail(CM_ERR_CUDA, "cm_run_schedule: clearing the sums");
+            return bail(CM_ERR_CUDA);
+        }
+        if ((st = index_stream_sums(ix, (int32_t)rest.size(), rest.data(), desc_host, work + wl.stage, wl.stage_bytes,
+                                    cs, &rows_streamed)) != CM_OK)
+            return bail(st);
+        S.h2d_bytes += rows_streamed * kDim;
+        S.kernels += (int64_t)((rows_streamed * kDim + wl.stage_bytes - 1) / wl.stage_bytes);
+        if (!kept0) {   // nothing kept: the mean is complete already
+            uint64_t total = 0;
+            for (int i = 0; i < ix->n_images; ++i) total += (uint64_t)ix->n_desc[i];
+            if ((st = index_mean_from_sums(ix, total, cs)) != CM_OK) return bail(st);
+            S.kernels += 1;
+        } else {
+            S.kernels += 2;   // the kept images' column sums and the mean, at publication
+        }
+    }
     for (int w = 0; w < n_workers; ++w) threads.emplace_back([&P] { P.worker(); });
     // hashing: (bias +) projection + buckets (+ the rerank row copies); matching: scan (+ tensor-core rerank)
     const int hash_kernels = (ix->p.projection == CM_PROJ_TC ? 3 : 2) + (tc_rerank(&ix->p) ? 1 : 0);
@@ -692,7 +741,10 @@ extern "C" cm_status cm_run_schedule_ex(cm_index* ix, const cm_schedule* s, cons
                 src[k] = desc_host[row.load[k]];
                 S.h2d_bytes += (uint64_t)ix->n_desc[row.load[k]] * kDim;
             }
-            if (prefetched[r]) {   // copied during the previous row: make resident and hash
+            if (prefetched[r] == 2) {   // copied by the centring pass: sum, set the mean, hash
+                if ((st = index_publish(ix, row.n_load, row.load, cs, true)) != CM_OK) return bail(st);
+                prefetched[r] = 0;
+            } else if (prefetched[r]) {   // copied during the previous row: make resident and hash
                 S.prefetched_rows++;
                 if (cudaStreamWaitEvent(cs, ev_copied[r], 0) != cudaSuccess) {
                     fail(CM_ERR_CUDA, "cm_run_schedule: stream wait");

@@ -68,8 +68,9 @@ def _compare_lists(lists, pairs, oix, p, affected, form):
     return total, excl, agree, jac
 
 
-@pytest.mark.parametrize("form", ["fp32", "bf16", "fp8"])
-def test_pipeline_match_lists_equal_the_oracle(form):
+@pytest.mark.parametrize("form,centre", [("fp32", "mean_host"), ("bf16", "mean_host"), ("fp8", "mean_host"),
+                                         ("bf16", "pipeline")])
+def test_pipeline_match_lists_equal_the_oracle(form, centre):
     wl, desc = _grid()
     off = wl.row_off
     p = cm.Params.make(rerank=form)
@@ -81,17 +82,24 @@ def test_pipeline_match_lists_equal_the_oracle(form):
     assert arena < ib, "the arena must be smaller than all images together, so freed space is reused"
     host = [torch.from_numpy(desc[off[i]:off[i + 1]]).pin_memory() for i in range(wl.n_images)]
     index = cm.Index(p, wl.n_desc, arena_bytes=arena)
-    index.mean_host(host)                                   # the library's own centring sums, from host rows
     oix = oracle.Index(desc, wl.n_desc, oparams(p))          # the oracle's own sums
-    sums, n_total = index.col_sums()
-    assert n_total == wl.total_desc and np.array_equal(sums, oix.sums)
+    if centre == "mean_host":
+        index.mean_host(host)                               # the library's own centring sums, from host rows
+        sums, n_total = index.col_sums()
+        assert n_total == wl.total_desc and np.array_equal(sums, oix.sums)
     got = {}
 
     def collect(row, pair_id, ij, matches):
         got[pair_id] = matches
         return 0
 
-    stats, _ = cm.run_schedule(index, sched, host, verify=collect, workers=2)
+    # centre == "pipeline": the run computes the mean itself (row 0's images summed in their slots)
+    stats, _ = cm.run_schedule(index, sched, host, verify=collect, workers=2, centre=centre == "pipeline")
+    if centre == "pipeline":
+        sums, n_total = index.col_sums()
+        assert n_total == wl.total_desc and np.array_equal(sums, oix.sums)
+        assert stats["h2d_bytes"] == 128 * (wl.total_desc + sum(int(wl.n_desc[i]) for r in sched.rows[1:]
+                                                                for i in r["load"]))
     assert sorted(got) == list(range(len(wl.pairs)))
     assert stats["rows"] == len(sched.rows) and stats["prefetched_rows"] >= 1, stats
     # the marginal-bit exclusions come from the same kernels on a resident index with the same mean

@@ -150,7 +150,9 @@ def test_load_evict_rehash_cycle():
     p = cm.Params.make()
     off = wl.row_off
     oix = oracle.Index(desc, wl.n_desc, oparams(p))
-    index = cm.Index(p, wl.n_desc, arena_bytes=int(cm.index_bytes(p, wl.n_desc) * 0.7))
+    # room for 70 % of the images plus one window's plan (its pair table and per-query lists)
+    plan_room = cm.plan_bytes(p, 12, 12 * 1200, 1200)
+    index = cm.Index(p, wl.n_desc, arena_bytes=int(cm.index_bytes(p, wl.n_desc) * 0.7) + plan_room)
     index.set_mean(oix.sums, int(off[-1]))
     dev = torch.from_numpy(desc).cuda()
     rows_seen = 0
