@@ -54,8 +54,9 @@ def parse():
     ap.add_argument("--vlad-codewords", type=int, default=128,
                     help="codebook size of the VLAD encoding timed beside the matching (0: skip)")
     ap.add_argument("--K", type=int, default=8)
-    ap.add_argument("--tune-pairs", type=int, default=120,
-                    help="pairs of the first block row the autotuner times (0: no tuning)")
+    ap.add_argument("--tune-pairs", type=int, default=600,
+                    help="pairs of the first block row the autotuner times (0: no tuning); the bucket-major "
+                         "form runs one pair per CTA, so a fair sample holds a few pairs per CTA")
     ap.add_argument("--verify-workers", type=int, default=-1,
                     help="CPU threads of the overlapped RANSAC run (-1: all host cores, 0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -425,8 +426,12 @@ def device_forms(args, wl, desc_dev, rows, stream, dev, world, forms, check=None
     for form in forms:
         p = cm.Params.make(rerank=form, algo=args.algo, projection=args.projection, K=args.K)
         sample = pairs[rows[0][:args.tune_pairs]] if args.tune_pairs > 0 else None
+        # plans take the most any thread mapping the tuner may choose needs (the tile form's
+        # hand-over to the tensor-core rerank is larger than the bucket-major form's key lists)
+        mappings = [p] + ([cm.Params.make(rerank=form, algo=a, projection=args.projection, K=args.K)
+                           for a in ("bucket", "tile", "warp")] if sample is not None and args.algo == "auto" else [])
         arena = (cm.index_bytes(p, wl.n_desc, inplace=True) + cm.PLAN_HEADROOM +
-                 sum(cm.pairs_plan_bytes(p, wl.n_desc, pairs[r]) for r in rows))
+                 sum(max(cm.pairs_plan_bytes(q, wl.n_desc, pairs[r]) for q in mappings) for r in rows))
         if sample is not None:   # the tuner's plan and decision scratch
             arena += cm.pairs_plan_bytes(p, wl.n_desc, sample) + 4 * int(wl.n_desc[sample[:, 0]].sum()) + (1 << 20)
         tuned = None
@@ -976,6 +981,13 @@ def run_sharded(args, rank, world, make_engine):
             "e2e": e2e, "gpu_launches": int(args.steps * sum(c[5] for c in parts))}
 
 
+def timed_leg(legs, name, fn):
+    t0 = time.time()
+    r = fn()
+    legs[name] = round(time.time() - t0, 1)
+    return r
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2505_22089_b300 as cm
@@ -1012,17 +1024,22 @@ def run_ours(args, rank, world, local):
     nn_sel = (np.sort(np.random.default_rng(123).choice(len(pairs), min(args.nn_pairs, len(pairs)), replace=False))
               if args.nn_pairs > 0 else np.zeros(0, np.int64))
     desc_dev = host.to(dev, non_blocking=False)
+    legs = {"generate": round(gen_s, 1)}
+    t_leg = time.time()
     fr = device_forms(args, wl, desc_dev, rows, stream, dev, world, forms,
                       check=sample if sample is not None else (np.zeros(0, np.int64),) * 3, extra=nn_sel)
     head = fr[args.rerank]
     got, sums = head.pop("_got"), head.pop("_sums")
     head_p = head.pop("_p")
     gpu_rows = {k: v[0] for k, v in got["full"].items()}
+    legs["device_forms"], t_leg = round(time.time() - t_leg, 1), time.time()
     vl = vlad_encoding(args, wl, desc_dev, host.numpy(), stream, world, dev) if args.vlad_codewords > 0 else None
+    legs["vlad"], t_leg = round(time.time() - t_leg, 1), time.time()
     ceiling = sweep = None
     if args.nn_pairs > 0:
         ceiling, sweep = exhaustive_leg(args, wl, desc_dev, host.numpy(), sums, pairs, nn_sel, gpu_rows, stream,
                                         world, dev, float(peaks()[0].get("bf16_tflops", 1800.0)))
+        legs["exhaustive_and_sweep"] = round(time.time() - t_leg, 1)
     del desc_dev
     torch.cuda.empty_cache()
     ms = head["ms_per_step"]
@@ -1053,15 +1070,20 @@ def run_ours(args, rank, world, local):
     # ---- end to end through the pipeline call, then the same with CPU verification overlapped
     e2e, verified = (None, None)
     if args.e2e_steps > 0:
+        t_leg = time.time()
         e2e, verified = pipeline_e2e(args, wl, host, kp, stream, world, dev)
+        legs["e2e_and_verified"] = round(time.time() - t_leg, 1)
 
     # ---- plain per-pair form (no schedule): upload both images, hash, match, download, free
+    t_leg = time.time()
     plain = plain_per_pair(args, wl, host, sums, stream, dev) if args.plain_pairs > 0 else None
+    legs["plain"], t_leg = round(time.time() - t_leg, 1), time.time()
 
     # ---- the FP64 oracle on its sample (rank 0 at N=1): agreement, and the CPU baseline from its timing
     cpu = base = None
     if check:
         cpu, base = oracle_check(wl, host.numpy(), head_p, pairs, *sample, got, sums, args.rerank)
+        legs["oracle_check"] = round(time.time() - t_leg, 1)
         cpu["fp64_rechecks_per_step"] = head["fp64_rechecks_per_step"]
         cpu["fp8_top2_swaps_per_step"] = head["fp8_top2_swaps_per_step"]
     del got
@@ -1087,8 +1109,11 @@ def run_ours(args, rank, world, local):
         "forms": forms_out,
         "plain_fp32_per_pair": plain,
         "pipeline_verified": verified,
-        "schedules": schedule_comparison(args, wl, p, stream, world, dev) if world == 1 else None,
-        "configs": config_lines(args, stream, dev) if (world == 1 and args.configs == "all") else None,
+        "schedules": timed_leg(legs, "schedules", lambda: schedule_comparison(args, wl, p, stream, world, dev)
+                               if world == 1 else None),
+        "configs": timed_leg(legs, "configs", lambda: config_lines(args, stream, dev)
+                             if (world == 1 and args.configs == "all") else None),
+        "leg_seconds": legs,
         "gpu_launches": args.steps * head["graph_kernels"],
         "roofline": roofline,
         "vlad": vl,

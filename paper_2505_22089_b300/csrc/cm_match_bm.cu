@@ -265,6 +265,8 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
                                               (reinterpret_cast<uintptr_t>(Ji + d0 + (uint32_t)c * kChunk) & 15);
                     const int n = (int)min((uint32_t)kChunk, nd - (uint32_t)c * kChunk);
                     int i = 0;
+                    // a candidate whose distance is not above the K-th kept one is buffered with its
+                    // index (the index is read only for those; the exact key order is settled in flush)
                     for (; i + 4 <= n; i += 4) {
                         // room for this step's 4 hits in every lane's buffer (counts carry over chunks)
                         if (__any_sync(kFull, cnt > kHitCap - 4)) {
