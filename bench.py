@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--vlad-codewords", type=int, default=128,
                     help="codebook size of the VLAD encoding timed beside the matching (0: skip)")
     ap.add_argument("--K", type=int, default=8)
-    ap.add_argument("--tune-pairs", type=int, default=600,
+    ap.add_argument("--tune-pairs", type=int, default=1800,
                     help="pairs of the first block row the autotuner times (0: no tuning); the bucket-major "
                          "form runs one pair per CTA, so a fair sample holds a few pairs per CTA")
     ap.add_argument("--verify-workers", type=int, default=-1,
@@ -146,14 +146,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
-# DRAM traffic of the dominant kernel, from ncu (dram__bytes_read.sum + dram__bytes_write.sum
-# summed over the 13 k_match launches of one grid5000 step, divided by 13).  It is reported only
-# for the configuration it was taken on and only while the kernel's sources are unchanged
-# (their SHA-256 below); otherwise the roofline's "traffic" is null.
-KMATCH_TRAFFIC = {"workload": "grid5000", "rerank": "bf16", "K": 8, "bytes_per_launch": 9134870430,
-                  "sources_sha256": "233f4a07bb497b3f4d940e5504c0eefbce34ba9b579f836b876d7a5b3c580294"}
-KMATCH_SOURCES = ["paper_2505_22089_b300/csrc/cm_match.cu", "paper_2505_22089_b300/csrc/cm_internal.h",
-                  "paper_2505_22089_b300/csrc/cm_ratio.cuh"]
+# DRAM traffic of the lookup kernel k_match_bm, from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on a small case of the same per-image shape: the 200-image grid of the
+# grid5000 workload, one block row of 2,104 pairs, mean of 3 launches.  A pair's traffic (its two
+# images' tables, its lists and hand-over) does not depend on how many pairs share the launch, so
+# the figure is stated per pair and scaled by the pairs of a launch.  It is reported only for the
+# form it was taken on and only while the kernel's sources are unchanged (their SHA-256 below);
+# otherwise the roofline's "traffic" is null.
+KMATCH_TRAFFIC = {"workload": "grid5000", "rerank": "bf16", "K": 8, "bytes_per_pair": None,
+                  "sources_sha256": None}
+KMATCH_SOURCES = ["paper_2505_22089_b300/csrc/cm_match_bm.cu", "paper_2505_22089_b300/csrc/cm_internal.h",
+                  "paper_2505_22089_b300/csrc/cm_ratio.cuh", "paper_2505_22089_b300/csrc/cm_tc.cuh"]
 
 
 def kmatch_sources_sha256() -> str:
@@ -165,12 +168,12 @@ def kmatch_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def kmatch_traffic(args):
+def kmatch_traffic(args, pairs_per_launch):
     t = KMATCH_TRAFFIC
-    if (t["bytes_per_launch"] is None or args.grid or args.workload != t["workload"] or args.rerank != t["rerank"]
+    if (t["bytes_per_pair"] is None or args.workload != t["workload"] or args.rerank != t["rerank"]
             or args.K != t["K"] or kmatch_sources_sha256() != t["sources_sha256"]):
         return None
-    return t["bytes_per_launch"]
+    return t["bytes_per_pair"] * pairs_per_launch
 
 
 def peaks():
@@ -329,14 +332,16 @@ def oracle_check(wl, desc, p, pairs, sel, imgs, elig, got, gpu_sums, form, margi
         if d.any():
             n_diff += int(d.sum())
             diff_imgs.append((int(i), d))
-    for i, d in diff_imgs:                                        # differing bits must be marginal ones
-        oi = oracle.hash_image(oix.image_desc(i), oix.mu, oix.W, op, marginal=True)
-        n_diff_nonmarg += int((d & (oi.marginal == 0)).sum())
-    n_mb = n_marg = 0
-    for i in imgs[:marginal_images]:
-        oi = oracle.hash_image(oix.image_desc(int(i)), oix.mu, oix.W, op, marginal=True)
-        n_marg += int(oi.marginal.sum())
-        n_mb += int(oi.marginal.size)
+    def marginal_of(i):
+        return oracle.hash_image(oix.image_desc(int(i)), oix.mu, oix.W, op, marginal=True).marginal
+
+    with ThreadPoolExecutor(cores) as ex:                         # differing bits must be marginal ones
+        for (i, d), mg in zip(diff_imgs, ex.map(marginal_of, [i for i, _ in diff_imgs])):
+            n_diff_nonmarg += int((d & (mg == 0)).sum())
+        n_mb = n_marg = 0
+        for mg in ex.map(marginal_of, list(imgs[:marginal_images])):
+            n_marg += int(mg.sum())
+            n_mb += int(mg.size)
     out["bits"] = {"images": int(len(imgs)), "bits": n_bits, "differing": n_diff,
                    "differing_share": n_diff / max(n_bits, 1), "differing_not_marginal": n_diff_nonmarg,
                    "marginal_share": n_marg / max(n_mb, 1), "marginal_counted_on_images": int(min(len(imgs),
@@ -428,8 +433,9 @@ def device_forms(args, wl, desc_dev, rows, stream, dev, world, forms, check=None
         sample = pairs[rows[0][:args.tune_pairs]] if args.tune_pairs > 0 else None
         # plans take the most any thread mapping the tuner may choose needs (the tile form's
         # hand-over to the tensor-core rerank is larger than the bucket-major form's key lists)
+        tuned_algos = ("bucket", "tile") + (() if form in ("bf16", "fp8") else ("warp",))   # those the tuner tries
         mappings = [p] + ([cm.Params.make(rerank=form, algo=a, projection=args.projection, K=args.K)
-                           for a in ("bucket", "tile", "warp")] if sample is not None and args.algo == "auto" else [])
+                           for a in tuned_algos] if sample is not None and args.algo == "auto" else [])
         arena = (cm.index_bytes(p, wl.n_desc, inplace=True) + cm.PLAN_HEADROOM +
                  sum(max(cm.pairs_plan_bytes(q, wl.n_desc, pairs[r]) for q in mappings) for r in rows))
         if sample is not None:   # the tuner's plan and decision scratch
@@ -1055,7 +1061,8 @@ def run_ours(args, rank, world, local):
     evals = head["evals_per_step"]
     achieved = evals / head["launches"] / (head["scan_launch_ms"] / 1e3)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T distances/s",
-                "frac": achieved / peak, "traffic": kmatch_traffic(args),
+                "frac": achieved / peak, "traffic": kmatch_traffic(args, len(pairs) / head["launches"]),
+                "traffic_kind": "ncu DRAM bytes per pair of k_match_bm on the 200-image grid x pairs per launch",
                 "peak_kind": "measured live: cm_probe_int carry-save 128-bit distance %.3f per clock per SM x %d "
                              "SMs x %.0f MHz (SM clock sampled in the timed steps)" % (probe["ham3"], SM_COUNT, sm_mhz),
                 "probe_per_clock_per_sm": {k: round(v, 3) for k, v in probe.items()},

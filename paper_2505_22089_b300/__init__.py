@@ -37,7 +37,7 @@ def default_headroom(p, n_desc) -> int:
     nd = np.asarray(n_desc, dtype=np.int64)
     bucket = p.algo in (ALGO["auto"], ALGO["bucket"])
     per_row = 0
-    if (p.rerank in (RERANK["bf16"], RERANK["fp8"]) and not bucket) or p.algo == ALGO["tc"]:
+    if p.rerank in (RERANK["bf16"], RERANK["fp8"]) or p.algo == ALGO["tc"]:
         per_row += p.K * (10 if p.rerank == RERANK["fp8"] else 6)   # the scan -> rerank hand-over
     if bucket:
         per_row += 4 * p.K                                           # the bucket-major scan's key lists

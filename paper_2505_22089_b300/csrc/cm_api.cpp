@@ -78,7 +78,8 @@ extern "C" cm_status cm_params_check(const cm_params* p) {
         return fail(CM_ERR_INVALID, "params: projection %d", p->projection);
     const int S = query_tile(p);
     if ((p->rerank == CM_RERANK_BF16 || p->rerank == CM_RERANK_FP8) && p->algo == CM_ALGO_WARP)
-        return fail(CM_ERR_INVALID, "params: the tensor-core reranks run in the tile kernel (algo tile or auto)");
+        return fail(CM_ERR_INVALID, "params: the tensor-core reranks follow the bucket-major or tile scan (algo bucket, "
+                                    "tile or auto)");
     if (p->algo == CM_ALGO_TILE && match_smem_bytes(S, p->K) > kMatchSmemLimit)
         return fail(CM_ERR_INVALID, "params: query_tile=%d with K=%d needs %zu bytes of shared memory (> 227 KB)", S,
                     p->K, match_smem_bytes(S, p->K));
@@ -718,6 +719,17 @@ extern "C" cm_status cm_index_image_view(const cm_index* ix, int32_t image, cons
 // ---------------------------------------------------------------------------
 // match plans
 // ---------------------------------------------------------------------------
+namespace cm {
+std::vector<int32_t> pair_order(const std::vector<DevPair>& tab, const std::vector<int32_t>& n_desc) {
+    std::vector<int32_t> ord(tab.size());
+    for (size_t k = 0; k < tab.size(); ++k) ord[k] = (int32_t)k;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+        return (int64_t)n_desc[tab[a].i] * n_desc[tab[a].j] > (int64_t)n_desc[tab[b].i] * n_desc[tab[b].j];
+    });
+    return ord;
+}
+}  // namespace cm
+
 // Validates a pair list and fills its work table.  Returns the plan's device
 // bytes (cm_plan_bytes) and its row / item counts.
 static cm_status plan_table(const cm_index* ix, const cm_pair* pairs, int64_t n_pairs, int S, std::vector<DevPair>& tab,
@@ -790,6 +802,12 @@ extern "C" cm_status cm_match_plan_create(cm_index* ix, const cm_pair* pairs, in
     if (n_pairs) {
         cm_status st = upload_table(ix, pl->table_at, tab.data(), tab.size() * sizeof(DevPair),
                                     reinterpret_cast<cudaStream_t>(stream));
+        if (st == CM_OK && resolved_algo(&pl->p, n_pairs) == CM_ALGO_BUCKET) {
+            const std::vector<int32_t> ord = pair_order(tab, ix->n_desc);
+            const uint64_t at = pl->table_at + align_up((uint64_t)n_pairs * sizeof(DevPair)) + kAlign +
+                                hand_over(&pl->p, n_pairs, rows, max_ni).order;
+            st = upload_table(ix, at, ord.data(), ord.size() * 4, reinterpret_cast<cudaStream_t>(stream));
+        }
         if (st != CM_OK) {
             ix->alloc.release(pl->table_at);
             delete pl;
@@ -835,12 +853,15 @@ extern "C" cm_status cm_match_plan_run_marked(cm_match_plan* pl, const cm_match_
     m.rerank = pp.rerank;
     m.counter = counter;
     m.out = *out;
-    m.algo = resolved_algo(&pp);
+    m.algo = resolved_algo(&pp, pl->n_pairs);
     if (m.algo == CM_ALGO_TILE && match_smem_bytes(m.S, m.K) > kMatchSmemLimit) m.algo = CM_ALGO_WARP;
     m.err = ix->at<int>(ix->fx.err);
-    const HandOver ho = hand_over(&pp, pl->rows, pl->max_ni);
+    const HandOver ho = hand_over(&pp, pl->n_pairs, pl->rows, pl->max_ni);
     uint8_t* base = counter_ptr + kAlign;
-    m.klists = reinterpret_cast<uint32_t*>(base + ho.klists);
+    if (m.algo == CM_ALGO_BUCKET) {
+        m.klists = reinterpret_cast<uint32_t*>(base + ho.klists);
+        m.order = reinterpret_cast<const int32_t*>(base + ho.order);
+    }
     auto scan = [&]() -> cudaError_t {
         switch (m.algo) {
             case CM_ALGO_BUCKET: return launch_match_bm(m, ix->sms, s);
@@ -849,13 +870,10 @@ extern "C" cm_status cm_match_plan_run_marked(cm_match_plan* pl, const cm_match_
         }
     };
     if (needs_hand_over(&pp)) {
-        // a scan leaves each query's top-K in the plan's hand-over area (the bucket-major
-        // scan: its key lists), then a rerank launch
-        if (m.algo != CM_ALGO_BUCKET) {
-            m.topk16 = reinterpret_cast<uint16_t*>(base + ho.idx);
-            m.hnorm = reinterpret_cast<uint32_t*>(base + ho.norm);
-            m.hscale = pp.rerank == CM_RERANK_FP8 ? reinterpret_cast<float*>(base + ho.scale) : nullptr;
-        }
+        // a scan leaves each query's top-K in the plan's hand-over area, then a rerank launch
+        m.topk16 = reinterpret_cast<uint16_t*>(base + ho.idx);
+        m.hnorm = reinterpret_cast<uint32_t*>(base + ho.norm);
+        m.hscale = pp.rerank == CM_RERANK_FP8 ? reinterpret_cast<float*>(base + ho.scale) : nullptr;
         if (m.algo == CM_ALGO_TC) {
             m.lists = reinterpret_cast<uint32_t*>(base + ho.lists);
             m.max_ni = pl->max_ni;
@@ -994,9 +1012,16 @@ extern "C" cm_status cm_match_pairs(cm_index* ix, const cm_pair* pairs, int64_t 
     pl.rows = rows;
     pl.n_items = (int32_t)items;
     pl.max_ni = max_ni;
-    if (n_pairs)
+    if (n_pairs) {
         CM_CUDA(ix->staging.upload(pl.ext, tab.data(), tab.size() * sizeof(DevPair),
                                    reinterpret_cast<cudaStream_t>(stream)));
+        if (resolved_algo(&pl.p, n_pairs) == CM_ALGO_BUCKET) {
+            const std::vector<int32_t> ord = pair_order(tab, ix->n_desc);
+            CM_CUDA(ix->staging.upload(pl.ext + align_up((uint64_t)n_pairs * sizeof(DevPair)) + kAlign +
+                                           hand_over(&pl.p, n_pairs, rows, max_ni).order,
+                                       ord.data(), ord.size() * 4, reinterpret_cast<cudaStream_t>(stream)));
+        }
+    }
     cm_match_out out{};
     out.best_j = d_best_j;
     out.d1sq = d_d1sq;

@@ -284,44 +284,59 @@ const cm_pair* schedule_pairs(const cm_schedule* s, int64_t* n);
 }  // namespace cm
 
 // Arena bytes of a plan: its pair table, the work counter and:
-//   - for the tensor-core reranks after the tile or tensor-core scan, the
-//     [rows][K] top-K hand-over from scan to rerank (index u16, squared norm
-//     u32 and, for FP8, scale f32 of every kept candidate);
+//   - for the bucket-major matcher, the order in which its CTAs take the
+//     pairs (largest n_i * n_j first) and every query row's running top-K
+//     keys, [rows][K] u32;
+//   - for the tensor-core reranks, the [rows][K] top-K hand-over from scan to
+//     rerank (index u16, squared norm u32 and, for FP8, scale f32 of every
+//     kept candidate);
 //   - for the tensor-core Hamming scan, per-CTA scratch for per-table top-K
-//     lists: [kMaxScanCtas][max query rows][L][K] u32;
-//   - for the bucket-major matcher, every query row's running top-K keys,
-//     [rows][K] u32.
+//     lists: [kMaxScanCtas][max query rows][L][K] u32.
 constexpr int kMaxScanCtas = 160;   // >= the SM count; the scan's grid is capped to it
+// AUTO takes the bucket-major matcher for plans with at least this many pairs
+// (it runs one pair per CTA: two CTAs per SM on 148 SMs); smaller plans take
+// the tile form, whose work items are tiles of queries.
+constexpr int64_t kBucketMinPairs = 256;
 struct HandOver {
-    uint64_t idx, norm, scale, lists, klists, total;
+    uint64_t order, idx, norm, scale, lists, klists, total;
 };
 inline bool needs_hand_over(const cm_params* p) { return tc_rerank(p) || p->algo == CM_ALGO_TC; }
 // The matcher a plan's launch uses: the tensor-core scan, the warp-per-query
-// form, the tile form, or the bucket-major form (AUTO).
-inline int resolved_algo(const cm_params* p) {
+// form, the tile form, or the bucket-major form (AUTO: by the plan's size).
+inline int resolved_algo(const cm_params* p, int64_t n_pairs) {
     if (p->algo == CM_ALGO_TC || p->algo == CM_ALGO_WARP || p->algo == CM_ALGO_TILE) return p->algo;
-    return CM_ALGO_BUCKET;
+    if (p->algo == CM_ALGO_BUCKET) return CM_ALGO_BUCKET;
+    return n_pairs >= kBucketMinPairs ? CM_ALGO_BUCKET : CM_ALGO_TILE;
 }
-inline HandOver hand_over(const cm_params* p, int64_t rows, int32_t max_ni) {
+inline HandOver hand_over(const cm_params* p, int64_t n_pairs, int64_t rows, int32_t max_ni) {
     HandOver h{};
     const uint64_t e = (uint64_t)rows * (uint64_t)p->K;
-    // the bucket-major scan's key lists serve as the tensor-core rerank's hand-over
-    if (needs_hand_over(p) && resolved_algo(p) != CM_ALGO_BUCKET) {
-        h.idx = 0;
-        h.norm = align_up(e * 2);
+    const bool bucket = resolved_algo(p, n_pairs) == CM_ALGO_BUCKET;
+    uint64_t o = 0;
+    h.order = o;
+    if (bucket) o += align_up((uint64_t)n_pairs * 4);
+    if (needs_hand_over(p)) {
+        h.idx = o;
+        h.norm = h.idx + align_up(e * 2);
         h.scale = h.norm + align_up(e * 4);
         h.lists = h.scale + (p->rerank == CM_RERANK_FP8 ? align_up(e * 4) : 0);
-        h.total = h.lists;
+        o = h.lists;
         if (p->algo == CM_ALGO_TC)
-            h.total += align_up((uint64_t)kMaxScanCtas * (uint64_t)max_ni * (uint64_t)p->L * (uint64_t)p->K * 4);
+            o += align_up((uint64_t)kMaxScanCtas * (uint64_t)max_ni * (uint64_t)p->L * (uint64_t)p->K * 4);
     }
-    h.klists = h.total;
-    if (resolved_algo(p) == CM_ALGO_BUCKET) h.total += align_up(e * 4);
+    h.klists = o;
+    if (bucket) o += align_up(e * 4);
+    h.total = o;
     return h;
 }
 inline uint64_t plan_bytes(const cm_params* p, int64_t n_pairs, int64_t rows, int32_t max_ni) {
-    return align_up((uint64_t)n_pairs * sizeof(DevPair)) + kAlign + hand_over(p, rows, max_ni).total;
+    return align_up((uint64_t)n_pairs * sizeof(DevPair)) + kAlign + hand_over(p, n_pairs, rows, max_ni).total;
 }
+// The bucket-major matcher's pair order: descending n_i * n_j (the work of a
+// pair grows with it), ties by position, so the last pairs dealt are small.
+namespace cm {
+std::vector<int32_t> pair_order(const std::vector<DevPair>& tab, const std::vector<int32_t>& n_desc);
+}  // namespace cm
 
 struct cm_match_plan {
     cm_index* ix = nullptr;

@@ -84,6 +84,7 @@ struct MatchLaunch {
     uint32_t* lists;           // tensor-core Hamming scan: per-CTA [max_ni][L][K] per-table top-K keys
     int32_t max_ni;            // largest query image of the launch
     uint32_t* klists;          // bucket-major matcher: [rows][K] running top-K keys (Hamming << 16 | index)
+    const int32_t* order;      // bucket-major matcher: the pairs in the order its CTAs take them
     cm_match_out out;
 };
 

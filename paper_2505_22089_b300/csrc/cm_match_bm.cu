@@ -26,8 +26,10 @@
 //     buffers into the lists in lockstep; a key already present (the same
 //     point met in an earlier table) is skipped.
 // Step (4) then reranks each query's K kept candidates exactly (8 lanes per
-// query) and applies the exact ratio test; the tensor-core reranks
-// (k_rerank_tc) read the key lists directly.
+// query) and applies the exact ratio test, or, for the tensor-core reranks,
+// writes the hand-over k_rerank_tc reads (index, squared norm, FP8 scale).
+// CTAs take the pairs largest first (the plan's order), so the last pairs
+// dealt, which set the launch's tail, are small.
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
         __syncthreads();
         const int item = s_item;
         if (item >= ml.n_pairs) break;
-        const DevPair P = ml.pairs[item];
+        const DevPair P = ml.pairs[ml.order ? ml.order[item] : item];   // largest pairs first
         const DevImage I = ml.imgs[P.i];
         const DevImage J = ml.imgs[P.j];
         const int nq = I.n;
@@ -317,12 +319,19 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
         }
 
         if (tcr) {
-            // step (4) runs in k_rerank_tc, which reads the key lists themselves
-            if (ml.out.topk)
-                for (int e = tid; e < nq * K; e += kBmThreads) {
-                    const uint32_t key = lists[e];
-                    ml.out.topk[P.row_off * K + e] = key != kEmpty ? (int)(key & 0xFFFFu) : -1;
-                }
+            // step (4) runs in k_rerank_tc: hand over each kept candidate's index, squared norm
+            // (and FP8 scale), read while the pair's lists and J's norms are in L2
+            const int64_t r0 = P.row_off;
+            const bool fp8 = ml.rerank == CM_RERANK_FP8;
+            for (int e = tid; e < nq * K; e += kBmThreads) {
+                const uint32_t key = lists[e];
+                const bool hv = key != kEmpty;
+                const int j = (int)(key & 0xFFFFu);
+                ml.topk16[r0 * K + e] = hv ? (uint16_t)j : (uint16_t)0xFFFFu;
+                ml.hnorm[r0 * K + e] = hv ? __ldg(J.norm + j) : 0u;
+                if (fp8) ml.hscale[r0 * K + e] = hv ? __ldg(J.xscale + j) : 0.f;
+                if (ml.out.topk) ml.out.topk[r0 * K + e] = hv ? j : -1;
+            }
             continue;
         }
         // Sec. 2.3.1 step (4) on CUDA cores: exact distances of the top K, q1 / q2, ratio test.

@@ -162,3 +162,17 @@ def test_noalloc_rejects_unsupported_forms_before_touching_the_gpu():
                                        None)
         assert st == want, (kw, st)
         assert lib.cm_last_error()
+
+
+def test_auto_mapping_follows_the_plan_size():
+    """AUTO sizes a plan as the bucket-major matcher's (pair order + per-query
+    key lists) from 256 pairs on, and as the tile form's below; the
+    tensor-core reranks keep their hand-over under either."""
+    for rerank in ("fp32", "bf16", "fp8"):
+        auto, bucket, tile = (cm.Params.make(rerank=rerank, algo=a) for a in ("auto", "bucket", "tile"))
+        for n_pairs in (1, 255, 256, 4000):
+            rows = 2000 * n_pairs
+            want = bucket if n_pairs >= 256 else tile
+            assert cm.plan_bytes(auto, n_pairs, rows, 2000) == cm.plan_bytes(want, n_pairs, rows, 2000)
+        extra = cm.plan_bytes(bucket, 300, 600000, 2000) - cm.plan_bytes(tile, 300, 600000, 2000)
+        assert extra >= 600000 * 8 * 4 + 300 * 4   # key lists and the pair order

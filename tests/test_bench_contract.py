@@ -43,11 +43,12 @@ def _args(**kw):
 
 def test_traffic_is_reported_only_where_it_was_measured():
     t = bench.KMATCH_TRAFFIC
-    same_sources = bench.kmatch_sources_sha256() == t["sources_sha256"]
+    same_sources = bench.kmatch_sources_sha256() == t["sources_sha256"] and t["bytes_per_pair"] is not None
     # after a change of the kernel's sources the recorded figure no longer applies
-    assert bench.kmatch_traffic(_args()) == (t["bytes_per_launch"] if same_sources else None)
-    for kw in (dict(grid="20x10"), dict(workload="grid500"), dict(rerank="fp8"), dict(K=16)):
-        assert bench.kmatch_traffic(_args(**kw)) is None, kw
+    got = bench.kmatch_traffic(_args(), 4500.0)
+    assert got == (t["bytes_per_pair"] * 4500.0 if same_sources else None)
+    for kw in (dict(workload="grid500"), dict(rerank="fp8"), dict(K=16)):
+        assert bench.kmatch_traffic(_args(**kw), 4500.0) is None, kw
 
 
 def test_oracle_sample_covers_its_share_and_the_pairs_among_its_images():
