@@ -73,9 +73,6 @@ struct RR {
     static constexpr int ACC = ACC_FIT < 8 ? ACC_FIT : 8;  // a multiple of the epilogue groups, which take turns
     static constexpr int STEPS = FP8 ? 4 : 8;              // MMAs of 32 bytes of K each
     static constexpr int CPR = FP8 ? 8 : 16;               // 16-byte chunks per row copy
-    static constexpr int ROWS = 128 + NB;                   // staged rows per sub-tile
-    static constexpr int CHUNKS = ROWS * CPR;
-    static constexpr int PER_THREAD = (CHUNKS + PROD - 1) / PROD;
     // stages (1024-aligned) + barriers: full/empty per stage, full/empty per accumulator
     static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 8 * (2 * STAGES + 2 * ACC) + 64;
     static_assert(ACC % EPI == 0, "accumulators are dealt to the epilogue groups in turn");
@@ -235,9 +232,25 @@ __global__ void __launch_bounds__(RR<K, FP8>::THREADS, RR<K, FP8>::CTAS) k_reran
     // counter `it` (stage it % STAGES, accumulator it % ACC) agrees across roles.
 
     if (warp < C::PROD_WARPS) {
-        // ---------------- producers: thread t copies chunks t, t + PROD, ... of each sub-tile
-        // (chunk e: staged row e / CPR, 16-byte chunk e % CPR; rows 0-127 = A, then B)
+        // ---------------- producers.  Thread t copies the 16-byte chunk c = t % CPR of the
+        // RPT consecutive A rows r0 = RPT * (t / CPR) .. r0 + RPT - 1 (the same chunk of
+        // every row, so the swizzle term of each row is fixed at compile time up to c)
+        // and of the B rows t / CPR + G q.  A warp's copies of one row index cover whole
+        // rows (coalesced).
+        constexpr int RPT = 128 * C::CPR / C::PROD;   // A rows per thread
+        constexpr int G = C::PROD / C::CPR;            // threads per chunk column
+        constexpr int NW = RPT / 2;                    // 32-bit words of RPT 16-bit indices
+        // the RPT indices of a thread's rows are contiguous in the hand-over; one vector
+        // load takes them when the sub-tile's first row keeps it aligned
+        constexpr int VB = 2 * RPT < 16 ? 2 * RPT : 16;
+        constexpr bool VEC = (2 * K) % VB == 0;
+        static_assert(RPT % 2 == 0 && 128 % RPT == 0, "rows per producer thread");
         const int rb = FP8 ? 128 : 256;   // bytes per row copy
+        const int c = tid % C::CPR, rg = tid / C::CPR;
+        const int r0 = RPT * rg;
+        const uint32_t cofs = (uint32_t)(c >> 3) * C::A_HALF;   // 128-byte column block of chunk c
+        const uint32_t bofs = (uint32_t)(c >> 3) * C::B_HALF;
+        const int c8 = c & 7;
         int it = 0;          // sub-tiles issued
         Cursor<true> cursor;
         bool ok = true;
@@ -250,38 +263,63 @@ __global__ void __launch_bounds__(RR<K, FP8>::THREADS, RR<K, FP8>::CTAS) k_reran
             }
             return false;
         };
-        // candidate index of each of this thread's chunks (kNoCand: not a candidate row);
-        // loaded one sub-tile before it is used
-        auto idx_of = [&](const SubTile& t, uint32_t (&jr)[C::PER_THREAD]) {
+        // candidate indices of the thread's rows, two per word (kNoCand: no candidate);
+        // loaded one sub-tile before they are used
+        auto idx_of = [&](const SubTile& t, uint32_t (&jw)[NW]) {
+            const int64_t e0 = t.row * K + r0;
+            if (VEC && ml.topk16 && (r0 + RPT - 1) / K < t.nq) {
+                if constexpr (VB == 16) {
+                    const uint4* p = reinterpret_cast<const uint4*>(ml.topk16 + e0);
 #pragma unroll
-            for (int q = 0; q < C::PER_THREAD; ++q) {
-                const int r = (tid + q * C::PROD) / C::CPR;
-                jr[q] = (r < 128 && r / K < t.nq) ? cand_index(ml, t.row * K + r) : (uint32_t)kNoCand;
+                    for (int w = 0; w < NW / 4; ++w) {
+                        const uint4 v = __ldg(p + w);
+                        jw[4 * w] = v.x;
+                        jw[4 * w + 1] = v.y;
+                        jw[4 * w + 2] = v.z;
+                        jw[4 * w + 3] = v.w;
+                    }
+                } else if constexpr (VB == 8) {
+                    const uint2 v = __ldg(reinterpret_cast<const uint2*>(ml.topk16 + e0));
+                    jw[0] = v.x;
+                    jw[1] = v.y;
+                } else {
+                    jw[0] = __ldg(reinterpret_cast<const uint32_t*>(ml.topk16 + e0));
+                }
+                return;
+            }
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const int ra = r0 + 2 * w, rc = ra + 1;
+                const uint32_t lo = ra / K < t.nq ? cand_index(ml, e0 + 2 * w) : (uint32_t)kNoCand;
+                const uint32_t hi = rc / K < t.nq ? cand_index(ml, e0 + 2 * w + 1) : (uint32_t)kNoCand;
+                jw[w] = lo | (hi << 16);
             }
         };
         // copies sub-tile t into stage it % STAGES; the stage goes to the MMA once every
         // producer thread's copies into it have landed
-        auto issue = [&](const SubTile& t, const uint32_t (&jr)[C::PER_THREAD]) -> bool {
+        auto issue = [&](const SubTile& t, const uint32_t (&jw)[NW]) -> bool {
             const int s = it % C::STAGES;
             const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
             if (!warp_wait(&empty[s], ph ^ 1u, abort_flag)) return false;
-            const uint32_t A = tc::smem_addr(ring + (size_t)s * C::STAGE);
-            const uint32_t B = A + C::HALVES * C::A_HALF;
-            const unsigned char* qrow = t.ixq + (size_t)t.q0 * rb;   // a valid row for padding
+            const uint32_t A = tc::smem_addr(ring + (size_t)s * C::STAGE) + cofs;
+            const uint32_t B = tc::smem_addr(ring + (size_t)s * C::STAGE) + C::HALVES * C::A_HALF + bofs;
+            const unsigned char* qrow = t.ixq + (size_t)t.q0 * rb + c * 16;   // a valid row for padding
+            const unsigned char* jrow = t.jxq + c * 16;
 #pragma unroll
-            for (int q = 0; q < C::PER_THREAD; ++q) {
-                const int e = tid + q * C::PROD;
-                if (e < C::CHUNKS) {
-                    const int r = e / C::CPR, c = e % C::CPR;
-                    const int h = c >> 3, c8 = c & 7;     // 128-byte column block, chunk in it
-                    const uint32_t dst = r < 128
-                        ? A + (uint32_t)h * C::A_HALF + (uint32_t)r * 128u + (uint32_t)((c8 ^ (r & 7)) << 4)
-                        : B + (uint32_t)h * C::B_HALF + (uint32_t)(r - 128) * 128u +
-                              (uint32_t)((c8 ^ ((r - 128) & 7)) << 4);
-                    const unsigned char* src = r < 128 ? (jr[q] != kNoCand ? t.jxq + (size_t)jr[q] * rb : qrow)
-                                                        : qrow + (size_t)(r - 128 < t.nq ? r - 128 : 0) * rb;
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src + c * 16)
-                                 : "memory");
+            for (int q = 0; q < RPT; ++q) {
+                const int r = r0 + q;
+                const uint32_t j = (jw[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+                const uint32_t dst = A + (uint32_t)r * 128u + (uint32_t)((c8 ^ (r & 7)) << 4);
+                const unsigned char* src = j != kNoCand ? jrow + (size_t)j * rb : qrow;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
+            }
+#pragma unroll
+            for (int q = 0; q < (C::NB + G - 1) / G; ++q) {
+                const int b = rg + G * q;
+                if (b < C::NB) {
+                    const uint32_t dst = B + (uint32_t)b * 128u + (uint32_t)((c8 ^ (b & 7)) << 4);
+                    const unsigned char* src = qrow + (size_t)(b < t.nq ? b : 0) * rb;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
                 }
             }
             // this thread's arrival on the stage, made when all its copies so far have landed
@@ -293,7 +331,7 @@ __global__ void __launch_bounds__(RR<K, FP8>::THREADS, RR<K, FP8>::CTAS) k_reran
         // ping-pong between two register sets, so a prefetched index is never copied
         // (a copy would wait for the load)
         SubTile tA{}, tB{};
-        uint32_t jA[C::PER_THREAD], jB[C::PER_THREAD];
+        uint32_t jA[NW], jB[NW];
         bool hA = next(tA), hB = false;
         if (hA) idx_of(tA, jA);
         while (hA) {
