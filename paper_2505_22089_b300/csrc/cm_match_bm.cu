@@ -63,13 +63,17 @@ __device__ __forceinline__ uint32_t ham128(uint4 a, uint4 b) {
     return (uint32_t)__popc(s2) + 2u * (uint32_t)(__popc(c1) + __popc(c2));
 }
 
-// Insert key into the ascending list s unless already present.
+// Insert key into the ascending list s unless already present.  check = false
+// skips the presence test: in the first table a database point meets each
+// query at most once (it lies in one bucket of that table), so no key repeats.
 template <int K>
-__device__ __forceinline__ void topk_insert(uint32_t (&s)[K], uint32_t key) {
-    bool dup = false;
+__device__ __forceinline__ void topk_insert(uint32_t (&s)[K], uint32_t key, bool check) {
+    if (check) {
+        bool dup = false;
 #pragma unroll
-    for (int i = 0; i < K; ++i) dup |= (s[i] == key);
-    if (dup) return;
+        for (int i = 0; i < K; ++i) dup |= (s[i] == key);
+        if (dup) return;
+    }
 #pragma unroll
     for (int i = K - 1; i > 0; --i) s[i] = max(s[i - 1], min(s[i], key));
     s[0] = min(s[0], key);
@@ -77,11 +81,11 @@ __device__ __forceinline__ void topk_insert(uint32_t (&s)[K], uint32_t key) {
 
 // Lockstep merge of every lane's buffered keys into its list.
 template <int K>
-__device__ __forceinline__ void flush(const uint32_t* __restrict__ col, int cnt, uint32_t (&s)[K]) {
+__device__ __forceinline__ void flush(const uint32_t* __restrict__ col, int cnt, uint32_t (&s)[K], bool check) {
     const int cmax = (int)__reduce_max_sync(kFull, (unsigned)cnt);
     for (int e = 0; e < cmax; ++e) {
         const uint32_t key = e < cnt ? col[e * kBmThreads] : kEmpty;
-        if (key < s[K - 1]) topk_insert<K>(s, key);
+        if (key < s[K - 1]) topk_insert<K>(s, key, check);
     }
 }
 
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
                     for (; i + 4 <= n; i += 4) {
                         // room for this step's 4 hits in every lane's buffer (counts carry over chunks)
                         if (__any_sync(kFull, cnt > kHitCap - 4)) {
-                            flush<K>(col, cnt, s);
+                            flush<K>(col, cnt, s, t > 0);
                             cnt = 0;
                             kh = s[K - 1] >> 16;
                         }
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
                     }
                     for (; i < n; ++i) {
                         if (__any_sync(kFull, cnt > kHitCap - 1)) {
-                            flush<K>(col, cnt, s);
+                            flush<K>(col, cnt, s, t > 0);
                             cnt = 0;
                             kh = s[K - 1] >> 16;
                         }
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
                     break;
                 }
                 seq += (uint32_t)nch;
-                if (__any_sync(kFull, cnt > 0)) flush<K>(col, cnt, s);
+                if (__any_sync(kFull, cnt > 0)) flush<K>(col, cnt, s, t > 0);
                 if (active) store_list<K>(lists + (size_t)q * K, s);
             }
             __syncthreads();
@@ -323,14 +327,21 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
             // (and FP8 scale), read while the pair's lists and J's norms are in L2
             const int64_t r0 = P.row_off;
             const bool fp8 = ml.rerank == CM_RERANK_FP8;
-            for (int e = tid; e < nq * K; e += kBmThreads) {
-                const uint32_t key = lists[e];
+            const int ne = nq * K;
+            // the next entry's key is loaded before this entry's stores (a store could alias
+            // it, so the compiler would not move the load up by itself)
+            uint32_t key = tid < ne ? lists[tid] : kEmpty;
+            for (int e = tid; e < ne; e += kBmThreads) {
+                const uint32_t key_next = e + kBmThreads < ne ? lists[e + kBmThreads] : kEmpty;
                 const bool hv = key != kEmpty;
                 const int j = (int)(key & 0xFFFFu);
+                const uint32_t nv = hv ? __ldg(J.norm + j) : 0u;
+                const float sv = fp8 && hv ? __ldg(J.xscale + j) : 0.f;
                 ml.topk16[r0 * K + e] = hv ? (uint16_t)j : (uint16_t)0xFFFFu;
-                ml.hnorm[r0 * K + e] = hv ? __ldg(J.norm + j) : 0u;
-                if (fp8) ml.hscale[r0 * K + e] = hv ? __ldg(J.xscale + j) : 0.f;
+                ml.hnorm[r0 * K + e] = nv;
+                if (fp8) ml.hscale[r0 * K + e] = sv;
                 if (ml.out.topk) ml.out.topk[r0 * K + e] = hv ? j : -1;
+                key = key_next;
             }
             continue;
         }

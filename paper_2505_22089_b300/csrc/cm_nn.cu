@@ -304,9 +304,9 @@ k_nn_exhaustive(const uint8_t* __restrict__ desc, const int64_t* __restrict__ im
             int j1 = -1;
             for (int c0 = 0; c0 < t.nj; c0 += kNnChunk, ++g) {
                 const uint32_t s = g & 1u, ph = (g >> 1) & 1u;
-                bool got = true;
-                if (lane == 0) got = nn_wait(&accFull[s], ph, abort_flag);
-                if (!__shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0)) { ok = false; break; }
+                // every lane waits itself: its TMEM loads are ordered after the phase only if it saw it
+                const bool got = nn_wait(&accFull[s], ph, abort_flag);
+                if (!__all_sync(0xFFFFFFFFu, got)) { ok = false; break; }
                 tc::fence_after();
                 // the accumulator holds t = |y|^2 - 2 x.y (exact); d^2 = |x|^2 + t is
                 // added at the end.  A group of 16 columns with no t below q2's is

@@ -167,11 +167,13 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, v
     return false;
 }
 
-// The same, decided once per warp (lane 0 polls) so the warp stays converged.
+// The same for a whole warp, which continues only if every lane saw the phase.
+// Every lane waits on the barrier itself: a tcgen05.ld or a shared-memory
+// write that must come after the phase is ordered after it only in a thread
+// that observed the phase.  With lane 0 alone polling and passing its result
+// on by shuffle, some builds read accumulators before the MMA had written them.
 __device__ __forceinline__ bool warp_wait(uint64_t* mbar, uint32_t parity, volatile int* abort_flag) {
-    bool ok = true;
-    if ((threadIdx.x & 31) == 0) ok = wait_or_abort(mbar, parity, abort_flag);
-    return __shfl_sync(0xFFFFFFFFu, ok ? 1 : 0, 0) != 0;
+    return __all_sync(0xFFFFFFFFu, wait_or_abort(mbar, parity, abort_flag));
 }
 
 __device__ __forceinline__ uint32_t exact_d2(const uint8_t* x, const uint8_t* y, int nb) {

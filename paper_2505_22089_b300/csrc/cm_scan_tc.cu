@@ -83,11 +83,11 @@ __device__ __forceinline__ bool sc_wait(uint64_t* mbar, uint32_t parity, volatil
     return false;
 }
 
-// decided once per warp (lane 0 polls) so the warp stays converged
+// decided once per warp, which continues only if every lane saw the phase; each
+// lane waits itself, since the tcgen05 loads and shared-memory writes that
+// follow are ordered after the phase only in a thread that observed it
 __device__ __forceinline__ bool sc_warp_wait(uint64_t* mbar, uint32_t parity, volatile int* abort_flag) {
-    bool ok = true;
-    if ((threadIdx.x & 31) == 0) ok = sc_wait(mbar, parity, abort_flag);
-    return __shfl_sync(0xFFFFFFFFu, ok ? 1 : 0, 0) != 0;
+    return __all_sync(0xFFFFFFFFu, sc_wait(mbar, parity, abort_flag));
 }
 
 __device__ __forceinline__ void named_sync(int id, int count) {
