@@ -128,7 +128,7 @@ __device__ __forceinline__ float offset_byte(uint32_t w, int b) {
 
 size_t match_bm_smem_bytes() {
     return (size_t)kWarps * 2 * kBufBytes + (size_t)kWarps * 2 * 8 + (size_t)kHitCap * kBmThreads * 4 + 256 * 4 +
-           260 * 4;
+           3 * 260 * 4;
 }
 
 template <int K>
@@ -139,6 +139,8 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
     uint32_t* hitbuf = reinterpret_cast<uint32_t*>(mbar + kWarps * 2);                   // [kHitCap][threads]
     uint32_t* order = hitbuf + kHitCap * kBmThreads;                                     // [256] rank -> bucket
     uint32_t* upre = order + 256;                                                        // [B + 1] unit prefix
+    uint32_t* sIo = upre + 260;                                                          // [B + 1] this table's
+    uint32_t* sJo = sIo + 260;                                                           // bucket offsets, I and J
     __shared__ int s_item;
     __shared__ unsigned s_unit;
     __shared__ uint32_t s_stats[3];
@@ -177,6 +179,10 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
             const uint32_t* Io = I.off + t * (B + 1);
             const uint32_t* Jo = J.off + t * (B + 1);
             if (tid < B) order[B - 1 - J.brank[t * 256 + tid]] = (uint32_t)tid;   // longest database run first
+            if (tid <= B) {   // the units read their runs' bounds from shared memory
+                sIo[tid] = Io[tid];
+                sJo[tid] = Jo[tid];
+            }
             __syncthreads();
             if (warp == 0) {
                 // units per bucket rank: ceil(|Q_b| / 32) where the bucket has candidates (in the first
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
                     const int r = lane * per + k;
                     if (r < B) {
                         const uint32_t b = order[r];
-                        const uint32_t qn = Io[b + 1] - Io[b], dn = Jo[b + 1] - Jo[b];
+                        const uint32_t qn = sIo[b + 1] - sIo[b], dn = sJo[b + 1] - sJo[b];
                         local += (qn && (dn || t == 0)) ? (qn + 31) / 32 : 0u;
                     }
                 }
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
                     if (r < B) {
                         upre[r] = run;
                         const uint32_t b = order[r];
-                        const uint32_t qn = Io[b + 1] - Io[b], dn = Jo[b + 1] - Jo[b];
+                        const uint32_t qn = sIo[b + 1] - sIo[b], dn = sJo[b + 1] - sJo[b];
                         run += (qn && (dn || t == 0)) ? (qn + 31) / 32 : 0u;
                     }
                 }
@@ -227,8 +233,8 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
                     if (upre[mid] <= u) lo = mid; else hi = mid;
                 }
                 const uint32_t b = order[lo];
-                const uint32_t pos = Io[b] + (u - upre[lo]) * 32 + lane;
-                const bool active = pos < Io[b + 1];
+                const uint32_t pos = sIo[b] + (u - upre[lo]) * 32 + lane;
+                const bool active = pos < sIo[b + 1];
                 uint32_t q = 0;
                 uint4 qc = make_uint4(0, 0, 0, 0);
                 uint32_t s[K];
@@ -239,7 +245,7 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
                     qc = Ic[pos];
                     if (t > 0) load_list<K>(lists + (size_t)q * K, s);
                 }
-                const uint32_t d0 = Jo[b], nd = Jo[b + 1] - d0;
+                const uint32_t d0 = sJo[b], nd = sJo[b + 1] - d0;
                 const int nch = (int)((nd + kChunk - 1) / kChunk);
                 // lane 0 stages chunk c of the run into buffer (seq + c) & 1
                 auto issue = [&](int c) {
