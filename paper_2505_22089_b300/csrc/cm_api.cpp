@@ -850,6 +850,8 @@ extern "C" cm_status cm_match_plan_run_marked(cm_match_plan* pl, const cm_match_
     m.K = pp.K;
     m.ratio_num = pp.ratio_num;
     m.ratio_den = pp.ratio_den;
+    m.ratio_lo = ratio_band(pp.ratio_num, pp.ratio_den).lo;
+    m.ratio_hi = ratio_band(pp.ratio_num, pp.ratio_den).hi;
     m.rerank = pp.rerank;
     m.counter = counter;
     m.out = *out;

@@ -7,6 +7,18 @@
 
 namespace cm {
 
+// The FP32 band of the ratio test for t_r = num / den (cm_ratio.cuh): a query
+// passes when d1 < lo d2 and fails when d1 > hi d2, with lo = (t_r - 1e-3)^2
+// (-1 when t_r <= 1e-3) and hi = (t_r + 1e-3)^2.  Computed once per launch on
+// the host, so the kernels read both from their parameters.
+struct RatioBand {
+    float lo, hi;
+};
+inline RatioBand ratio_band(int num, int den) {
+    const float tr = (float)num / (float)den;
+    return {tr > 1e-3f ? (tr - 1e-3f) * (tr - 1e-3f) : -1.f, (tr + 1e-3f) * (tr + 1e-3f)};
+}
+
 constexpr int kDim = 128;          // descriptor length (SIFT)
 constexpr int kMaxL = 8;
 constexpr int kMaxM = 8;
@@ -73,6 +85,7 @@ struct MatchLaunch {
     int32_t S;                 // queries per work item
     int32_t L, m, K;
     int32_t ratio_num, ratio_den;
+    float ratio_lo, ratio_hi;  // FP32 band of the ratio test (ratio_band)
     int32_t rerank;
     int32_t algo;              // CM_ALGO_TILE, CM_ALGO_WARP, CM_ALGO_BUCKET or CM_ALGO_TC
     unsigned* counter;         // work counter (zeroed before each launch)

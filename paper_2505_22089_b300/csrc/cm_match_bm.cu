@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(kBmThreads, 2) k_match_bm(MatchLaunch ml) {
                 const int64_t row = P.row_off + q;
                 bool pass = false;
                 uint32_t rc = 0;
-                if (j2 >= 0) pass = ratio_pass(d1, d2, ml.ratio_num, ml.ratio_den, rc);
+                if (j2 >= 0) pass = ratio_pass(d1, d2, ml.ratio_num, ml.ratio_den, ml.ratio_lo, ml.ratio_hi, rc);
                 if (l8 == 0) {
                     rechecks += rc;
                     ml.out.best_j[row] = pass ? j1 : -1;

@@ -187,7 +187,7 @@ __device__ __forceinline__ void match_query(const MatchLaunch& ml, const DevImag
         const bool h1 = m1 != ~0ull, h2 = m2 != ~0ull;
         const uint32_t d1 = h1 ? (uint32_t)(m1 >> 16) : kEmpty;
         const uint32_t d2 = h2 ? (uint32_t)(m2 >> 16) : kEmpty;
-        const bool ok = h2 && ratio_pass(d1, d2, ml.ratio_num, ml.ratio_den, rechecks);
+        const bool ok = h2 && ratio_pass(d1, d2, ml.ratio_num, ml.ratio_den, ml.ratio_lo, ml.ratio_hi, rechecks);
         ml.out.best_j[row] = ok ? (int32_t)(m1 & 0xFFFFu) : -1;
         if (ml.out.d1sq) ml.out.d1sq[row] = d1;
         if (ml.out.d2sq) ml.out.d2sq[row] = d2;

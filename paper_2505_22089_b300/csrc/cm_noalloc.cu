@@ -280,6 +280,8 @@ extern "C" cm_status cm_match_pair_noalloc(const cm_params* p, const uint8_t* d_
         m.K = p->K;
         m.ratio_num = p->ratio_num;
         m.ratio_den = p->ratio_den;
+        m.ratio_lo = ratio_band(p->ratio_num, p->ratio_den).lo;
+        m.ratio_hi = ratio_band(p->ratio_num, p->ratio_den).hi;
         m.rerank = p->rerank;
         m.algo = tile ? CM_ALGO_TILE : CM_ALGO_WARP;
         m.counter = reinterpret_cast<unsigned*>(base + g.counter);

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kRcThreads) k_rerank_cc(MatchLaunch ml) {
         }
         if (active && l8 == 0) {
             bool pass = false;
-            if (j2 >= 0) pass = ratio_pass(d1, d2, ml.ratio_num, ml.ratio_den, rechecks);
+            if (j2 >= 0) pass = ratio_pass(d1, d2, ml.ratio_num, ml.ratio_den, ml.ratio_lo, ml.ratio_hi, rechecks);
             ml.out.best_j[row] = pass ? j1 : -1;
             if (ml.out.d1sq) ml.out.d1sq[row] = d1;
             if (ml.out.d2sq) ml.out.d2sq[row] = d2;

@@ -80,3 +80,30 @@ def test_mutual_filter_rejects_aliasing():
         cm.check(cm.lib().cm_match_plan_mutual(plan.h, cm._ptr(out["best_j"]), cm._ptr(out["best_j"]),
                                                cm._stream(None)))
     assert e.value.status == cm.CM_ERR_INVALID
+
+
+@pytest.mark.parametrize("form", ["fp32", "int", "bf16", "fp8"])
+def test_ratio_recheck_count_is_the_band(form):
+    # The ratio test is decided in FP32 outside the band |sqrt(d1 / d2) - t_r| < 1e-3
+    # and re-checked in FP64 inside it (Sec. 2.3.1 step (4) with the exact
+    # threshold): the re-check count must be the number of queries in the band,
+    # up to rounding at its two edges, and the match count the number of matches.
+    # t_r = 0.95 puts many queries in the band (most second neighbours are close)
+    wl = synth.strip30(n_images=8, n=6000)
+    desc = torch.from_numpy(wl.generate()).cuda()
+    p = cm.Params.make(rerank=form, ratio=(19, 20))
+    index = cm.Index.build(p, wl.n_desc, desc)
+    plan, out = _best(index, wl.pairs)
+    best = out["best_j"].cpu().numpy()
+    d1 = out["d1sq"].cpu().numpy().view(np.uint32).astype(np.float64)
+    d2 = out["d2sq"].cpu().numpy().view(np.uint32).astype(np.float64)
+    rechecks, matches = (int(x) for x in out["stats"].cpu().numpy()[:2])
+    assert matches == int((best >= 0).sum())
+    tr = p.ratio_num / p.ratio_den
+    tested = (d2 > 0) & (d2 != 0xFFFFFFFF)
+    r = np.sqrt(d1[tested] / d2[tested])
+    gap = np.abs(np.abs(r - tr) - 1e-3)
+    inside = int((np.abs(r - tr) < 1e-3).sum())
+    edge = int((gap < 1e-6).sum())
+    assert inside - edge <= rechecks <= inside + edge, (rechecks, inside, edge)
+    assert inside > 10   # the workload reaches the band
