@@ -49,17 +49,17 @@ constexpr uint16_t kNoCand = 0xFFFFu;
 
 template <int K, bool FP8>
 struct RR {
-    // Launch shape.  BF16: two CTAs per SM (two MMA issuers; one issuing
+    // Launch shape, both forms: two CTAs per SM (two MMA issuers; one issuing
     // thread's 8 MMAs per sub-tile bounded a CTA), 4 producer warps and one
-    // epilogue group each.  FP8: its exact re-score makes the epilogue the
-    // busier role, which wants two epilogue groups; those do not fit the
-    // register file twice, so FP8 keeps one CTA per SM with 8 producer warps.
-    static constexpr int CTAS = FP8 ? 1 : 2;              // CTAs per SM
-    static constexpr int PROD_WARPS = FP8 ? 8 : 4;
+    // epilogue group each.  Two epilogue groups per CTA do not fit the
+    // register file twice: BF16 then needs fewer producers and lost, FP8
+    // spilled and was no faster.
+    static constexpr int CTAS = 2;                        // CTAs per SM
+    static constexpr int PROD_WARPS = 4;
     static constexpr int PROD = PROD_WARPS * 32;          // producer threads
     static constexpr int MMA_WARP = PROD_WARPS;
     static constexpr int EPI_WARP0 = PROD_WARPS + 1;
-    static constexpr int EPI = FP8 ? 2 : 1;               // epilogue groups of 4 warps, taking sub-tiles in turn
+    static constexpr int EPI = 1;                         // epilogue groups of 4 warps, taking sub-tiles in turn
     static constexpr int THREADS = (PROD_WARPS + 1 + 4 * EPI) * 32;
     static constexpr int QS = 128 / K;                    // queries per sub-tile
     static constexpr int NB = QS < 16 ? 16 : QS;          // B rows = MMA N
