@@ -117,9 +117,25 @@ struct Cursor {
     const float *iscale = nullptr, *jscale = nullptr;
     const uint8_t *idesc = nullptr, *jdesc = nullptr;
     DevPair nxt{};   // record of pair + 1
+    // u = item * per_item + part, stepped without a division when u grows by the grid
+    int last_u = -1, cur_item = 0, cur_part = 0, step_item = 0, step_part = 0;
 
     __device__ __forceinline__ SubTile at(const MatchLaunch& ml, int u, int per_item, int qs) {
-        const int item = u / per_item;
+        if (last_u >= 0 && u == last_u + (int)gridDim.x) {
+            cur_item += step_item;
+            cur_part += step_part;
+            if (cur_part >= per_item) {
+                cur_part -= per_item;
+                ++cur_item;
+            }
+        } else {
+            step_item = (int)gridDim.x / per_item;
+            step_part = (int)gridDim.x % per_item;
+            cur_item = u / per_item;
+            cur_part = u % per_item;
+        }
+        last_u = u;
+        const int item = cur_item;
         while (item >= item_end && pair + 1 < ml.n_pairs) {
             ++pair;
             const DevPair P = pair == 0 ? ml.pairs[0] : nxt;
@@ -142,7 +158,7 @@ struct Cursor {
             }
         }
         SubTile t;
-        t.q0 = (item - item0) * ml.S + (u % per_item) * qs;
+        t.q0 = (item - item0) * ml.S + cur_part * qs;
         t.nq = (item < item_end && t.q0 < n_i) ? min(qs, n_i - t.q0) : 0;
         t.row = row_off + t.q0;
         t.ixq = ixq;
