@@ -94,6 +94,7 @@ struct SubTile {
     const uint32_t *inorm, *jnorm;
     const float *iscale, *jscale;
     const uint8_t *idesc, *jdesc;
+    int n_j;       // rows of the database image
 };
 
 // Index of kept candidate e (flat [row][K] position) and, from the plan's
@@ -116,6 +117,7 @@ struct Cursor {
     const uint32_t *inorm = nullptr, *jnorm = nullptr;
     const float *iscale = nullptr, *jscale = nullptr;
     const uint8_t *idesc = nullptr, *jdesc = nullptr;
+    int n_j = 0;
     DevPair nxt{};   // record of pair + 1
     // u = item * per_item + part, stepped without a division when u grows by the grid
     int last_u = -1, cur_item = 0, cur_part = 0, step_item = 0, step_part = 0;
@@ -149,6 +151,7 @@ struct Cursor {
                 const DevImage& J = ml.imgs[P.j];
                 ixq = static_cast<const unsigned char*>(I.xq);
                 jxq = static_cast<const unsigned char*>(J.xq);
+                n_j = J.n;
                 inorm = I.norm;
                 jnorm = J.norm;
                 iscale = I.xscale;
@@ -169,6 +172,7 @@ struct Cursor {
         t.jscale = jscale;
         t.idesc = idesc;
         t.jdesc = jdesc;
+        t.n_j = n_j;
         return t;
     }
 };
@@ -322,13 +326,16 @@ __global__ void __launch_bounds__(RR<K, FP8>::THREADS, RR<K, FP8>::CTAS) k_reran
             const uint32_t A = tc::smem_addr(ring + (size_t)s * C::STAGE) + cofs;
             const uint32_t B = tc::smem_addr(ring + (size_t)s * C::STAGE) + C::HALVES * C::A_HALF + bofs;
             const unsigned char* qrow = t.ixq + (size_t)t.q0 * rb + c * 16;   // a valid row for padding
-            const unsigned char* jrow = t.jxq + c * 16;
+            // an empty slot (kNoCand) copies the database image's last row, a real row whose
+            // product the epilogue ignores; with no database row at all, the query row
+            const unsigned char* jrow = t.n_j > 0 ? t.jxq + c * 16 : qrow;
+            const uint32_t jmax = t.n_j > 0 ? (uint32_t)(t.n_j - 1) : 0u;
 #pragma unroll
             for (int q = 0; q < RPT; ++q) {
                 const int r = r0 + q;
                 const uint32_t j = (jw[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
                 const uint32_t dst = A + (uint32_t)r * 128u + (uint32_t)((c8 ^ (r & 7)) << 4);
-                const unsigned char* src = j != kNoCand ? jrow + (size_t)j * rb : qrow;
+                const unsigned char* src = jrow + (size_t)min(j, jmax) * rb;
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
             }
 #pragma unroll
