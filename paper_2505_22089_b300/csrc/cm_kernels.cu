@@ -277,21 +277,39 @@ __global__ void __launch_bounds__(128) k_bucket(HashLaunch h) {
     const unsigned lt = (1u << lane) - 1u;
     uint4* scode = e.scode + (size_t)t * e.n;
     uint16_t* sidx = e.sidx + (size_t)t * e.n;
-    for (int c0 = 0; c0 < e.n; c0 += 32) {
-        const int i = c0 + lane;
-        const unsigned vm = __ballot_sync(0xFFFFFFFFu, i < e.n);
-        if (i < e.n) {
-            const int k = (int)((e.key[i] >> (8 * t)) & 0xFFu);
-            const unsigned peers = __match_any_sync(vm, k);
-            const int rank = __popc(peers & lt);
-            const uint32_t p0 = base[k];
-            __syncwarp(vm);
-            if (rank == 0) base[k] = p0 + __popc(peers);
-            __syncwarp(vm);
-            scode[p0 + rank] = e.code[i];
-            sidx[p0 + rank] = (uint16_t)i;
+    // rows in groups of 32, U groups at a time: their keys and codes are loaded
+    // before the first is scattered (the scatter is a chain through base[], the
+    // loads are not), so one warp keeps U loads of each in flight
+    constexpr int U = 8;
+    for (int c0 = 0; c0 < e.n; c0 += 32 * U) {
+        uint64_t kk[U];
+        uint4 cc[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int i = c0 + 32 * q + lane;
+            if (i < e.n) {
+                kk[q] = e.key[i];
+                cc[q] = e.code[i];
+            }
         }
-        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int i = c0 + 32 * q + lane;
+            const unsigned vm = __ballot_sync(0xFFFFFFFFu, i < e.n);
+            if (vm == 0u) break;   // the image's rows end in this group (uniform)
+            if (i < e.n) {
+                const int k = (int)((kk[q] >> (8 * t)) & 0xFFu);
+                const unsigned peers = __match_any_sync(vm, k);
+                const int rank = __popc(peers & lt);
+                const uint32_t p0 = base[k];
+                __syncwarp(vm);
+                if (rank == 0) base[k] = p0 + __popc(peers);
+                __syncwarp(vm);
+                scode[p0 + rank] = cc[q];
+                sidx[p0 + rank] = (uint16_t)i;
+            }
+            __syncwarp();
+        }
     }
 }
 
