@@ -278,12 +278,14 @@ class Schedule:
         self.pairs = pairs
         self.rows = []
         r = ScheduleRow()
+
+        def ids(ptr, n):
+            return np.ctypeslib.as_array(ptr, shape=(n,)).tolist() if n > 0 else []
+
         for k in range(lib().cm_schedule_num_rows(h)):
             check(lib().cm_schedule_get_row(h, k, ctypes.byref(r)))
-            self.rows.append({"iteration": r.iteration,
-                              "load": [r.load[q] for q in range(r.n_load)],
-                              "free": [r.free_ids[q] for q in range(r.n_free)],
-                              "pairs": [r.pairs[q] for q in range(r.n_pairs)]})
+            self.rows.append({"iteration": r.iteration, "load": ids(r.load, r.n_load),
+                              "free": ids(r.free_ids, r.n_free), "pairs": ids(r.pairs, r.n_pairs)})
         self.iterations = lib().cm_schedule_num_iterations(h)
 
     def close(self):

@@ -115,14 +115,13 @@ void order_component(const Graph& g, const std::vector<int>& nodes, const std::v
     std::vector<std::vector<int>> by_level(k + 1);
     for (int w : sorted_nodes) by_level[level[w]].push_back(w);
     std::vector<int> number(g.n, -1);
+    std::vector<long long> first(g.n, LLONG_MAX);   // smallest number of a neighbour in the previous level
     int next_number = (int)out.size();
     for (int l = 0; l <= k; ++l) {
         auto& members = by_level[l];
         if (l == 0) {
             std::sort(members.begin(), members.end(), by_deg_id);
         } else {
-            std::vector<std::pair<long long, int>> key(members.size());
-            std::map<int, long long> first;
             for (int w : members) {
                 long long best = LLONG_MAX;
                 for (int y : g.adj[w])
@@ -231,8 +230,10 @@ extern "C" cm_status cm_schedule_blocks(const cm_pair* pairs, int64_t n_pairs, i
         cm_status st = cm_image_bytes(p, n_desc[i], &nbytes[i]);
         if (st != CM_OK) return st;
     }
-    // step (1): symmetric adjacency; an edge carries every input pair on it
-    std::map<std::pair<int, int>, std::vector<int64_t>> edge_pairs;
+    // step (1): symmetric adjacency; an edge carries every input pair on it.  The
+    // pairs sorted by edge (min, max, then pair id): edge e owns pair ids
+    // epair[ebeg[e] .. ebeg[e+1]), edges in (min, max) order.
+    std::vector<std::pair<uint64_t, int64_t>> keyed((size_t)n_pairs);
     for (int64_t k = 0; k < n_pairs; ++k) {
         const int a = pairs[k].i, b = pairs[k].j;
         if (a < 0 || b < 0 || a >= n_images || b >= n_images)
@@ -241,17 +242,35 @@ extern "C" cm_status cm_schedule_blocks(const cm_pair* pairs, int64_t n_pairs, i
         if (nbytes[a] + nbytes[b] > budget)
             return sfail(CM_ERR_BUDGET, "schedule: pair %lld (%d,%d) needs %llu bytes, budget %llu", (long long)k, a, b,
                          (unsigned long long)(nbytes[a] + nbytes[b]), (unsigned long long)budget);
-        edge_pairs[{std::min(a, b), std::max(a, b)}].push_back(k);
+        keyed[(size_t)k] = {((uint64_t)std::min(a, b) << 32) | (uint64_t)std::max(a, b), k};
     }
+    std::sort(keyed.begin(), keyed.end());
+    std::vector<std::pair<int, int>> edge;   // (min, max) per edge
+    std::vector<int64_t> ebeg, epair((size_t)n_pairs);
+    for (size_t q = 0; q < keyed.size(); ++q) {
+        if (q == 0 || keyed[q].first != keyed[q - 1].first) {
+            edge.push_back({(int)(keyed[q].first >> 32), (int)(keyed[q].first & 0xFFFFFFFFu)});
+            ebeg.push_back((int64_t)q);
+        }
+        epair[q] = keyed[q].second;
+    }
+    ebeg.push_back((int64_t)keyed.size());
+    const int n_edges = (int)edge.size();
     cm_schedule* s = new (std::nothrow) cm_schedule();
     if (!s) return sfail(CM_ERR_NOMEM, "schedule: host allocation");
     s->pairs.assign(pairs, pairs + n_pairs);
-    std::set<std::pair<int, int>> remaining;
-    for (auto& kv : edge_pairs) remaining.insert(kv.first);
+    std::vector<char> alive((size_t)n_edges, 1);   // not yet placed in a row
+    int n_remaining = n_edges;
+    auto edge_pair_ids = [&](int e, std::vector<int64_t>& dst) {
+        dst.insert(dst.end(), epair.begin() + ebeg[e], epair.begin() + ebeg[e + 1]);
+    };
     int it = 0;
-    while (!remaining.empty()) {
+    while (n_remaining > 0) {
         // step (2): GPS permutation of the remaining graph
-        std::vector<std::pair<int, int>> E(remaining.begin(), remaining.end());
+        std::vector<std::pair<int, int>> E;
+        E.reserve((size_t)n_remaining);
+        for (int e = 0; e < n_edges; ++e)
+            if (alive[e]) E.push_back(edge[e]);
         const std::vector<int> order = gps(n_images, E);
         // step (3): chunks and block rows
         std::vector<std::vector<int>> chunks;
@@ -276,11 +295,13 @@ extern "C" cm_status cm_schedule_blocks(const cm_pair* pairs, int64_t n_pairs, i
                 chunk_of[w] = c;
                 chunk_bytes[c] += nbytes[w];
             }
-        std::vector<std::vector<std::pair<int, std::pair<int, int>>>> by_lower(nc);
-        for (auto& e : remaining) {
-            const int ca = chunk_of[e.first], cb = chunk_of[e.second];
-            by_lower[std::min(ca, cb)].push_back({std::max(ca, cb), e});
-        }
+        // edges by their lower chunk: (upper chunk, edge id), in edge order
+        std::vector<std::vector<std::pair<int, int>>> by_lower(nc);
+        for (int e = 0; e < n_edges; ++e)
+            if (alive[e]) {
+                const int ca = chunk_of[edge[e].first], cb = chunk_of[edge[e].second];
+                by_lower[std::min(ca, cb)].push_back({std::max(ca, cb), e});
+            }
         std::vector<int> resident;
         std::vector<char> is_res(n_images, 0);
         int64_t placed = 0;
@@ -300,15 +321,14 @@ extern "C" cm_status cm_schedule_blocks(const cm_pair* pairs, int64_t n_pairs, i
                         resident.push_back(w);
                         is_res[w] = 1;
                     }
-            std::vector<std::pair<int, int>> take;
             for (auto& ce : by_lower[r])
-                if (ce.first <= hi) take.push_back(ce.second);
-            for (auto& e : take) {
-                for (int64_t k : edge_pairs[e]) row.pairs.push_back(k);
-                remaining.erase(e);
-            }
+                if (ce.first <= hi) {
+                    edge_pair_ids(ce.second, row.pairs);
+                    alive[ce.second] = 0;
+                    --n_remaining;
+                    ++placed;
+                }
             std::sort(row.pairs.begin(), row.pairs.end());
-            placed += (int64_t)take.size();
             // step (4) / Sec. 2.3.2 step (3): free the first block; everything after the last row
             std::vector<int> freed = (r == nc - 1) ? resident : chunks[r];
             for (int w : freed) is_res[w] = 0;
@@ -320,16 +340,18 @@ extern "C" cm_status cm_schedule_blocks(const cm_pair* pairs, int64_t n_pairs, i
             s->rows.push_back(std::move(row));
         }
         if (placed == 0) {
-            for (auto& e : remaining) {
+            for (int e = 0; e < n_edges; ++e) {
+                if (!alive[e]) continue;
                 cm_schedule::Row row;
                 row.iteration = it;
-                row.load = {e.first, e.second};
-                row.free_ids = {e.first, e.second};
-                row.pairs = edge_pairs[e];
+                row.load = {edge[e].first, edge[e].second};
+                row.free_ids = {edge[e].first, edge[e].second};
+                edge_pair_ids(e, row.pairs);
                 std::sort(row.pairs.begin(), row.pairs.end());
                 s->rows.push_back(std::move(row));
+                alive[e] = 0;
             }
-            remaining.clear();
+            n_remaining = 0;
         }
         ++it;
     }
