@@ -94,21 +94,47 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_hash_tc(HashLaunch h) {
     const int B = 1 << h.m, LB = h.L * B;
     uint32_t parity = 0;
 
-    for (int tile = blockIdx.x; tile < h.n_tiles128; tile += gridDim.x) {
+    // The tile's image, first row and rows, and thread tid's descriptor row of it
+    // (zeros past the image).  Each tile's row is loaded one tile ahead, so the
+    // loads are in flight while the tile before is converted, multiplied and signed.
+    auto tile_of = [&](int tile, DevImage& e, int& row0, int& nrows) {
         const int bidx = find_tile_image(h.tile_pref128, h.n_batch, tile);
-        const DevImage e = h.imgs[h.batch[bidx]];
-        const int row0 = (tile - h.tile_pref128[bidx]) * kTcRows;
-        const int nrows = min(kTcRows, e.n - row0);
+        e = h.imgs[h.batch[bidx]];
+        row0 = (tile - h.tile_pref128[bidx]) * kTcRows;
+        nrows = min(kTcRows, e.n - row0);
+    };
+    auto load_row = [&](const DevImage& e, int row0, int nrows, uint4 (&v)[8]) {
+        const bool have = tid < nrows;
+        const uint4* src = reinterpret_cast<const uint4*>(e.desc + (size_t)(row0 + (have ? tid : 0)) * kDim);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = have ? __ldg(src + c) : make_uint4(0, 0, 0, 0);
+    };
+    DevImage e_next{};
+    int row0_next = 0, nrows_next = 0;
+    uint4 v_next[8];
+    if (blockIdx.x < h.n_tiles128) {
+        tile_of(blockIdx.x, e_next, row0_next, nrows_next);
+        load_row(e_next, row0_next, nrows_next, v_next);
+    }
+
+    for (int tile = blockIdx.x; tile < h.n_tiles128; tile += gridDim.x) {
+        const DevImage e = e_next;
+        const int row0 = row0_next, nrows = nrows_next;
+        uint4 vrow[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) vrow[c] = v_next[c];
+        if (tile + (int)gridDim.x < h.n_tiles128) {   // the next tile's row, loaded during this one
+            tile_of(tile + (int)gridDim.x, e_next, row0_next, nrows_next);
+            load_row(e_next, row0_next, nrows_next, v_next);
+        }
         for (int b = tid; b < LB; b += kTcThreads) hist[b] = 0;
 
         // stage: thread tid converts descriptor row0 + tid to BF16 in the operand layout
         const bool have = tid < nrows;
-        const uint4* src = reinterpret_cast<const uint4*>(e.desc + (size_t)(row0 + (have ? tid : 0)) * kDim);
         unsigned nn = 0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (have) v = __ldg(src + c);
+            const uint4 v = vrow[c];
             nn = __dp4a(v.x, v.x, nn);
             nn = __dp4a(v.y, v.y, nn);
             nn = __dp4a(v.z, v.z, nn);
