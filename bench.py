@@ -1283,7 +1283,10 @@ def run_reference(args, rank, world):
     return {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": np.mean(times) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (%s)" % args.workload,
-            "config": {"workload": args.workload}, "impl": "reference",
+            "config": {"workload": args.workload, "images": wl.n_images, "pairs": len(wl.pairs),
+                       "descriptors": int(np.sum(wl.n_desc)), "L": op.L, "m": op.m, "K": op.K,
+                       "ratio": "%d/%d" % (op.ratio_num, op.ratio_den), "sample_pairs": int(len(sel))},
+            "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
